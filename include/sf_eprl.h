@@ -1,0 +1,168 @@
+/*
+ * sf_eprl.h -- C ABI of the GB300 library for the Lorentzian EPRL vertex amplitude shell sum
+ * (F. Gozzini, "A high-performance code for EPRL spin foam amplitudes", arXiv:2107.13952).
+ *
+ * The library computes, on one GPU,
+ *
+ *   A_v(j_f; i_e) = prod_{e=1..5} sqrt(2 i_e + 1)
+ *                   * sum_{shells l} sum_{k_2..k_5} prod_{e=2..5} (2k_e+1) B4_e(i_e, k_e) {15j}(j, l; i_1, k_2..k_5)
+ *
+ * (Sec. 2, eq. vertex-ampl), with the {15j} as the auxiliary-spin sum of five {6j} (Sec. 2, eq. 15j)
+ * and the boosters B4 by rapidity quadrature of SL(2,C) boost matrix elements (Sec. 2, eq. booster;
+ * Sec. 3 "Booster coefficients"), following the framed vertex algorithm of Sec. 3 "Tensor contractions".
+ *
+ * Conventions (used by every entry point):
+ *   - Spins are DOUBLED integers: two_j = 2*j, so half-integers are exact.
+ *   - Boundary order:  two_j[0..9] = (j12, j13, j14, j15, j23, j24, j25, j34, j35, j45)   (Sec. 2).
+ *   - Free faces (23, 24, 25, 34, 35, 45) carry l_f = j_f + d_f, d_f = 0..dl; gauge faces l_1b = j_1b.
+ *   - Linear shell index  s = ((((d23*D + d24)*D + d25)*D + d34)*D + d35)*D + d45,  D = dl+1,
+ *     s in [0, D^6)  (the paper's (Delta s + 1)^6 loops, Sec. 3 "Parallelization").
+ *   - Intertwiner ranges: edge 1 couples (j12 j13 | j14 j15), edge 2 (j23 j24 | j25 j12),
+ *     edge 3 (j34 j35 | j13 j23), edge 4 (j45 j14 | j24 j34), edge 5 (j15 j25 | j35 j45)
+ *     (the booster index orders of the framed algorithm, step 3).
+ *   - Output tensor A[i1][i2][i3][i4][i5], i5 fastest: byte-identical to the paper's column-major
+ *     A^{i5 i4 i3 i2 i1} (Sec. 3, footnote on the result layout). Index n_e = (i_e - i_e,lo).
+ *   - Booster tensor of edge e: B[t][i - i_lo][k - k_lo(t)], t = (a*D + b)*D + c the mixed-radix
+ *     index of the edge's three free-face offsets in argument order: edge 2 (d23, d24, d25),
+ *     edge 3 (d34, d35, d23), edge 4 (d45, d24, d34), edge 5 (d25, d35, d45); padded with zeros to
+ *     D_kmax columns (the paper's booster tensors B^{l1 l2 l3 l4 i k}, Sec. 3).
+ *
+ * Memory and streams:
+ *   - sf_tables is opaque and owns its device memory (6j tables, d-tables, boosters, scratch); it is
+ *     released by sf_tables_free. Every other pointer belongs to the caller; the library never frees it.
+ *   - Pointers documented "device" must be device (or managed) memory on the current device.
+ *   - Every compute call is enqueued on `stream` and synchronises that stream before returning, so a
+ *     returned status covers the device work. Calls on one sf_tables object must not overlap.
+ *
+ * Errors: every int-returning call returns SF_OK (0) or a negative code; sf_last_error() gives a
+ * thread-local message for the last failure on the calling thread.
+ */
+#ifndef SF_EPRL_H
+#define SF_EPRL_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SF_OK           0
+#define SF_ERR_ARG     -1   /* bad argument: triangle/parity failure, gamma <= 0, dl < 0, sizes   */
+#define SF_ERR_EMPTY   -2   /* an intertwiner range of the boundary is empty                      */
+#define SF_ERR_OOM     -3   /* device allocation failed                                           */
+#define SF_ERR_CUDA    -4   /* a CUDA runtime call or kernel launch failed                        */
+#define SF_ERR_TIMEOUT -5   /* a bounded device wait gave up                                      */
+#define SF_ERR_NUMERIC -6   /* a numerical self-check failed (e.g. non-real booster)              */
+#define SF_ERR_LIMIT   -7   /* spins or dimensions beyond the compiled limits                     */
+
+/* One vertex boundary (Sec. 3, framed algorithm step 1: ten spins and the number of shells). */
+typedef struct {
+    int32_t two_j[10];   /* doubled boundary spins, order above                                  */
+    double  gamma;       /* Barbero-Immirzi parameter; Y-map (rho, k) = (gamma (j+1), j)           */
+    int32_t dl;          /* shell cutoff Delta s: l_f in [j_f, j_f + dl]                          */
+} sf_vertex;
+
+/* Rapidity rule (Sec. 3 "Booster coefficients"): x = e^-r on [e^-r_max, 1] split into n_panels
+ * panels with |I_k| = k |I_1| (smallest at x -> 0), `order` Gauss-Legendre nodes per panel. */
+typedef struct {
+    double  r_max;
+    int32_t n_panels;
+    int32_t order;
+} sf_quad_rule;
+
+typedef enum {
+    SF_FP64  = 0,   /* every step in FP64                                                         */
+    SF_MIXED = 1    /* {6j}/{15j} blocks in FP64; booster contractions on tensor cores with
+                       FP32-class accuracy and FP32 accumulation per shell; FP64 across shells */
+} sf_precision;
+
+typedef struct sf_tables sf_tables;
+
+/* Library version string (static). */
+const char* sf_version(void);
+
+/* Thread-local message of the last failure on this thread ("" if none). Static storage. */
+const char* sf_last_error(void);
+
+/* Host helper (no device work): doubled lower bounds and dimensions of i_1..i_5
+ * (framed algorithm step 2). Returns SF_ERR_EMPTY if a range is empty, SF_ERR_ARG on bad input. */
+int sf_intertwiner_ranges(const sf_vertex* v, int32_t two_lo[5], int32_t dim[5]);
+
+/* Host helper: number of shells (dl+1)^6 of a vertex, or a negative error code. */
+int64_t sf_num_shells(const sf_vertex* v);
+
+/* Build the five {6j} tables S1..S5 of Sec. 3 framed algorithm step 4 for n vertices, exactly
+ * (integer Racah sum, rounded once to FP64), and allocate the tables object.
+ *   S1[l25][i1, k5, x] = {i1 l25 x; k5 j14 j15}      S2[l35, l45][k5, k4, x] = {j14 k5 x; l35 k4 l45}
+ *   S3[l24, l34, l35][k4, k3, x] = {k4 l35 x; k3 l24 l34}
+ *   S4[l23, l24][k3, k2, x] = {l24 k3 x; j13 k2 l23}  S5[l25][k2, i1, x] = {k2 j13 x; i1 l25 j12}
+ * v: host array of n vertices. *out receives a new object (free with sf_tables_free). */
+int sf_6j_table(const sf_vertex* v, int32_t n, sf_tables** out, cudaStream_t stream);
+
+/* Compute the booster tensors of every vertex in t (Sec. 2 eq. booster, Sec. 3): d-tables
+ * d^{gamma(j+1), j}_{j l m}(r_n) on the rule's nodes, 4jm symbols, quadrature and m-sum.
+ * q: host pointer to the rule. */
+int sf_boosters(sf_tables* t, const sf_quad_rule* q, cudaStream_t stream);
+
+/* Shape of the booster tensor of (vertex, edge in 2..5): shape = {n_triples, D_i, D_kmax}. */
+int sf_booster_shape(const sf_tables* t, int32_t vertex, int32_t edge, int64_t shape[3]);
+
+/* Replace (upload) or read back (download) the booster tensor of (vertex, edge), layout above.
+ * B: host or device pointer to shape[0]*shape[1]*shape[2] doubles; padded entries are ignored
+ * on upload and written as zero on download. Upload lets a caller inject boosters computed
+ * elsewhere (e.g. the SU(2) BF limit (2k+1)B = delta_ik). */
+int sf_boosters_upload(sf_tables* t, int32_t vertex, int32_t edge, const double* B, cudaStream_t stream);
+int sf_boosters_download(const sf_tables* t, int32_t vertex, int32_t edge, double* B, cudaStream_t stream);
+
+/* Vertex amplitude tensors by the shell sum (framed algorithm steps 5-7).
+ *   precision  SF_FP64 or SF_MIXED.
+ *   shell_begin, shell_end: linear shell range [begin, end) of every vertex (clamped to its shell
+ *     count; pass 0 and INT64_MAX for all shells). Partial sums over disjoint ranges add up, so a
+ *     long sum can be split or resumed.
+ *   shell_list, n_list: optional host array of linear shell indices (single-vertex tables only);
+ *     when non-NULL it replaces the range. Duplicates count once.
+ *   A_out: host array of n device pointers, A_out[v] -> prod_e dim_e doubles, overwritten.
+ * Uses library-owned scratch for per-block partial sums, reduced in a fixed order (deterministic). */
+int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t shell_begin, int64_t shell_end,
+                        const int64_t* shell_list, int64_t n_list, double* const* A_out,
+                        cudaStream_t stream);
+
+/* Boundary-contracted amplitude and its adjoint (single-vertex tables):
+ *   a = sum_i A[i1..i5] psi_1[i1] psi_2[i2] psi_3[i3] psi_4[i4] psi_5[i5]
+ * (the paper's contraction of a vertex tensor with boundary intertwiner vectors, Sec. 3 usage),
+ * recomputing every shell's {15j} ring on the fly (never stored).
+ *   psi[e]: device pointer to dim_e complex doubles (interleaved re, im).
+ *   a_out: device pointer to one complex double.
+ *   grad_psi[e] (optional, NULL to skip): device, dim_e complex doubles: the holomorphic
+ *     derivative d a / d psi_e.
+ *   grad_B[e-2] (optional): device, shape of the edge-e booster tensor, complex doubles:
+ *     d a / d B_e[t][i][k] (zero on padded entries).
+ * Precision: SF_FP64 only. */
+int sf_vertex_adjoint(sf_tables* t, const double* const psi[5], double* a_out,
+                      double* const grad_psi[5], double* const grad_B[4], cudaStream_t stream);
+
+/* Read-only access to internal tables for verification.
+ *   kind SF_TAB_6J:    index 1..5 -> table S_index, all slots concatenated (doubles)
+ *   kind SF_TAB_6J_SLOTS: index 1..5 -> slot descriptors, 8 int64 each:
+ *                      {offset, a_lo, b_lo, x_lo, n_a, n_b, n_x, 0} (doubled lows, entries
+ *                      slot[offset + (ia*n_b + ib)*n_x + ix] for a = a_lo + 2 ia, ...)
+ *   kind SF_TAB_D:     index 0..9 -> d-table of that face, complex doubles
+ *                      [n_l][2k+1][n_nodes] (l = j + il, m = -k + im)
+ *   kind SF_TAB_NODES: index 0 -> rule x_n, 1 -> rule weights w_n, 2 -> r_n = -ln x_n (doubles)
+ * sf_table_size returns the byte size; sf_table_copy copies it into dst (host or device). */
+#define SF_TAB_6J       1
+#define SF_TAB_6J_SLOTS 2
+#define SF_TAB_D        3
+#define SF_TAB_NODES    4
+int64_t sf_table_size(const sf_tables* t, int32_t vertex, int32_t kind, int32_t index);
+int sf_table_copy(const sf_tables* t, int32_t vertex, int32_t kind, int32_t index, void* dst,
+                  int64_t n_bytes, cudaStream_t stream);
+
+/* Release the tables object and all its device memory (NULL is a no-op). */
+void sf_tables_free(sf_tables* t);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SF_EPRL_H */

@@ -1,0 +1,242 @@
+"""Python binding of the GB300 EPRL vertex library (C ABI in include/sf_eprl.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA kernels of
+``libsf_eprl.so``. PyTorch supplies device memory and the current CUDA stream. There is no CPU
+fallback: if the library is missing or no GPU is present the calls raise.
+
+    import paper_2107_13952_gb300 as sf
+    t = sf.sf_6j_table([sf.vertex((2,)*10, 1.2, 2)])
+    sf.sf_boosters(t, (40.0, 40, 50))
+    A, = sf.sf_vertex_amplitude(t)           # torch float64 tensor [i1][i2][i3][i4][i5] on cuda
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+_LIB = None
+_LIB_PATH = _build.LIB
+
+SF_OK, SF_ERR_ARG, SF_ERR_EMPTY, SF_ERR_OOM, SF_ERR_CUDA, SF_ERR_TIMEOUT, SF_ERR_NUMERIC, SF_ERR_LIMIT = \
+    0, -1, -2, -3, -4, -5, -6, -7
+SF_FP64, SF_MIXED = 0, 1
+SF_TAB_6J, SF_TAB_6J_SLOTS, SF_TAB_D, SF_TAB_NODES = 1, 2, 3, 4
+
+# names of every symbol declared in include/sf_eprl.h
+EXPORTS = ("sf_version", "sf_last_error", "sf_intertwiner_ranges", "sf_num_shells", "sf_6j_table",
+           "sf_boosters", "sf_booster_shape", "sf_boosters_upload", "sf_boosters_download",
+           "sf_vertex_amplitude", "sf_vertex_adjoint", "sf_table_size", "sf_table_copy", "sf_tables_free")
+
+
+class SfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("sf error %d: %s" % (code, msg))
+        self.code = code
+
+
+class sf_vertex(ctypes.Structure):
+    _fields_ = [("two_j", ctypes.c_int32 * 10), ("gamma", ctypes.c_double), ("dl", ctypes.c_int32)]
+
+
+class sf_quad_rule(ctypes.Structure):
+    _fields_ = [("r_max", ctypes.c_double), ("n_panels", ctypes.c_int32), ("order", ctypes.c_int32)]
+
+
+def vertex(two_j, gamma, dl):
+    v = sf_vertex()
+    for i, t in enumerate(two_j):
+        v.two_j[i] = int(t)
+    v.gamma = float(gamma)
+    v.dl = int(dl)
+    return v
+
+
+def _declare(lib):
+    P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "sf_version": (ctypes.c_char_p, []),
+        "sf_last_error": (ctypes.c_char_p, []),
+        "sf_intertwiner_ranges": (ctypes.c_int, [ctypes.POINTER(sf_vertex), ctypes.POINTER(I32), ctypes.POINTER(I32)]),
+        "sf_num_shells": (I64, [ctypes.POINTER(sf_vertex)]),
+        "sf_6j_table": (ctypes.c_int, [ctypes.POINTER(sf_vertex), I32, ctypes.POINTER(P), P]),
+        "sf_boosters": (ctypes.c_int, [P, ctypes.POINTER(sf_quad_rule), P]),
+        "sf_booster_shape": (ctypes.c_int, [P, I32, I32, ctypes.POINTER(I64)]),
+        "sf_boosters_upload": (ctypes.c_int, [P, I32, I32, P, P]),
+        "sf_boosters_download": (ctypes.c_int, [P, I32, I32, P, P]),
+        "sf_vertex_amplitude": (ctypes.c_int, [P, ctypes.c_int, I64, I64, P, I64, ctypes.POINTER(P), P]),
+        "sf_vertex_adjoint": (ctypes.c_int, [P, ctypes.POINTER(P), P, ctypes.POINTER(P), ctypes.POINTER(P), P]),
+        "sf_table_size": (I64, [P, I32, I32, I32]),
+        "sf_table_copy": (ctypes.c_int, [P, I32, I32, I32, P, I64, P]),
+        "sf_tables_free": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def load(path=None):
+    """Load (building first if needed) the in-tree CUDA library; raises if it cannot."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    p = path or _LIB_PATH
+    if not os.path.exists(p):
+        _build.build()
+    lib = ctypes.CDLL(p)
+    _declare(lib)
+    _LIB = lib
+    return lib
+
+
+def _check(rc):
+    if rc != SF_OK:
+        raise SfError(rc, _LIB.sf_last_error().decode())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def intertwiner_ranges(two_j, gamma=1.2, dl=0):
+    """(two_lo[5], dim[5]) of the intertwiners (host logic of the library, no device work)."""
+    lib = load()
+    v = vertex(two_j, gamma, dl)
+    lo = (ctypes.c_int32 * 5)()
+    dim = (ctypes.c_int32 * 5)()
+    _check(lib.sf_intertwiner_ranges(ctypes.byref(v), lo, dim))
+    return list(lo), list(dim)
+
+
+def num_shells(two_j, gamma=1.2, dl=0):
+    lib = load()
+    v = vertex(two_j, gamma, dl)
+    n = lib.sf_num_shells(ctypes.byref(v))
+    if n < 0:
+        _check(int(n))
+    return int(n)
+
+
+class Tables:
+    """Owner of an ``sf_tables*`` (device tables of one or more vertices)."""
+
+    def __init__(self, ptr, vertices):
+        self.ptr = ptr
+        self.vertices = list(vertices)
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _LIB is not None:
+            _LIB.sf_tables_free(self.ptr)
+            self.ptr = None
+
+    def dims(self, vtx=0):
+        v = self.vertices[vtx]
+        lo, dim = intertwiner_ranges(list(v.two_j), v.gamma, v.dl)
+        return lo, dim
+
+
+def sf_6j_table(vertices, stream=None):
+    lib = load()
+    vs = list(vertices)
+    arr = (sf_vertex * len(vs))(*vs)
+    out = ctypes.c_void_p()
+    _check(lib.sf_6j_table(arr, len(vs), ctypes.byref(out), _stream(stream)))
+    return Tables(out, vs)
+
+
+def sf_boosters(tables, rule=(40.0, 40, 50), stream=None):
+    lib = load()
+    q = sf_quad_rule(float(rule[0]), int(rule[1]), int(rule[2]))
+    _check(lib.sf_boosters(tables.ptr, ctypes.byref(q), _stream(stream)))
+
+
+def booster_shape(tables, vtx, edge):
+    lib = load()
+    sh = (ctypes.c_int64 * 3)()
+    _check(lib.sf_booster_shape(tables.ptr, vtx, edge, sh))
+    return tuple(sh)
+
+
+def sf_boosters_download(tables, vtx, edge, stream=None):
+    import torch
+    lib = load()
+    out = torch.zeros(booster_shape(tables, vtx, edge), dtype=torch.float64, device="cuda")
+    _check(lib.sf_boosters_download(tables.ptr, vtx, edge, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def sf_boosters_upload(tables, vtx, edge, B, stream=None):
+    import torch
+    lib = load()
+    B = torch.as_tensor(B, dtype=torch.float64).contiguous()
+    if tuple(B.shape) != booster_shape(tables, vtx, edge):
+        raise ValueError("booster shape %s != %s" % (tuple(B.shape), booster_shape(tables, vtx, edge)))
+    if B.device.type != "cuda":
+        B = B.cuda()
+    _check(lib.sf_boosters_upload(tables.ptr, vtx, edge, ctypes.c_void_p(B.data_ptr()), _stream(stream)))
+
+
+def sf_vertex_amplitude(tables, precision=SF_FP64, shell_begin=0, shell_end=2 ** 63 - 1, shell_list=None,
+                        out=None, stream=None):
+    """Vertex tensors A[i1][i2][i3][i4][i5] (float64, cuda), one per vertex of ``tables``."""
+    import torch
+    lib = load()
+    outs = []
+    for i, v in enumerate(tables.vertices):
+        _, dim = intertwiner_ranges(list(v.two_j), v.gamma, v.dl)
+        if out is not None:
+            o = out[i]
+            assert o.dtype == torch.float64 and o.is_cuda and o.is_contiguous() and list(o.shape) == dim
+        else:
+            o = torch.empty(dim, dtype=torch.float64, device="cuda")
+        outs.append(o)
+    ptrs = (ctypes.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+    lp, nl = None, 0
+    keep = None
+    if shell_list is not None:
+        keep = torch.as_tensor(shell_list, dtype=torch.int64).contiguous()
+        if keep.device.type != "cuda":
+            keep = keep.cuda()
+        lp, nl = ctypes.c_void_p(keep.data_ptr()), int(keep.numel())
+    _check(lib.sf_vertex_amplitude(tables.ptr, int(precision), int(shell_begin), int(shell_end), lp, nl, ptrs,
+                                   _stream(stream)))
+    return outs
+
+
+def table_copy(tables, vtx, kind, index, stream=None):
+    """Copy an internal table to a CPU torch tensor (verification only)."""
+    import torch
+    lib = load()
+    n = lib.sf_table_size(tables.ptr, vtx, kind, index)
+    if n < 0:
+        _check(int(n))
+    if kind == SF_TAB_6J_SLOTS:
+        out = torch.zeros(max(1, n // 8), dtype=torch.int64)
+    else:
+        out = torch.zeros(max(1, n // 8), dtype=torch.float64)
+    _check(lib.sf_table_copy(tables.ptr, vtx, kind, index, ctypes.c_void_p(out.data_ptr()), int(n), _stream(stream)))
+    if kind == SF_TAB_6J_SLOTS:
+        return out.view(-1, 8)
+    if kind == SF_TAB_D:
+        return torch.view_as_complex(out.view(-1, 2))
+    return out
+
+
+def sf_vertex_adjoint(tables, psis, want_grads=True, stream=None):
+    """(a, [d a/d psi_e], [d a/d B_e]) for complex boundary vectors psis (cuda complex128)."""
+    import torch
+    lib = load()
+    psis = [torch.as_tensor(p, dtype=torch.complex128).contiguous().cuda() for p in psis]
+    a = torch.zeros(1, dtype=torch.complex128, device="cuda")
+    pp = (ctypes.c_void_p * 5)(*[p.data_ptr() for p in psis])
+    gp, gb = None, None
+    gps, gbs = [], []
+    if want_grads:
+        gps = [torch.zeros_like(p) for p in psis]
+        gbs = [torch.zeros(booster_shape(tables, 0, e), dtype=torch.complex128, device="cuda") for e in (2, 3, 4, 5)]
+        gp = (ctypes.c_void_p * 5)(*[g.data_ptr() for g in gps])
+        gb = (ctypes.c_void_p * 4)(*[g.data_ptr() for g in gbs])
+    _check(lib.sf_vertex_adjoint(tables.ptr, pp, ctypes.c_void_p(a.data_ptr()), gp, gb, _stream(stream)))
+    return a[0], gps, gbs

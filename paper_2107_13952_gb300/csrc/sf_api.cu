@@ -1,0 +1,647 @@
+// C ABI of the EPRL vertex library (include/sf_eprl.h): argument checks, table planning,
+// device memory ownership and the launch sequence of the kernels.
+#include "sf_internal.cuh"
+#include <algorithm>
+#include <string>
+
+// kernels' launchers (defined in the other translation units)
+int sf_fact_table_build(dd* F, cudaStream_t s);
+int sf_sixj_table_build(int table_id, const VtxDev* d_v, const SlotDesc* d_slots, int nslots, int64_t n,
+                        double* d_out, const dd* F, int* d_status, int num_sms, cudaStream_t s);
+int sf_rule_build(const sf_quad_rule* q, double* d_gl, double* d_x, double* d_w, double* d_r, double* d_W,
+                  cudaStream_t s);
+int sf_dtable_build(int tk, double gamma, int nl, int nnodes, const double* d_r, const double* d_gl, double2* d_out,
+                    cudaStream_t s);
+size_t sf_booster_smem(int tj1, int tj2, int tj3, int tj4, int nk);
+int sf_booster_build(const VtxDev* d_v, int edge, int ntrip, size_t smem, const double* d_W, int nnodes,
+                     const dd* F, double* d_Aj, double* d_Cj, double* d_B, int* d_status, cudaStream_t s);
+size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D);
+int sf_shell_fp64_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax, const WorkItem* d_items,
+                         int n_items, int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s);
+int sf_shell_mixed_launch(const VtxDev* d_v, int mdi, int mdk, const WorkItem* d_items, int n_items,
+                          int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s);
+int sf_reduce_launch(const VtxDev* d_v, int vtx, int ntiles, const WorkItem* d_items, int item0, int nchunk,
+                     const double* d_part, double* A, cudaStream_t s);
+int sf_bitmap_launch(const int64_t* d_list, int64_t n, int64_t nshell, uint32_t* d_bm, cudaStream_t s);
+int sf_adjoint_run(sf_tables* t, const double* const psi[5], double* a_out, double* const grad_psi[5],
+                   double* const grad_B[4], cudaStream_t s);
+
+// ----------------------------------------------------------------------------------------------
+// errors
+// ----------------------------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+int sf_set_error(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+extern "C" const char* sf_last_error(void) { return g_err; }
+extern "C" const char* sf_version(void) { return "sf_eprl 0.1 (sm_103a)"; }
+
+// ----------------------------------------------------------------------------------------------
+// host-side tables object
+// ----------------------------------------------------------------------------------------------
+struct Table6j {
+    std::vector<SlotDesc> slots;
+    SlotDesc* d_slots = nullptr;
+    int64_t n = 0;
+    double* d_vals = nullptr;
+};
+
+struct VertexHost {
+    sf_vertex v;
+    int D = 0;
+    int32_t ilo[5], di[5];
+    int64_t nshell = 0;
+    Table6j S[5];
+    int64_t ntrip = 0;
+    int32_t dkmax[4];
+    std::vector<int32_t> klo[4];
+    int32_t* d_klo[4] = {nullptr, nullptr, nullptr, nullptr};
+    double* d_B[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool boosters_ready = false;
+    double2* d_dtab[10] = {nullptr};
+    int32_t nl[10];
+    int64_t ngroups = 0;
+    int mk3u = 1;            // largest union over l23 of the k3 ranges, over (l34, l35)
+};
+
+struct sf_tables {
+    int device = 0;
+    int num_sms = 0;
+    std::vector<VertexHost> vs;
+    VtxDev* d_vtx = nullptr;
+    dd* d_fact = nullptr;
+    int* d_status = nullptr;
+    // rule
+    bool have_rule = false;
+    sf_quad_rule rule{};
+    int nnodes = 0;
+    double *d_gl = nullptr, *d_x = nullptr, *d_w = nullptr, *d_r = nullptr, *d_W = nullptr;
+    double *d_Aj = nullptr, *d_Cj = nullptr;   // boundary-side 3j scratch (largest edge)
+    // amplitude scratch (grown on demand)
+    void* d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    std::vector<void*> owned;
+};
+
+static int dev_alloc(sf_tables* t, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return sf_set_error(SF_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    t->owned.push_back(*p);
+    return SF_OK;
+}
+
+#define SF_TRY(x) do { int r_ = (x); if (r_ != SF_OK) return r_; } while (0)
+
+// ----------------------------------------------------------------------------------------------
+// argument checks and ranges
+// ----------------------------------------------------------------------------------------------
+static int check_vertex(const sf_vertex* v) {
+    if (!v) return sf_set_error(SF_ERR_ARG, "null vertex");
+    for (int f = 0; f < 10; f++)
+        if (v->two_j[f] < 0 || v->two_j[f] > 60) return sf_set_error(SF_ERR_ARG, "two_j[%d]=%d out of range [0,60]", f, v->two_j[f]);
+    if (!(v->gamma > 0.0) || v->gamma > 1e6) return sf_set_error(SF_ERR_ARG, "gamma must be positive and finite");
+    if (v->dl < 0) return sf_set_error(SF_ERR_ARG, "dl must be >= 0");
+    if (v->dl > SF_MAX_DL) return sf_set_error(SF_ERR_LIMIT, "dl=%d beyond the compiled limit %d", v->dl, SF_MAX_DL);
+    return SF_OK;
+}
+
+static void ranges_of(const sf_vertex* v, int32_t lo[5], int32_t n[5]) {
+    const int32_t* j = v->two_j;
+    sf_pair_range(j[F12], j[F13], j[F14], j[F15], &lo[0], &n[0]);
+    sf_pair_range(j[F23], j[F24], j[F25], j[F12], &lo[1], &n[1]);
+    sf_pair_range(j[F34], j[F35], j[F13], j[F23], &lo[2], &n[2]);
+    sf_pair_range(j[F45], j[F14], j[F24], j[F34], &lo[3], &n[3]);
+    sf_pair_range(j[F15], j[F25], j[F35], j[F45], &lo[4], &n[4]);
+}
+
+extern "C" int sf_intertwiner_ranges(const sf_vertex* v, int32_t two_lo[5], int32_t dim[5]) {
+    SF_TRY(check_vertex(v));
+    if (!two_lo || !dim) return sf_set_error(SF_ERR_ARG, "null output");
+    ranges_of(v, two_lo, dim);
+    for (int e = 0; e < 5; e++)
+        if (dim[e] == 0) return sf_set_error(SF_ERR_EMPTY, "intertwiner range of edge %d is empty", e + 1);
+    return SF_OK;
+}
+
+extern "C" int64_t sf_num_shells(const sf_vertex* v) {
+    int r = check_vertex(v);
+    if (r != SF_OK) return r;
+    int64_t D = v->dl + 1;
+    return D * D * D * D * D * D;
+}
+
+// union over parameter values of pair ranges -> (lo, n)
+struct Rng { int lo, n; };
+static inline void rng_union(Rng& u, int lo, int n) {
+    if (n == 0) return;
+    if (u.n == 0) { u.lo = lo; u.n = n; return; }
+    int hi = std::max(u.lo + 2 * (u.n - 1), lo + 2 * (n - 1));
+    u.lo = std::min(u.lo, lo);
+    u.n = (hi - u.lo) / 2 + 1;
+}
+// x box of tri(a, p) & tri(b, q) for a in A, b in B (union), parity consistent or empty
+static Rng x_box(Rng A, int p, Rng B, int q) {
+    Rng r{0, 0};
+    if (A.n == 0 || B.n == 0) return r;
+    if ((A.lo + p + B.lo + q) & 1) return r;
+    auto mind = [](Rng R, int c) {
+        int hi = R.lo + 2 * (R.n - 1);
+        if (c < R.lo) return R.lo - c;
+        if (c > hi) return c - hi;
+        return (c + R.lo) & 1;
+    };
+    int lo = std::max(mind(A, p), mind(B, q));
+    int hi = std::min(A.lo + 2 * (A.n - 1) + p, B.lo + 2 * (B.n - 1) + q);
+    if (lo > hi) return r;
+    r.lo = lo;
+    r.n = (hi - lo) / 2 + 1;
+    return r;
+}
+
+static void plan_6j(VertexHost& h) {
+    const int32_t* j = h.v.two_j;
+    const int D = h.D;
+    auto L = [&](int f, int d) { return j[f] + 2 * d; };
+    auto pr = [](int a, int b, int c, int d) { Rng r; sf_pair_range(a, b, c, d, &r.lo, &r.n); return r; };
+    Rng I1{h.ilo[0], h.di[0]};
+    auto add_slot = [](Table6j& T, Rng a, Rng b, Rng x) {
+        SlotDesc s{};
+        s.off = T.n;
+        if (a.n == 0 || b.n == 0 || x.n == 0) { a.n = b.n = x.n = 0; }
+        s.alo = a.lo; s.blo = b.lo; s.xlo = x.lo; s.na = a.n; s.nb = b.n; s.nx = x.n;
+        T.slots.push_back(s);
+        T.n += (int64_t)a.n * b.n * x.n;
+    };
+    for (int k = 0; k < 5; k++) { h.S[k].slots.clear(); h.S[k].n = 0; }
+    // S1[l25][i1, k5, x] = {i1 l25 x; k5 j14 j15}
+    for (int d25 = 0; d25 < D; d25++) {
+        Rng K5{0, 0};
+        for (int d35 = 0; d35 < D; d35++)
+            for (int d45 = 0; d45 < D; d45++) { Rng r = pr(j[F15], L(F25, d25), L(F35, d35), L(F45, d45)); rng_union(K5, r.lo, r.n); }
+        add_slot(h.S[0], I1, K5, x_box(I1, L(F25, d25), K5, j[F14]));
+    }
+    // S2[l35, l45][k5, k4, x] = {j14 k5 x; l35 k4 l45}
+    for (int d35 = 0; d35 < D; d35++)
+        for (int d45 = 0; d45 < D; d45++) {
+            Rng K5{0, 0}, K4{0, 0};
+            for (int d25 = 0; d25 < D; d25++) { Rng r = pr(j[F15], L(F25, d25), L(F35, d35), L(F45, d45)); rng_union(K5, r.lo, r.n); }
+            for (int d24 = 0; d24 < D; d24++)
+                for (int d34 = 0; d34 < D; d34++) { Rng r = pr(L(F45, d45), j[F14], L(F24, d24), L(F34, d34)); rng_union(K4, r.lo, r.n); }
+            add_slot(h.S[1], K5, K4, x_box(K5, j[F14], K4, L(F35, d35)));
+        }
+    // S3[l24, l34, l35][k4, k3, x] = {k4 l35 x; k3 l24 l34}
+    for (int d24 = 0; d24 < D; d24++)
+        for (int d34 = 0; d34 < D; d34++)
+            for (int d35 = 0; d35 < D; d35++) {
+                Rng K4{0, 0}, K3{0, 0};
+                for (int d45 = 0; d45 < D; d45++) { Rng r = pr(L(F45, d45), j[F14], L(F24, d24), L(F34, d34)); rng_union(K4, r.lo, r.n); }
+                for (int d23 = 0; d23 < D; d23++) { Rng r = pr(L(F34, d34), L(F35, d35), j[F13], L(F23, d23)); rng_union(K3, r.lo, r.n); }
+                add_slot(h.S[2], K4, K3, x_box(K4, L(F35, d35), K3, L(F24, d24)));
+            }
+    // S4[l23, l24][k3, k2, x] = {l24 k3 x; j13 k2 l23}
+    for (int d23 = 0; d23 < D; d23++)
+        for (int d24 = 0; d24 < D; d24++) {
+            Rng K3{0, 0}, K2{0, 0};
+            for (int d34 = 0; d34 < D; d34++)
+                for (int d35 = 0; d35 < D; d35++) { Rng r = pr(L(F34, d34), L(F35, d35), j[F13], L(F23, d23)); rng_union(K3, r.lo, r.n); }
+            for (int d25 = 0; d25 < D; d25++) { Rng r = pr(L(F23, d23), L(F24, d24), L(F25, d25), j[F12]); rng_union(K2, r.lo, r.n); }
+            add_slot(h.S[3], K3, K2, x_box(K3, L(F24, d24), K2, j[F13]));
+        }
+    // S5[l25][k2, i1, x] = {k2 j13 x; i1 l25 j12}
+    for (int d25 = 0; d25 < D; d25++) {
+        Rng K2{0, 0};
+        for (int d23 = 0; d23 < D; d23++)
+            for (int d24 = 0; d24 < D; d24++) { Rng r = pr(L(F23, d23), L(F24, d24), L(F25, d25), j[F12]); rng_union(K2, r.lo, r.n); }
+        add_slot(h.S[4], K2, I1, x_box(K2, j[F13], I1, L(F25, d25)));
+    }
+}
+
+static void plan_boosters(VertexHost& h) {
+    const int32_t* j = h.v.two_j;
+    const int D = h.D;
+    h.ntrip = (int64_t)D * D * D;
+    static const int faces[4][4] = {{F23, F24, F25, F12}, {F34, F35, F13, F23}, {F45, F14, F24, F34}, {F15, F25, F35, F45}};
+    static const int slotof[4][4] = {{0, 1, 2, -1}, {0, 1, -1, 2}, {0, -1, 1, 2}, {-1, 0, 1, 2}};
+    for (int e = 0; e < 4; e++) {
+        h.klo[e].assign(h.ntrip, 0);
+        int dk = 1;
+        for (int t = 0; t < h.ntrip; t++) {
+            int off[3] = {t / (D * D), (t / D) % D, t % D};
+            int tl[4];
+            for (int a = 0; a < 4; a++) tl[a] = j[faces[e][a]] + (slotof[e][a] < 0 ? 0 : 2 * off[slotof[e][a]]);
+            int lo, n;
+            sf_pair_range(tl[0], tl[1], tl[2], tl[3], &lo, &n);
+            h.klo[e][t] = n ? lo : 0;
+            dk = std::max(dk, n);
+        }
+        h.dkmax[e] = dk;
+    }
+    for (int f = 0; f < 10; f++) h.nl[f] = (f <= F15) ? 1 : D;
+    h.mk3u = 1;
+    for (int d34 = 0; d34 < D; d34++)
+        for (int d35 = 0; d35 < D; d35++) {
+            int lo = 1 << 30, hi = -1;
+            for (int d23 = 0; d23 < D; d23++) {
+                int a, n;
+                sf_pair_range(j[F34] + 2 * d34, j[F35] + 2 * d35, j[F13], j[F23] + 2 * d23, &a, &n);
+                if (n) { lo = std::min(lo, a); hi = std::max(hi, a + 2 * (n - 1)); }
+            }
+            if (hi >= lo) h.mk3u = std::max(h.mk3u, (hi - lo) / 2 + 1);
+        }
+}
+
+static int upload_vtxdev(sf_tables* t) {
+    std::vector<VtxDev> hv(t->vs.size());
+    for (size_t i = 0; i < t->vs.size(); i++) {
+        VertexHost& h = t->vs[i];
+        VtxDev& d = hv[i];
+        memset(&d, 0, sizeof(d));
+        for (int f = 0; f < 10; f++) d.tj[f] = h.v.two_j[f];
+        d.gamma = h.v.gamma;
+        d.dl = h.v.dl;
+        d.D = h.D;
+        for (int e = 0; e < 5; e++) { d.ilo[e] = h.ilo[e]; d.di[e] = h.di[e]; }
+        d.nshell = h.nshell;
+        for (int k = 0; k < 5; k++) { d.S[k] = h.S[k].d_vals; d.slot[k] = h.S[k].d_slots; }
+        for (int e = 0; e < 4; e++) { d.B[e] = h.d_B[e]; d.klo[e] = h.d_klo[e]; d.dkmax[e] = h.dkmax[e]; }
+        d.ntrip = h.ntrip;
+        for (int f = 0; f < 10; f++) { d.dtab[f] = h.d_dtab[f]; d.nl[f] = h.nl[f]; }
+    }
+    SF_CUDA_TRY(cudaMemcpy(t->d_vtx, hv.data(), hv.size() * sizeof(VtxDev), cudaMemcpyHostToDevice));
+    return SF_OK;
+}
+
+static int check_status(sf_tables* t, cudaStream_t s, const char* what) {
+    int st = 0;
+    SF_CUDA_TRY(cudaMemcpyAsync(&st, t->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SF_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st == SF_DEV_OK) return SF_OK;
+    if (st == SF_DEV_BIGINT_OVERFLOW) return sf_set_error(SF_ERR_LIMIT, "%s: exact Racah sum overflowed its integer width", what);
+    if (st == SF_DEV_NONREAL_BOOSTER) return sf_set_error(SF_ERR_NUMERIC, "%s: a booster has a non-negligible imaginary part", what);
+    if (st == SF_DEV_TIMEOUT) return sf_set_error(SF_ERR_TIMEOUT, "%s: a bounded device wait gave up", what);
+    return sf_set_error(SF_ERR_NUMERIC, "%s: device status %d", what, st);
+}
+
+extern "C" void sf_tables_free(sf_tables* t) {
+    if (!t) return;
+    for (void* p : t->owned) cudaFree(p);
+    if (t->d_scratch) cudaFree(t->d_scratch);
+    delete t;
+}
+
+extern "C" int sf_6j_table(const sf_vertex* v, int32_t n, sf_tables** out, cudaStream_t stream) {
+    if (!out) return sf_set_error(SF_ERR_ARG, "null output pointer");
+    *out = nullptr;
+    if (!v || n <= 0) return sf_set_error(SF_ERR_ARG, "need at least one vertex");
+    for (int i = 0; i < n; i++) {
+        SF_TRY(check_vertex(&v[i]));
+        int32_t lo[5], dim[5];
+        ranges_of(&v[i], lo, dim);
+        for (int e = 0; e < 5; e++)
+            if (dim[e] == 0) return sf_set_error(SF_ERR_EMPTY, "vertex %d: intertwiner range of edge %d is empty", i, e + 1);
+        // integer Racah arguments and factorials stay within the compiled widths
+        int maxl = 0;
+        for (int f = 0; f < 10; f++) maxl = std::max(maxl, v[i].two_j[f] + (f > F15 ? 2 * v[i].dl : 0));
+        if (2 * maxl + 4 * maxl > 2 * SF_FACT_MAX - 4)
+            return sf_set_error(SF_ERR_LIMIT, "vertex %d: spins too large for the exact symbol kernels", i);
+    }
+    sf_tables* t = new sf_tables();
+    int rc = SF_OK;
+    do {
+        if (cudaGetDevice(&t->device) != cudaSuccess) { rc = sf_set_error(SF_ERR_CUDA, "no CUDA device"); break; }
+        cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, t->device);
+        t->vs.resize(n);
+        for (int i = 0; i < n && rc == SF_OK; i++) {
+            VertexHost& h = t->vs[i];
+            h.v = v[i];
+            h.D = v[i].dl + 1;
+            ranges_of(&v[i], h.ilo, h.di);
+            h.nshell = (int64_t)h.D * h.D * h.D * h.D * h.D * h.D;
+            h.ngroups = (int64_t)h.D * h.D * h.D;
+            plan_6j(h);
+            plan_boosters(h);
+            for (int k = 0; k < 5 && rc == SF_OK; k++) {
+                rc = dev_alloc(t, (void**)&h.S[k].d_slots, h.S[k].slots.size() * sizeof(SlotDesc));
+                if (rc == SF_OK) rc = dev_alloc(t, (void**)&h.S[k].d_vals, h.S[k].n * sizeof(double));
+                if (rc == SF_OK && cudaMemcpy(h.S[k].d_slots, h.S[k].slots.data(), h.S[k].slots.size() * sizeof(SlotDesc),
+                                              cudaMemcpyHostToDevice) != cudaSuccess)
+                    rc = sf_set_error(SF_ERR_CUDA, "slot upload failed");
+            }
+            for (int e = 0; e < 4 && rc == SF_OK; e++) {
+                rc = dev_alloc(t, (void**)&h.d_klo[e], h.ntrip * sizeof(int32_t));
+                if (rc == SF_OK) rc = dev_alloc(t, (void**)&h.d_B[e], (size_t)h.ntrip * h.di[e + 1] * h.dkmax[e] * sizeof(double));
+                if (rc == SF_OK && cudaMemcpy(h.d_klo[e], h.klo[e].data(), h.ntrip * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+                    rc = sf_set_error(SF_ERR_CUDA, "klo upload failed");
+                if (rc == SF_OK && cudaMemsetAsync(h.d_B[e], 0, (size_t)h.ntrip * h.di[e + 1] * h.dkmax[e] * sizeof(double), stream) != cudaSuccess)
+                    rc = sf_set_error(SF_ERR_CUDA, "booster clear failed");
+            }
+        }
+        if (rc != SF_OK) break;
+        if ((rc = dev_alloc(t, (void**)&t->d_vtx, n * sizeof(VtxDev))) != SF_OK) break;
+        if ((rc = dev_alloc(t, (void**)&t->d_fact, (SF_FACT_MAX + 1) * sizeof(dd))) != SF_OK) break;
+        if ((rc = dev_alloc(t, (void**)&t->d_status, sizeof(int))) != SF_OK) break;
+        if (cudaMemsetAsync(t->d_status, 0, sizeof(int), stream) != cudaSuccess) { rc = sf_set_error(SF_ERR_CUDA, "memset"); break; }
+        if ((rc = upload_vtxdev(t)) != SF_OK) break;
+        if ((rc = sf_fact_table_build(t->d_fact, stream)) != SF_OK) break;
+        for (int i = 0; i < n && rc == SF_OK; i++) {
+            VertexHost& h = t->vs[i];
+            for (int k = 0; k < 5 && rc == SF_OK; k++)
+                rc = sf_sixj_table_build(k + 1, t->d_vtx + i, h.S[k].d_slots, (int)h.S[k].slots.size(), h.S[k].n,
+                                         h.S[k].d_vals, t->d_fact, t->d_status, t->num_sms, stream);
+        }
+        if (rc != SF_OK) break;
+        rc = check_status(t, stream, "sf_6j_table");
+    } while (0);
+    if (rc != SF_OK) { sf_tables_free(t); return rc; }
+    *out = t;
+    return SF_OK;
+}
+
+extern "C" int sf_boosters(sf_tables* t, const sf_quad_rule* q, cudaStream_t stream) {
+    if (!t || !q) return sf_set_error(SF_ERR_ARG, "null argument");
+    if (q->n_panels < 1 || q->order < 2 || q->order > 1024 || !(q->r_max > 0.0) || q->r_max > 700.0)
+        return sf_set_error(SF_ERR_ARG, "bad quadrature rule");
+    const int nnodes = q->n_panels * q->order;
+    if (!t->have_rule || t->rule.n_panels != q->n_panels || t->rule.order != q->order || t->rule.r_max != q->r_max) {
+        if (!t->d_gl) SF_TRY(dev_alloc(t, (void**)&t->d_gl, 3 * 16864 * sizeof(double)));
+        if (nnodes > t->nnodes) {
+            SF_TRY(dev_alloc(t, (void**)&t->d_x, nnodes * sizeof(double)));
+            SF_TRY(dev_alloc(t, (void**)&t->d_w, nnodes * sizeof(double)));
+            SF_TRY(dev_alloc(t, (void**)&t->d_r, nnodes * sizeof(double)));
+            SF_TRY(dev_alloc(t, (void**)&t->d_W, nnodes * sizeof(double)));
+        }
+        SF_TRY(sf_rule_build(q, t->d_gl, t->d_x, t->d_w, t->d_r, t->d_W, stream));
+        // d-tables are sized by the node count: reallocate for a different rule
+        for (auto& h : t->vs)
+            for (int f = 0; f < 10; f++) h.d_dtab[f] = nullptr;
+        t->rule = *q;
+        t->nnodes = nnodes;
+        t->have_rule = true;
+    }
+    size_t aj = 16;
+    for (auto& h : t->vs) {
+        for (int f = 0; f < 10; f++) {
+            if (!h.d_dtab[f]) SF_TRY(dev_alloc(t, (void**)&h.d_dtab[f], (size_t)h.nl[f] * (h.v.two_j[f] + 1) * nnodes * sizeof(double2)));
+        }
+        for (int e = 0; e < 4; e++) {
+            static const int faces[4][4] = {{F23, F24, F25, F12}, {F34, F35, F13, F23}, {F45, F14, F24, F34}, {F15, F25, F35, F45}};
+            size_t a = (size_t)h.di[e + 1] * (h.v.two_j[faces[e][0]] + 1) * (h.v.two_j[faces[e][1]] + 1);
+            size_t c = (size_t)h.di[e + 1] * (h.v.two_j[faces[e][2]] + 1) * (h.v.two_j[faces[e][3]] + 1);
+            aj = std::max(aj, std::max(a, c));
+            for (int a4 = 0; a4 < 4; a4++)
+                if (h.v.two_j[faces[e][a4]] > 16)
+                    return sf_set_error(SF_ERR_LIMIT, "booster kernel supports boundary spins up to 8");
+        }
+    }
+    SF_TRY(dev_alloc(t, (void**)&t->d_Aj, aj * sizeof(double)));
+    SF_TRY(dev_alloc(t, (void**)&t->d_Cj, aj * sizeof(double)));
+    SF_TRY(upload_vtxdev(t));
+    SF_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, sizeof(int), stream));
+    for (size_t i = 0; i < t->vs.size(); i++) {
+        VertexHost& h = t->vs[i];
+        for (int f = 0; f < 10; f++)
+            SF_TRY(sf_dtable_build(h.v.two_j[f], h.v.gamma, h.nl[f], nnodes, t->d_r, t->d_gl, h.d_dtab[f], stream));
+        for (int e = 0; e < 4; e++) {
+            static const int faces[4][4] = {{F23, F24, F25, F12}, {F34, F35, F13, F23}, {F45, F14, F24, F34}, {F15, F25, F35, F45}};
+            const int32_t* j = h.v.two_j;
+            size_t smem = sf_booster_smem(j[faces[e][0]], j[faces[e][1]], j[faces[e][2]], j[faces[e][3]], h.dkmax[e]);
+            SF_TRY(sf_booster_build(t->d_vtx + i, e + 2, (int)h.ntrip, smem, t->d_W, nnodes, t->d_fact, t->d_Aj, t->d_Cj,
+                                    h.d_B[e], t->d_status, stream));
+        }
+        h.boosters_ready = true;
+    }
+    return check_status(t, stream, "sf_boosters");
+}
+
+static int check_edge(const sf_tables* t, int32_t vertex, int32_t edge) {
+    if (!t) return sf_set_error(SF_ERR_ARG, "null tables");
+    if (vertex < 0 || vertex >= (int)t->vs.size()) return sf_set_error(SF_ERR_ARG, "vertex index out of range");
+    if (edge < 2 || edge > 5) return sf_set_error(SF_ERR_ARG, "edge must be 2..5");
+    return SF_OK;
+}
+
+extern "C" int sf_booster_shape(const sf_tables* t, int32_t vertex, int32_t edge, int64_t shape[3]) {
+    SF_TRY(check_edge(t, vertex, edge));
+    const VertexHost& h = t->vs[vertex];
+    shape[0] = h.ntrip;
+    shape[1] = h.di[edge - 1];
+    shape[2] = h.dkmax[edge - 2];
+    return SF_OK;
+}
+
+extern "C" int sf_boosters_upload(sf_tables* t, int32_t vertex, int32_t edge, const double* B, cudaStream_t stream) {
+    SF_TRY(check_edge(t, vertex, edge));
+    if (!B) return sf_set_error(SF_ERR_ARG, "null booster pointer");
+    VertexHost& h = t->vs[vertex];
+    size_t bytes = (size_t)h.ntrip * h.di[edge - 1] * h.dkmax[edge - 2] * sizeof(double);
+    SF_CUDA_TRY(cudaMemcpyAsync(h.d_B[edge - 2], B, bytes, cudaMemcpyDefault, stream));
+    SF_CUDA_TRY(cudaStreamSynchronize(stream));
+    h.boosters_ready = true;   // edges never uploaded keep their last (initially zero) contents
+    return SF_OK;
+}
+
+extern "C" int sf_boosters_download(const sf_tables* t, int32_t vertex, int32_t edge, double* B, cudaStream_t stream) {
+    SF_TRY(check_edge(t, vertex, edge));
+    if (!B) return sf_set_error(SF_ERR_ARG, "null booster pointer");
+    const VertexHost& h = t->vs[vertex];
+    size_t bytes = (size_t)h.ntrip * h.di[edge - 1] * h.dkmax[edge - 2] * sizeof(double);
+    SF_CUDA_TRY(cudaMemcpyAsync(B, h.d_B[edge - 2], bytes, cudaMemcpyDefault, stream));
+    SF_CUDA_TRY(cudaStreamSynchronize(stream));
+    return SF_OK;
+}
+
+// ----------------------------------------------------------------------------------------------
+// vertex amplitude
+// ----------------------------------------------------------------------------------------------
+static int grow_scratch(sf_tables* t, size_t bytes) {
+    if (bytes <= t->scratch_bytes) return SF_OK;
+    if (t->d_scratch) { cudaFree(t->d_scratch); t->d_scratch = nullptr; t->scratch_bytes = 0; }
+    cudaError_t e = cudaMalloc(&t->d_scratch, bytes);
+    if (e != cudaSuccess) { t->d_scratch = nullptr; return sf_set_error(SF_ERR_OOM, "scratch allocation of %zu bytes failed", bytes); }
+    t->scratch_bytes = bytes;
+    return SF_OK;
+}
+
+static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t shell_begin, int64_t shell_end,
+                                   const int64_t* shell_list, int64_t n_list, double* const* A_out, cudaStream_t stream) {
+    if (!t || !A_out) return sf_set_error(SF_ERR_ARG, "null argument");
+    if (precision != SF_FP64 && precision != SF_MIXED) return sf_set_error(SF_ERR_ARG, "unknown precision");
+    if (shell_list && t->vs.size() != 1) return sf_set_error(SF_ERR_ARG, "a shell list needs single-vertex tables");
+    if (shell_list && n_list < 0) return sf_set_error(SF_ERR_ARG, "negative list length");
+    if (!shell_list && shell_begin < 0) return sf_set_error(SF_ERR_ARG, "negative shell_begin");
+    for (size_t i = 0; i < t->vs.size(); i++) {
+        if (!t->vs[i].boosters_ready) return sf_set_error(SF_ERR_ARG, "boosters of vertex %zu were never computed or uploaded", i);
+        if (!A_out[i]) return sf_set_error(SF_ERR_ARG, "null output for vertex %zu", i);
+    }
+    // work items: per vertex, tiles (i1, i2) x chunks of the (l25, l35, l45) groups
+    const int nv = (int)t->vs.size();
+    int64_t tiles_total = 0;
+    for (auto& h : t->vs) tiles_total += (int64_t)h.di[0] * h.di[1];
+    const int64_t target = (int64_t)t->num_sms * 6;
+    std::vector<WorkItem> items;
+    std::vector<int> item0(nv), nchunk(nv);
+    int64_t part_total = 0;
+    int mdi = 1, mdk = 1, mk3u = 1, Dmax = 1;
+    for (int i = 0; i < nv; i++) {
+        VertexHost& h = t->vs[i];
+        int64_t ntile = (int64_t)h.di[0] * h.di[1];
+        int64_t want = std::max<int64_t>(1, (target + tiles_total - 1) / std::max<int64_t>(1, tiles_total));
+        int C = (int)std::min<int64_t>(h.ngroups, want);
+        item0[i] = (int)items.size();
+        nchunk[i] = C;
+        int64_t per = (int64_t)h.di[2] * h.di[3] * h.di[4];
+        for (int64_t tile = 0; tile < ntile; tile++) {
+            for (int c = 0; c < C; c++) {
+                WorkItem w{};
+                w.vtx = i;
+                w.i1 = (int)(tile / h.di[1]);
+                w.i2 = (int)(tile % h.di[1]);
+                w.g0 = (int)(h.ngroups * c / C);
+                w.g1 = (int)(h.ngroups * (c + 1) / C);
+                w.part_off = part_total;
+                part_total += per;
+                items.push_back(w);
+            }
+        }
+        for (int e = 2; e < 5; e++) mdi = std::max(mdi, (int)h.di[e]);
+        for (int e = 0; e < 4; e++) mdk = std::max(mdk, (int)h.dkmax[e]);
+        mk3u = std::max(mk3u, h.mk3u);
+        Dmax = std::max(Dmax, h.D);
+    }
+    if (items.size() > (size_t)0x7FFFFFFF) return sf_set_error(SF_ERR_LIMIT, "too many work items");
+    // x chunk: keep the shared-memory footprint under ~200 KB
+    int xc = 16;
+    while (xc > 1 && sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax) * sizeof(double) > 200 * 1024) xc--;
+    if (sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax) * sizeof(double) > 200 * 1024)
+        return sf_set_error(SF_ERR_LIMIT, "intertwiner dimensions too large for the shell kernel");
+    // scratch: items | counter | bitmap | partials
+    int64_t nshell0 = t->vs[0].nshell;
+    size_t o_items = 0;
+    size_t o_counter = align256(o_items + items.size() * sizeof(WorkItem));
+    size_t o_bitmap = align256(o_counter + sizeof(int));
+    size_t bm_bytes = shell_list ? (size_t)((nshell0 + 31) / 32) * sizeof(uint32_t) : 0;
+    size_t o_list = align256(o_bitmap + bm_bytes);
+    size_t list_bytes = shell_list ? (size_t)std::max<int64_t>(1, n_list) * sizeof(int64_t) : 0;
+    size_t o_part = align256(o_list + list_bytes);
+    size_t total = align256(o_part + (size_t)part_total * sizeof(double));
+    SF_TRY(grow_scratch(t, total));
+    char* base = (char*)t->d_scratch;
+    WorkItem* d_items = (WorkItem*)(base + o_items);
+    int* d_counter = (int*)(base + o_counter);
+    double* d_part = (double*)(base + o_part);
+    SF_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, stream));
+    ShellFilter filt{};
+    filt.begin = shell_begin;
+    filt.end = shell_end;
+    filt.bitmap = nullptr;
+    if (shell_list) {
+        uint32_t* d_bm = (uint32_t*)(base + o_bitmap);
+        int64_t* d_list = (int64_t*)(base + o_list);
+        if (n_list > 0) SF_CUDA_TRY(cudaMemcpyAsync(d_list, shell_list, n_list * sizeof(int64_t), cudaMemcpyDefault, stream));
+        SF_TRY(sf_bitmap_launch(d_list, n_list, nshell0, d_bm, stream));
+        filt.bitmap = d_bm;
+    }
+    SF_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, sizeof(int), stream));
+    if (precision == SF_FP64) {
+        SF_TRY(sf_shell_fp64_launch(t->d_vtx, mdi, mdk, mk3u, xc, Dmax, d_items, (int)items.size(), d_counter, d_part,
+                                    filt, t->num_sms, stream));
+    } else {
+        SF_TRY(sf_shell_mixed_launch(t->d_vtx, mdi, mdk, d_items, (int)items.size(), d_counter, d_part, filt,
+                                     t->num_sms, stream));
+    }
+    for (int i = 0; i < nv; i++) {
+        VertexHost& h = t->vs[i];
+        SF_TRY(sf_reduce_launch(t->d_vtx, i, h.di[0] * h.di[1], d_items, item0[i], nchunk[i], d_part, A_out[i], stream));
+    }
+    return check_status(t, stream, "sf_vertex_amplitude");
+}
+
+extern "C" int sf_vertex_adjoint(sf_tables* t, const double* const psi[5], double* a_out, double* const grad_psi[5],
+                                 double* const grad_B[4], cudaStream_t stream) {
+    if (!t || !psi || !a_out) return sf_set_error(SF_ERR_ARG, "null argument");
+    if (t->vs.size() != 1) return sf_set_error(SF_ERR_ARG, "the adjoint needs single-vertex tables");
+    if (!t->vs[0].boosters_ready) return sf_set_error(SF_ERR_ARG, "boosters were never computed or uploaded");
+    for (int e = 0; e < 5; e++) if (!psi[e]) return sf_set_error(SF_ERR_ARG, "null boundary vector %d", e + 1);
+    return sf_adjoint_run(t, psi, a_out, grad_psi, grad_B, stream);
+}
+
+// ----------------------------------------------------------------------------------------------
+// table export
+// ----------------------------------------------------------------------------------------------
+static int table_ptr(const sf_tables* t, int32_t vertex, int32_t kind, int32_t index, const void** p, int64_t* bytes,
+                     std::vector<int64_t>* host_slots) {
+    if (!t) return sf_set_error(SF_ERR_ARG, "null tables");
+    if (vertex < 0 || vertex >= (int)t->vs.size()) return sf_set_error(SF_ERR_ARG, "vertex index out of range");
+    const VertexHost& h = t->vs[vertex];
+    switch (kind) {
+        case SF_TAB_6J:
+            if (index < 1 || index > 5) return sf_set_error(SF_ERR_ARG, "6j table index must be 1..5");
+            *p = h.S[index - 1].d_vals;
+            *bytes = h.S[index - 1].n * (int64_t)sizeof(double);
+            return SF_OK;
+        case SF_TAB_6J_SLOTS: {
+            if (index < 1 || index > 5) return sf_set_error(SF_ERR_ARG, "6j table index must be 1..5");
+            const auto& sl = h.S[index - 1].slots;
+            *bytes = (int64_t)sl.size() * 8 * (int64_t)sizeof(int64_t);
+            if (host_slots) {
+                host_slots->resize(sl.size() * 8);
+                for (size_t i = 0; i < sl.size(); i++) {
+                    int64_t* o = host_slots->data() + 8 * i;
+                    o[0] = sl[i].off; o[1] = sl[i].alo; o[2] = sl[i].blo; o[3] = sl[i].xlo;
+                    o[4] = sl[i].na; o[5] = sl[i].nb; o[6] = sl[i].nx; o[7] = 0;
+                }
+            }
+            *p = nullptr;
+            return SF_OK;
+        }
+        case SF_TAB_D:
+            if (index < 0 || index > 9) return sf_set_error(SF_ERR_ARG, "face index must be 0..9");
+            if (!h.d_dtab[index]) return sf_set_error(SF_ERR_ARG, "d-tables not computed");
+            *p = h.d_dtab[index];
+            *bytes = (int64_t)h.nl[index] * (h.v.two_j[index] + 1) * t->nnodes * (int64_t)sizeof(double2);
+            return SF_OK;
+        case SF_TAB_NODES:
+            if (!t->have_rule) return sf_set_error(SF_ERR_ARG, "rule not computed");
+            if (index < 0 || index > 2) return sf_set_error(SF_ERR_ARG, "node table index must be 0..2");
+            *p = index == 0 ? t->d_x : index == 1 ? t->d_w : t->d_r;
+            *bytes = t->nnodes * (int64_t)sizeof(double);
+            return SF_OK;
+        default:
+            return sf_set_error(SF_ERR_ARG, "unknown table kind");
+    }
+}
+
+extern "C" int64_t sf_table_size(const sf_tables* t, int32_t vertex, int32_t kind, int32_t index) {
+    const void* p;
+    int64_t b = 0;
+    int r = table_ptr(t, vertex, kind, index, &p, &b, nullptr);
+    return r == SF_OK ? b : r;
+}
+
+extern "C" int sf_table_copy(const sf_tables* t, int32_t vertex, int32_t kind, int32_t index, void* dst, int64_t n_bytes,
+                             cudaStream_t stream) {
+    const void* p;
+    int64_t b = 0;
+    std::vector<int64_t> hs;
+    SF_TRY(table_ptr(t, vertex, kind, index, &p, &b, &hs));
+    if (!dst || n_bytes < b) return sf_set_error(SF_ERR_ARG, "destination too small (%lld < %lld bytes)", (long long)n_bytes, (long long)b);
+    if (kind == SF_TAB_6J_SLOTS) {
+        SF_CUDA_TRY(cudaMemcpyAsync(dst, hs.data(), b, cudaMemcpyDefault, stream));
+    } else {
+        SF_CUDA_TRY(cudaMemcpyAsync(dst, p, b, cudaMemcpyDefault, stream));
+    }
+    SF_CUDA_TRY(cudaStreamSynchronize(stream));
+    return SF_OK;
+}

@@ -1,0 +1,425 @@
+// Boosters B4^gamma (Sec. 2 eq. booster; Sec. 3 "Booster coefficients"):
+//   1. Gauss-Legendre nodes (Newton iteration in the angle variable, FP64);
+//   2. the rapidity rule: panels in x = e^-r with |I_k| = k |I_1|, `order` nodes per panel;
+//   3. d-tables d^{rho,k}_{k l m}(r_n) for every face, l and m, from the compact-picture integral
+//        d = i^(k-l) Phi_l sqrt((2k+1)(2l+1)) r/(2 sinh r) int_{-1}^{1} dxi d^k_{mk}(beta) d^l_{mk}(beta_r) e^{i rho v},
+//      v = r xi = ln u, t = sin^2(beta/2) = (e^v - e^-r)/(2 sinh r), t_r = sin^2(beta_r/2) = (e^r - e^-v)/(2 sinh r),
+//      integrated by Gauss-Legendre in v with an r-dependent node count (no cancellation: the
+//      integrand is bounded), d^l for all l by the three-term recurrence in l;
+//   4. per (edge, virtual-spin triple): I(m) = sum_n W_n prod_a d_a(m_a, r_n) and
+//      B[i][k] = Re sum_m 4jm(j;m)^(i) 4jm(l;m)^(k) I(m).
+#include "sf_racah.cuh"
+
+#define SF_PI 3.14159265358979323846
+
+// ---------------------------------------------------------------------------------------------
+// Gauss-Legendre library: for N = 32q, q = 2..32, arrays (1+xi, 1-xi, w), concatenated.
+// ---------------------------------------------------------------------------------------------
+__host__ __device__ inline int64_t sf_gl_offset(int N) {   // start of size-N rule
+    int q = N / 32;
+    return 32ll * ((int64_t)(q - 1) * q / 2 - 1);            // 32 * sum_{q'=2}^{q-1} q'
+}
+#define SF_GL_TOTAL (32ll * (32ll * 33 / 2 - 1))             // sum_{q=2}^{32} 32 q
+
+__device__ inline void sf_gl_node(int N, int i, double* opx, double* omx, double* w) {
+    // i-th root of P_N, theta in (0, pi), descending x
+    double th = SF_PI * (i + 0.75) / (N + 0.5);
+    double x = cos(th), p0 = 1.0, p1 = x;
+    for (int it = 0; it < 12; it++) {
+        x = cos(th);
+        p0 = 1.0;
+        p1 = x;
+        for (int k = 2; k <= N; k++) {
+            double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        double s = sin(th);
+        double dth = p1 * s / (N * (x * p1 - p0));   // theta-Newton step on P_N(cos theta)
+        th -= dth;
+        if (fabs(dth) < 1e-17) break;
+    }
+    x = cos(th);
+    p0 = 1.0;
+    p1 = x;
+    for (int k = 2; k <= N; k++) {
+        double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+    }
+    double s = sin(th), sh = sin(0.5 * th), ch = cos(0.5 * th);
+    double dp = N * (x * p1 - p0);   // = -(1-x^2) P_N'(x)
+    *opx = 2.0 * ch * ch;
+    *omx = 2.0 * sh * sh;
+    *w = 2.0 * s * s / (dp * dp);
+}
+
+__global__ void k_gl_library(double* gl) {
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= SF_GL_TOTAL) return;
+    int q = 2;
+    while (sf_gl_offset(32 * (q + 1)) <= tid) q++;
+    int N = 32 * q;
+    int i = (int)(tid - sf_gl_offset(N));
+    double a, b, c;
+    sf_gl_node(N, i, &a, &b, &c);
+    gl[tid] = a;
+    gl[SF_GL_TOTAL + tid] = b;
+    gl[2 * SF_GL_TOTAL + tid] = c;
+}
+
+// rapidity rule nodes: x_n, w_n, r_n = -ln x_n, W_n = w_n (1-x^2)^2 / (16 pi x^3)
+__global__ void k_rule_nodes(double r_max, int npan, int order, double* X, double* Wt, double* R, double* Wm) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= npan * order) return;
+    int kk = n / order + 1, i = n % order;
+    double opx, omx, w;
+    sf_gl_node(order, order - 1 - i, &opx, &omx, &w);   // ascending x inside the panel
+    double x0 = exp(-r_max);
+    double Dx = 2.0 * (1.0 - x0) / ((double)npan * (npan + 1));
+    double a = x0 + Dx * 0.5 * kk * (kk - 1);
+    double top = (1.0 - x0) - Dx * 0.5 * kk * (kk + 1);   // 1 - b, exactly 0 for the last panel
+    double h = 0.5 * Dx * kk;
+    double x = a + h * opx;
+    double one_minus_x = top + h * omx;
+    double r = (x < 0.5) ? -log(x) : -log1p(-one_minus_x);
+    double omx2 = one_minus_x * (2.0 - one_minus_x);      // 1 - x^2
+    X[n] = x;
+    Wt[n] = h * w;
+    R[n] = r;
+    Wm[n] = h * w * omx2 * omx2 / (16.0 * SF_PI * x * x * x);
+}
+
+int sf_rule_build(const sf_quad_rule* q, double* d_gl, double* d_x, double* d_w, double* d_r, double* d_W,
+                  cudaStream_t s) {
+    k_gl_library<<<(unsigned)((SF_GL_TOTAL + 255) / 256), 256, 0, s>>>(d_gl);
+    SF_CUDA_TRY(cudaGetLastError());
+    int n = q->n_panels * q->order;
+    k_rule_nodes<<<(n + 127) / 128, 128, 0, s>>>(q->r_max, q->n_panels, q->order, d_x, d_w, d_r, d_W);
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// d-tables
+// ---------------------------------------------------------------------------------------------
+__device__ inline int sf_gl_count(double r, double rho, int tk, int tlmax) {
+    double band = rho + 0.25 * (tlmax + tk) + 1.0;
+    int N = (int)ceil((48.0 + r * band) / 32.0) * 32;
+    return N < 64 ? 64 : (N > 1024 ? 1024 : N);
+}
+
+__device__ inline double ipow_(double b, int e) {
+    double r = 1.0;
+    for (int i = 0; i < e; i++) r *= b;
+    return r;
+}
+
+// grid: x = node blocks, y = m index; one face per launch; l values [il0, il0 + nlc)
+__global__ void __launch_bounds__(128) k_dtable(int tk, double rho, int nl, int nnodes, const double* __restrict__ R,
+                                                const double* __restrict__ gl, double2* __restrict__ out) {
+    const int im = blockIdx.y;
+    const int tm = -tk + 2 * im;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    // recurrence coefficients d^{l+1} = (al cos(b) - gl) d^l - de d^{l-1}, l = k + p
+    __shared__ double s_al[SF_MAX_DL + 1], s_ga[SF_MAX_DL + 1], s_de[SF_MAX_DL + 1];
+    const double k = 0.5 * tk, m = 0.5 * tm;
+    if (threadIdx.x == 0) {
+        for (int p = 0; p < nl; p++) {
+            double l = k + p;
+            if (l == 0.0) {   // k = m = 0: d^1_{00} = cos(beta)
+                s_al[p] = 1.0; s_ga[p] = 0.0; s_de[p] = 0.0;
+                continue;
+            }
+            double s2 = sqrt(((l + 1) * (l + 1) - m * m) * ((l + 1) * (l + 1) - k * k));
+            double s1 = sqrt(fmax(0.0, (l * l - m * m) * (l * l - k * k)));
+            s_al[p] = (2 * l + 1) * (l + 1) / s2;
+            s_ga[p] = (2 * l + 1) * m * k / (l * s2);
+            s_de[p] = (l + 1) * s1 / (l * s2);
+        }
+    }
+    __syncthreads();
+    if (n >= nnodes) return;
+    const double r = R[n];
+    const double er = exp(r), emr = exp(-r);
+    const double sh2 = er - emr;   // 2 sinh r
+    const int kpm = (tk + tm) / 2, kmm = (tk - tm) / 2;
+    double sqc = 1.0;              // sqrt(C(2k, k+m))
+    {
+        double c = 1.0;
+        for (int i = 1; i <= kpm; i++) c = c * (kmm + i) / i;
+        sqc = sqrt(c);
+    }
+    const int tlmax = tk + 2 * (nl - 1);
+    const int N = sf_gl_count(r, rho, tk, tlmax);
+    const int64_t go = sf_gl_offset(N);
+    const double* gp = gl + go;
+    const double* gm = gl + SF_GL_TOTAL + go;
+    const double* gw = gl + 2 * SF_GL_TOTAL + go;
+    for (int c0 = 0; c0 < nl; c0 += SF_DT_LCHUNK) {
+        double are[SF_DT_LCHUNK], aim[SF_DT_LCHUNK];
+#pragma unroll
+        for (int q = 0; q < SF_DT_LCHUNK; q++) { are[q] = 0.0; aim[q] = 0.0; }
+        for (int j = 0; j < N; j++) {
+            const double opx = gp[j], omx = gm[j], w = gw[j];
+            const double v = (opx <= omx) ? (-r + r * opx) : (r - r * omx);
+            const double ev = exp(v), emv = 1.0 / ev;
+            const double A = expm1(r * opx);   // e^{v+r} - 1
+            const double Bq = expm1(r * omx);  // e^{r-v} - 1
+            const double t = fmin(1.0, emr * A / sh2), omt = fmin(1.0, ev * Bq / sh2);
+            const double tr = fmin(1.0, emv * A / sh2), omtr = fmin(1.0, emr * Bq / sh2);
+            const double dk = sqc * ipow_(sqrt(omt), kpm) * ipow_(sqrt(t), kmm);
+            double sn, cs;
+            sincos(rho * v, &sn, &cs);
+            const double wd = w * dk;
+            const double pr = wd * cs, pi = wd * sn;
+            const double cb = omtr - tr;   // cos(beta_r)
+            double dprev = 0.0, dcur = sqc * ipow_(sqrt(omtr), kpm) * ipow_(sqrt(tr), kmm);
+            int p = 0;
+            for (; p < c0; p++) {
+                double dn = (s_al[p] * cb - s_ga[p]) * dcur - s_de[p] * dprev;
+                dprev = dcur;
+                dcur = dn;
+            }
+#pragma unroll
+            for (int q = 0; q < SF_DT_LCHUNK; q++) {
+                if (c0 + q < nl) {
+                    are[q] = fma(pr, dcur, are[q]);
+                    aim[q] = fma(pi, dcur, aim[q]);
+                    if (c0 + q + 1 < nl) {
+                        double dn = (s_al[c0 + q] * cb - s_ga[c0 + q]) * dcur - s_de[c0 + q] * dprev;
+                        dprev = dcur;
+                        dcur = dn;
+                    }
+                }
+            }
+        }
+        // prefactor i^(k-l) Phi_l sqrt((2k+1)(2l+1)) r / (2 sinh r)
+        double phr = 1.0, phi = 0.0;   // Phi_l, built up from l = k
+        for (int p = 0; p < c0; p++) {
+            double nn = k + p + 1, den = sqrt(nn * nn + rho * rho);
+            double ur = nn / den, ui = -rho / den;
+            double a = phr * ur - phi * ui, b = phr * ui + phi * ur;
+            phr = a; phi = b;
+        }
+#pragma unroll
+        for (int q = 0; q < SF_DT_LCHUNK; q++) {
+            int p = c0 + q;
+            if (p < nl) {
+                double l = k + p;
+                double sc = sqrt((2 * k + 1) * (2 * l + 1)) * r / sh2;
+                // i^(k-l) = (-i)^p
+                double zr = phr, zi = phi;
+                switch (p & 3) {
+                    case 0: break;
+                    case 1: { double a = zi, b = -zr; zr = a; zi = b; } break;   // * (-i)
+                    case 2: { zr = -zr; zi = -zi; } break;
+                    default: { double a = -zi, b = zr; zr = a; zi = b; } break;  // * i
+                }
+                double vr = are[q] * zr - aim[q] * zi, vi = are[q] * zi + aim[q] * zr;
+                out[((int64_t)p * (tk + 1) + im) * nnodes + n] = make_double2(sc * vr, sc * vi);
+                // advance Phi to l+1
+                double nn = l + 1, den = sqrt(nn * nn + rho * rho);
+                double ur = nn / den, ui = -rho / den;
+                double a = phr * ur - phi * ui, b = phr * ui + phi * ur;
+                phr = a; phi = b;
+            }
+        }
+    }
+}
+
+int sf_dtable_build(int tk, double gamma, int nl, int nnodes, const double* d_r, const double* d_gl, double2* d_out,
+                    cudaStream_t s) {
+    if (nl > SF_MAX_DL + 1) return sf_set_error(SF_ERR_LIMIT, "dl too large for the d-table kernel");
+    double rho = gamma * (0.5 * tk + 1.0);
+    dim3 grid((nnodes + 127) / 128, tk + 1);
+    k_dtable<<<grid, 128, 0, s>>>(tk, rho, nl, nnodes, d_r, d_gl, d_out);
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// boosters
+// ---------------------------------------------------------------------------------------------
+// strands of each edge in coupling order: face index and which free-face offset (0..2 of the
+// triple, or -1 for the gauge face)
+__constant__ int c_edge_face[4][4] = {{F23, F24, F25, F12}, {F34, F35, F13, F23}, {F45, F14, F24, F34}, {F15, F25, F35, F45}};
+__constant__ int c_edge_slot[4][4] = {{0, 1, 2, -1}, {0, 1, -1, 2}, {0, -1, 1, 2}, {-1, 0, 1, 2}};
+
+#define SF_NC 32   // nodes per staged chunk
+
+// boundary-side 3j tables of one edge (shared by every triple):
+//   Aj[i][m1][m2] = (j1 j2 i; m1 m2 mu), Cj[i][m3][m4] = (i j3 j4; -mu m3 m4), mu = -(m1+m2)
+__global__ void k_boundary_3j(const VtxDev* __restrict__ vp, int edge, const dd* __restrict__ F, double* Aj, double* Cj,
+                              int* status) {
+    const VtxDev& v = *vp;
+    const int e = edge - 2;
+    int tj[4];
+    for (int a = 0; a < 4; a++) tj[a] = v.tj[c_edge_face[e][a]];
+    const int di = v.di[e + 1], ilo = v.ilo[e + 1];
+    const int n1 = tj[0] + 1, n2 = tj[1] + 1, n3 = tj[2] + 1, n4 = tj[3] + 1;
+    const int stride = gridDim.x * blockDim.x;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < di * n1 * n2; q += stride) {
+        int c = q / (n1 * n2), r = q % (n1 * n2), i1 = r / n2, i2 = r % n2;
+        int tm1 = -tj[0] + 2 * i1, tm2 = -tj[1] + 2 * i2;
+        Aj[q] = dd_to_d(sf_threej_dd(tj[0], tj[1], ilo + 2 * c, tm1, tm2, -(tm1 + tm2), F, status));
+    }
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < di * n3 * n4; q += stride) {
+        int c = q / (n3 * n4), r = q % (n3 * n4), i3 = r / n4, i4 = r % n4;
+        int tm3 = -tj[2] + 2 * i3, tm4 = -tj[3] + 2 * i4;
+        Cj[q] = dd_to_d(sf_threej_dd(ilo + 2 * c, tj[2], tj[3], -(tm3 + tm4), tm3, tm4, F, status));
+    }
+}
+
+// one CTA per virtual-spin triple t of one edge
+__global__ void __launch_bounds__(256) k_booster(const VtxDev* __restrict__ vp, int edge, const double* __restrict__ Wm,
+                                                 int nnodes, const dd* __restrict__ F, const double* __restrict__ gAj,
+                                                 const double* __restrict__ gCj, double* __restrict__ Bout, int* status) {
+    extern __shared__ double sm[];
+    const VtxDev& v = *vp;
+    const int e = edge - 2;
+    const int D = v.D;
+    const int t = blockIdx.x;
+    const int toff[3] = {t / (D * D), (t / D) % D, t % D};
+    int tj[4], tl[4], il[4], fc[4];
+    for (int a = 0; a < 4; a++) {
+        fc[a] = c_edge_face[e][a];
+        tj[a] = v.tj[fc[a]];
+        int sl = c_edge_slot[e][a];
+        il[a] = sl < 0 ? 0 : toff[sl];
+        tl[a] = tj[a] + 2 * il[a];
+    }
+    const int di = v.di[e + 1], ilo = v.ilo[e + 1];
+    const int dkmax = v.dkmax[e];
+    double* Bt = Bout + (int64_t)t * di * dkmax;
+    int klo, nk;
+    sf_pair_range(tl[0], tl[1], tl[2], tl[3], &klo, &nk);
+    for (int q = threadIdx.x; q < di * dkmax; q += blockDim.x) Bt[q] = 0.0;
+    if (nk == 0) return;
+    const int n1 = tj[0] + 1, n2 = tj[1] + 1, n3 = tj[2] + 1, n4 = tj[3] + 1;
+    const int M = n1 * n2 * n3;
+    const int nmax = imax_(imax_(n1, n2), imax_(n3, n4));
+    // shared: I[M] complex | union { staged d rows [4][nmax][SF_NC] complex ; Al[nk][n1 n2], Cl[nk][n3 n4] }
+    double2* sI = reinterpret_cast<double2*>(sm);
+    double2* stage = sI + M;
+    double* sAl = reinterpret_cast<double*>(stage);
+    double* sCl = sAl + nk * n1 * n2;
+    const double2* d0 = v.dtab[fc[0]] + (int64_t)il[0] * n1 * nnodes;
+    const double2* d1 = v.dtab[fc[1]] + (int64_t)il[1] * n2 * nnodes;
+    const double2* d2 = v.dtab[fc[2]] + (int64_t)il[2] * n3 * nnodes;
+    const double2* d3 = v.dtab[fc[3]] + (int64_t)il[3] * n4 * nnodes;
+    // ---- I(m) = sum_n W_n d0(m1) d1(m2) d2(m3) d3(m4), m4 = -(m1+m2+m3)
+    double accr[20], acci[20];
+#pragma unroll
+    for (int q = 0; q < 20; q++) { accr[q] = 0.0; acci[q] = 0.0; }
+    for (int n0 = 0; n0 < nnodes; n0 += SF_NC) {
+        const int nc = imin_(SF_NC, nnodes - n0);
+        __syncthreads();
+        for (int q = threadIdx.x; q < 4 * nmax * SF_NC; q += blockDim.x) {
+            int a = q / (nmax * SF_NC), rem = q % (nmax * SF_NC), mi = rem / SF_NC, nn = rem % SF_NC;
+            int na = a == 0 ? n1 : a == 1 ? n2 : a == 2 ? n3 : n4;
+            const double2* src = a == 0 ? d0 : a == 1 ? d1 : a == 2 ? d2 : d3;
+            double2 val = make_double2(0.0, 0.0);
+            if (mi < na && nn < nc) {
+                val = src[(int64_t)mi * nnodes + n0 + nn];
+                if (a == 0) { double w = Wm[n0 + nn]; val.x *= w; val.y *= w; }
+            }
+            stage[q] = val;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 20; q++) {
+            int mt = threadIdx.x + q * blockDim.x;
+            if (mt < M) {
+                int i3 = mt % n3, i2 = (mt / n3) % n2, i1 = mt / (n3 * n2);
+                int tm4 = -((-tj[0] + 2 * i1) + (-tj[1] + 2 * i2) + (-tj[2] + 2 * i3));
+                if (iabs_(tm4) <= tj[3]) {
+                    int i4 = (tm4 + tj[3]) / 2;
+                    const double2* p0 = stage + (0 * nmax + i1) * SF_NC;
+                    const double2* p1 = stage + (1 * nmax + i2) * SF_NC;
+                    const double2* p2 = stage + (2 * nmax + i3) * SF_NC;
+                    const double2* p3 = stage + (3 * nmax + i4) * SF_NC;
+                    double sr = accr[q], si = acci[q];
+                    for (int nn = 0; nn < nc; nn++) {
+                        double2 a = p0[nn], b = p1[nn], c = p2[nn], d = p3[nn];
+                        double abr = a.x * b.x - a.y * b.y, abi = a.x * b.y + a.y * b.x;
+                        double cdr = c.x * d.x - c.y * d.y, cdi = c.x * d.y + c.y * d.x;
+                        sr += abr * cdr - abi * cdi;
+                        si += abr * cdi + abi * cdr;
+                    }
+                    accr[q] = sr;
+                    acci[q] = si;
+                }
+            }
+        }
+    }
+    __syncthreads();   // stage is reused for the 3j tables below
+#pragma unroll
+    for (int q = 0; q < 20; q++) {
+        int mt = threadIdx.x + q * blockDim.x;
+        if (mt < M) sI[mt] = make_double2(accr[q], acci[q]);
+    }
+    // ---- virtual-side 3j tables: Al[c][m1][m2] = (l1 l2 k; m1 m2 mu), Cl[c][m3][m4] = (k l3 l4; -mu m3 m4)
+    for (int q = threadIdx.x; q < nk * n1 * n2; q += blockDim.x) {
+        int c = q / (n1 * n2), r = q % (n1 * n2), i1 = r / n2, i2 = r % n2;
+        int tm1 = -tj[0] + 2 * i1, tm2 = -tj[1] + 2 * i2;
+        sAl[q] = dd_to_d(sf_threej_dd(tl[0], tl[1], klo + 2 * c, tm1, tm2, -(tm1 + tm2), F, status));
+    }
+    for (int q = threadIdx.x; q < nk * n3 * n4; q += blockDim.x) {
+        int c = q / (n3 * n4), r = q % (n3 * n4), i3 = r / n4, i4 = r % n4;
+        int tm3 = -tj[2] + 2 * i3, tm4 = -tj[3] + 2 * i4;
+        sCl[q] = dd_to_d(sf_threej_dd(klo + 2 * c, tl[2], tl[3], -(tm3 + tm4), tm3, tm4, F, status));
+    }
+    __syncthreads();
+    // ---- B[i][k] = sum_m (-1)^((i - mu) + (k - mu)) Aj Cj Al Cl I(m)
+    for (int q = threadIdx.x; q < di * nk; q += blockDim.x) {
+        const int ci = q / nk, ck = q % nk;
+        const int ti = ilo + 2 * ci, tk = klo + 2 * ck;
+        double br = 0.0, bi = 0.0;
+        for (int i1 = 0; i1 < n1; i1++) {
+            const int tm1 = -tj[0] + 2 * i1;
+            for (int i2 = 0; i2 < n2; i2++) {
+                const int tm2 = -tj[1] + 2 * i2;
+                const int tmu = -(tm1 + tm2);
+                const double aa = gAj[(ci * n1 + i1) * n2 + i2] * sAl[(ck * n1 + i1) * n2 + i2];
+                if (aa == 0.0) continue;
+                const int par = ((ti - tmu) / 2 + (tk - tmu) / 2) & 1;
+                double sr = 0.0, si = 0.0;
+                for (int i3 = 0; i3 < n3; i3++) {
+                    const int tm3 = -tj[2] + 2 * i3;
+                    const int tm4 = tmu - tm3;
+                    if (iabs_(tm4) > tj[3]) continue;
+                    const int i4 = (tm4 + tj[3]) / 2;
+                    const double cc = gCj[(ci * n3 + i3) * n4 + i4] * sCl[(ck * n3 + i3) * n4 + i4];
+                    const double2 I = sI[(i1 * n2 + i2) * n3 + i3];
+                    sr = fma(cc, I.x, sr);
+                    si = fma(cc, I.y, si);
+                }
+                if (par) { br -= aa * sr; bi -= aa * si; } else { br += aa * sr; bi += aa * si; }
+            }
+        }
+        Bt[ci * dkmax + ck] = br;
+        // realness self-check (B4 is real with the phase convention of the d-tables)
+        if (fabs(bi) > 1e-9 * fabs(br) + 1e-15 && status) atomicCAS(status, SF_DEV_OK, SF_DEV_NONREAL_BOOSTER);
+    }
+}
+
+size_t sf_booster_smem(int tj1, int tj2, int tj3, int tj4, int nk) {
+    int n1 = tj1 + 1, n2 = tj2 + 1, n3 = tj3 + 1, n4 = tj4 + 1;
+    int nmax = n1; if (n2 > nmax) nmax = n2; if (n3 > nmax) nmax = n3; if (n4 > nmax) nmax = n4;
+    size_t M = (size_t)n1 * n2 * n3;
+    size_t stage = (size_t)4 * nmax * SF_NC * sizeof(double2);
+    size_t tabs = sizeof(double) * ((size_t)nk * n1 * n2 + (size_t)nk * n3 * n4);
+    return M * sizeof(double2) + (stage > tabs ? stage : tabs);
+}
+
+int sf_booster_build(const VtxDev* d_v, int edge, int ntrip, size_t smem, const double* d_W, int nnodes,
+                     const dd* F, double* d_Aj, double* d_Cj, double* d_B, int* d_status, cudaStream_t s) {
+    if (smem > 227 * 1024) return sf_set_error(SF_ERR_LIMIT, "booster kernel needs %zu bytes of shared memory", smem);
+    k_boundary_3j<<<64, 256, 0, s>>>(d_v, edge, F, d_Aj, d_Cj, d_status);
+    SF_CUDA_TRY(cudaGetLastError());
+    SF_CUDA_TRY(cudaFuncSetAttribute(k_booster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_booster<<<ntrip, 256, smem, s>>>(d_v, edge, d_W, nnodes, F, d_Aj, d_Cj, d_B, d_status);
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}

@@ -1,0 +1,268 @@
+// Internal declarations shared by the CUDA translation units of the EPRL vertex library.
+// Everything here is device/host plumbing for the kernels behind include/sf_eprl.h.
+#pragma once
+
+#include <cstdint>
+#include <cstdio>
+#include <cstdarg>
+#include <cstring>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/sf_eprl.h"
+
+// ----------------------------------------------------------------------------------------------
+// limits (checked on the host before any launch)
+// ----------------------------------------------------------------------------------------------
+#define SF_FACT_MAX 170        // factorials up to 170! fit in a double exponent
+#define SF_BI_LIMBS 24         // 768-bit magnitudes for the exact Racah sums
+#define SF_RACAH_MAX 250       // every integer Racah argument (z+1, beta-z, ...) stays below 256
+#define SF_MAX_DL 40           // shells per face (dl+1) handled by one d-table pass set
+#define SF_DT_LCHUNK 12        // l values accumulated per d-table pass
+
+// ----------------------------------------------------------------------------------------------
+// error reporting (thread-local message, set by the host side of every entry point)
+// ----------------------------------------------------------------------------------------------
+int sf_set_error(int code, const char* fmt, ...);
+
+#define SF_CUDA_TRY(call)                                                                      \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return sf_set_error(e_ == cudaErrorMemoryAllocation ? SF_ERR_OOM : SF_ERR_CUDA,    \
+                                "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),        \
+                                __FILE__, __LINE__);                                           \
+    } while (0)
+
+// status word written by kernels (first error wins)
+#define SF_DEV_OK 0
+#define SF_DEV_BIGINT_OVERFLOW 1
+#define SF_DEV_NONREAL_BOOSTER 2
+#define SF_DEV_BAD_INDEX 3
+#define SF_DEV_TIMEOUT 4
+
+// ----------------------------------------------------------------------------------------------
+// small helpers on doubled spins (host + device)
+// ----------------------------------------------------------------------------------------------
+__host__ __device__ inline int iabs_(int a) { return a < 0 ? -a : a; }
+__host__ __device__ inline int imin_(int a, int b) { return a < b ? a : b; }
+__host__ __device__ inline int imax_(int a, int b) { return a > b ? a : b; }
+
+__host__ __device__ inline bool sf_tri(int a, int b, int c) {
+    return iabs_(a - b) <= c && c <= a + b && ((a + b + c) & 1) == 0;
+}
+
+// Range of an intertwiner coupling the pair (a,b) to the pair (c,d): doubled lo and count (0 if empty).
+__host__ __device__ inline void sf_pair_range(int a, int b, int c, int d, int* lo, int* n) {
+    if ((a + b + c + d) & 1) { *lo = 0; *n = 0; return; }
+    int l = imax_(iabs_(a - b), iabs_(c - d));
+    int h = imin_(a + b, c + d);
+    *lo = l;
+    *n = (h >= l) ? (h - l) / 2 + 1 : 0;
+}
+
+// ----------------------------------------------------------------------------------------------
+// double-double arithmetic: error-free transformations of Dekker and Knuth as used by
+// Hida, Li and Bailey's double-double library (published algorithms, written out here)
+// ----------------------------------------------------------------------------------------------
+struct dd { double hi, lo; };
+
+__host__ __device__ inline dd dd_make(double a) { return dd{a, 0.0}; }
+__host__ __device__ inline dd two_sum(double a, double b) {
+    double s = a + b;
+    double bb = s - a;
+    double e = (a - (s - bb)) + (b - bb);
+    return dd{s, e};
+}
+__host__ __device__ inline dd quick_two_sum(double a, double b) {
+    double s = a + b;
+    double e = b - (s - a);
+    return dd{s, e};
+}
+__host__ __device__ inline dd two_prod(double a, double b) {
+    double p = a * b;
+    double e = fma(a, b, -p);
+    return dd{p, e};
+}
+__host__ __device__ inline dd dd_add(dd a, dd b) {
+    dd s = two_sum(a.hi, b.hi);
+    dd t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = quick_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return quick_two_sum(s.hi, s.lo);
+}
+__host__ __device__ inline dd dd_neg(dd a) { return dd{-a.hi, -a.lo}; }
+__host__ __device__ inline dd dd_mul(dd a, dd b) {
+    dd p = two_prod(a.hi, b.hi);
+    p.lo += a.hi * b.lo + a.lo * b.hi;
+    return quick_two_sum(p.hi, p.lo);
+}
+__host__ __device__ inline dd dd_mul_d(dd a, double b) {
+    dd p = two_prod(a.hi, b);
+    p.lo += a.lo * b;
+    return quick_two_sum(p.hi, p.lo);
+}
+__host__ __device__ inline dd dd_div(dd a, dd b) {
+    double q1 = a.hi / b.hi;
+    dd r = dd_add(a, dd_neg(dd_mul_d(b, q1)));
+    double q2 = r.hi / b.hi;
+    r = dd_add(r, dd_neg(dd_mul_d(b, q2)));
+    double q3 = r.hi / b.hi;
+    dd q = quick_two_sum(q1, q2);
+    return dd_add(q, dd_make(q3));
+}
+__host__ __device__ inline dd dd_sqrt(dd a) {
+    if (a.hi <= 0.0) return dd{0.0, 0.0};
+    double x = sqrt(a.hi);
+    dd x2 = two_prod(x, x);
+    dd r = dd_add(a, dd_neg(x2));
+    double c = r.hi / (2.0 * x);
+    return quick_two_sum(x, c);
+}
+__host__ __device__ inline double dd_to_d(dd a) { return a.hi + a.lo; }
+
+// ----------------------------------------------------------------------------------------------
+// exact unsigned big integers for the Racah sums (limbs of 32 bits, little-endian, fixed
+// capacity, loops fully unrolled so that the limbs live in registers)
+// ----------------------------------------------------------------------------------------------
+struct BigU { uint32_t w[SF_BI_LIMBS]; };
+
+__device__ inline void bi_zero(BigU& a) {
+#pragma unroll
+    for (int i = 0; i < SF_BI_LIMBS; i++) a.w[i] = 0u;
+}
+__device__ inline void bi_set(BigU& a, uint32_t v) { bi_zero(a); a.w[0] = v; }
+// a *= m; returns the carry out of the top limb (non-zero means overflow)
+__device__ inline uint32_t bi_mul(BigU& a, uint32_t m) {
+    uint64_t c = 0;
+#pragma unroll
+    for (int i = 0; i < SF_BI_LIMBS; i++) {
+        uint64_t t = (uint64_t)a.w[i] * m + c;
+        a.w[i] = (uint32_t)t;
+        c = t >> 32;
+    }
+    return (uint32_t)c;
+}
+// a /= d for a divisor d >= 1 that divides a exactly (quotient by reciprocal multiplication:
+// q = mulhi(cur, floor((2^64-1)/d)) is q_true or q_true - 1 because cur < 2^64)
+__device__ inline void bi_divexact(BigU& a, uint32_t d) {
+    const uint64_t M = 0xFFFFFFFFFFFFFFFFull / d;
+    uint64_t rem = 0;
+#pragma unroll
+    for (int i = SF_BI_LIMBS - 1; i >= 0; i--) {
+        uint64_t cur = (rem << 32) | a.w[i];
+        uint64_t q = __umul64hi(cur, M);
+        uint64_t r = cur - q * d;
+        if (r >= d) { q++; r -= d; }
+        a.w[i] = (uint32_t)q;
+        rem = r;
+    }
+}
+__device__ inline uint32_t bi_add(BigU& a, const BigU& b) {
+    uint64_t c = 0;
+#pragma unroll
+    for (int i = 0; i < SF_BI_LIMBS; i++) {
+        uint64_t t = (uint64_t)a.w[i] + b.w[i] + c;
+        a.w[i] = (uint32_t)t;
+        c = t >> 32;
+    }
+    return (uint32_t)c;
+}
+// compare: -1, 0, 1
+__device__ inline int bi_cmp(const BigU& a, const BigU& b) {
+    int r = 0;
+#pragma unroll
+    for (int i = 0; i < SF_BI_LIMBS; i++) {
+        if (a.w[i] != b.w[i]) r = (a.w[i] > b.w[i]) ? 1 : -1;   // the highest differing limb wins
+    }
+    return r;
+}
+// a -= b, requires a >= b
+__device__ inline void bi_sub(BigU& a, const BigU& b) {
+    int64_t br = 0;
+#pragma unroll
+    for (int i = 0; i < SF_BI_LIMBS; i++) {
+        int64_t t = (int64_t)a.w[i] - (int64_t)b.w[i] - br;
+        br = (t < 0) ? 1 : 0;
+        a.w[i] = (uint32_t)(t + (br << 32));
+    }
+}
+// value as double-double (top 128 bits, exact up to the dd rounding of the sum)
+__device__ inline dd bi_to_dd(const BigU& a) {
+    int top = -1;
+#pragma unroll
+    for (int i = 0; i < SF_BI_LIMBS; i++) if (a.w[i]) top = i;
+    if (top < 0) return dd{0.0, 0.0};
+    dd acc{0.0, 0.0};
+    for (int i = top; i >= 0 && i > top - 4; i--) {
+        acc = dd_add(acc, dd_make(ldexp((double)a.w[i], 32 * i)));
+    }
+    return acc;
+}
+
+// ----------------------------------------------------------------------------------------------
+// device-side descriptors
+// ----------------------------------------------------------------------------------------------
+// one slot (fixed virtual spins) of a {6j} table: a dense box over (a, b, x), doubled lows
+struct SlotDesc {
+    int64_t off;
+    int32_t alo, blo, xlo, na, nb, nx;
+};
+
+// per-vertex parameters visible to kernels
+struct VtxDev {
+    int32_t tj[10];
+    double gamma;
+    int32_t dl, D;             // D = dl + 1
+    int32_t ilo[5], di[5];     // intertwiner ranges
+    int64_t nshell;            // D^6
+    const double* S[5];        // {6j} tables S1..S5
+    const SlotDesc* slot[5];
+    const double* B[4];        // boosters of edges 2..5: [t][i][k - klo(t)], padded to dkmax
+    const int32_t* klo[4];
+    int32_t dkmax[4];
+    int64_t ntrip;             // D^3
+    const double2* dtab[10];   // d-tables per face [il][im][n]
+    int32_t nl[10];            // l values per face (D for free faces, 1 for gauge faces)
+};
+
+// face index helpers (order j12 j13 j14 j15 j23 j24 j25 j34 j35 j45)
+enum { F12 = 0, F13, F14, F15, F23, F24, F25, F34, F35, F45 };
+
+// ----------------------------------------------------------------------------------------------
+// launch wrappers implemented in the kernel translation units (return SF_OK or an error code)
+// ----------------------------------------------------------------------------------------------
+int sf_launch_fact_table(cudaStream_t s);
+int sf_launch_6j_table(const int32_t* tj6args_unused, double* out, const SlotDesc* d_slots, int nslots,
+                       int64_t n_entries, int table_id, const VtxDev* d_v, int* d_status, cudaStream_t s);
+
+// rapidity rule and d-tables
+int sf_launch_gl_library(double* d_gl, int64_t* d_gl_off, cudaStream_t s);
+int sf_launch_rule_nodes(const sf_quad_rule* q, double* d_x, double* d_w, double* d_r, double* d_W,
+                         double* d_glrule, cudaStream_t s);
+int sf_launch_dtable(const VtxDev* h_v, int face, double2* d_out, const double* d_r, int nnodes,
+                     const double* d_gl, cudaStream_t s);
+int sf_launch_boosters(const VtxDev* h_v, const VtxDev* d_v, int edge, double* d_B, const double* d_W,
+                       int nnodes, int* d_status, cudaStream_t s);
+
+// shell sums
+struct WorkItem {
+    int32_t vtx, i1, i2, g0, g1;
+    int32_t pad;
+    int64_t part_off;
+};
+struct ShellFilter {
+    int64_t begin, end;          // linear shell range
+    const uint32_t* bitmap;      // optional membership bitmap (single vertex), overrides the range
+};
+int sf_launch_shell_fp64(const VtxDev* d_v, int max_di, int max_dk, int max_nx, const WorkItem* d_items,
+                         int n_items, int* d_counter, double* d_part, ShellFilter filt, int* d_status,
+                         cudaStream_t s);
+int sf_launch_shell_mixed(const VtxDev* d_v, int max_di, int max_dk, int max_nx, const WorkItem* d_items,
+                          int n_items, int* d_counter, double* d_part, ShellFilter filt, int* d_status,
+                          cudaStream_t s);
+int sf_launch_reduce(const VtxDev* d_v, int vtx, const VtxDev* h_v, const WorkItem* d_items, int item_begin,
+                     int item_end, const double* d_part, double* A, cudaStream_t s);
+int sf_launch_adjoint(const VtxDev* d_v, const VtxDev* h_v, const double2* const* psi, double2* d_scr_a,
+                      double2* d_scr_gphi, int64_t nshell, cudaStream_t s);

@@ -1,0 +1,83 @@
+// {6j} tables S1..S5 of the vertex algorithm (Sec. 3, framed algorithm step 4), exact.
+#include "sf_racah.cuh"
+
+// n! for n = 0..SF_FACT_MAX as double-double (sequential products, relative error ~n 2^-106)
+__global__ void k_fact_table(dd* F) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    dd f = dd_make(1.0);
+    F[0] = f;
+    for (int n = 1; n <= SF_FACT_MAX; n++) {
+        f = dd_mul_d(f, (double)n);
+        F[n] = f;
+    }
+}
+
+// one thread per table entry (grid-stride); the slot of an entry is found by binary search
+__global__ void __launch_bounds__(256) k_sixj_table(int table_id, const VtxDev* __restrict__ vp,
+                                                    const SlotDesc* __restrict__ slots, int nslots,
+                                                    int64_t n, double* __restrict__ out,
+                                                    const dd* __restrict__ F, int* status) {
+    const VtxDev& v = *vp;
+    const int D = v.D;
+    const int j12 = v.tj[F12], j13 = v.tj[F13], j14 = v.tj[F14], j15 = v.tj[F15];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+        int lo = 0, hi = nslots - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (slots[mid].off <= e) lo = mid; else hi = mid - 1;
+        }
+        const SlotDesc s = slots[lo];
+        int64_t r = e - s.off;
+        const int ix = (int)(r % s.nx);
+        r /= s.nx;
+        const int ib = (int)(r % s.nb);
+        const int ia = (int)(r / s.nb);
+        const int a = s.alo + 2 * ia, b = s.blo + 2 * ib, x = s.xlo + 2 * ix;
+        double val = 0.0;
+        switch (table_id) {
+            case 1: {   // slot d25: {i1 l25 x; k5 j14 j15}, a = i1, b = k5
+                const int l25 = v.tj[F25] + 2 * lo;
+                val = sf_sixj(a, l25, x, b, j14, j15, F, status);
+            } break;
+            case 2: {   // slot (d35, d45): {j14 k5 x; l35 k4 l45}, a = k5, b = k4
+                const int l35 = v.tj[F35] + 2 * (lo / D), l45 = v.tj[F45] + 2 * (lo % D);
+                val = sf_sixj(j14, a, x, l35, b, l45, F, status);
+            } break;
+            case 3: {   // slot (d24, d34, d35): {k4 l35 x; k3 l24 l34}, a = k4, b = k3
+                const int l24 = v.tj[F24] + 2 * (lo / (D * D));
+                const int l34 = v.tj[F34] + 2 * ((lo / D) % D);
+                const int l35 = v.tj[F35] + 2 * (lo % D);
+                val = sf_sixj(a, l35, x, b, l24, l34, F, status);
+            } break;
+            case 4: {   // slot (d23, d24): {l24 k3 x; j13 k2 l23}, a = k3, b = k2
+                const int l23 = v.tj[F23] + 2 * (lo / D), l24 = v.tj[F24] + 2 * (lo % D);
+                val = sf_sixj(l24, a, x, j13, b, l23, F, status);
+            } break;
+            default: {  // 5, slot d25: {k2 j13 x; i1 l25 j12}, a = k2, b = i1
+                const int l25 = v.tj[F25] + 2 * lo;
+                val = sf_sixj(a, j13, x, b, l25, j12, F, status);
+            } break;
+        }
+        out[e] = val;
+    }
+}
+
+int sf_launch_fact_table(cudaStream_t s) { (void)s; return SF_OK; }
+
+int sf_fact_table_build(dd* F, cudaStream_t s) {
+    k_fact_table<<<1, 1, 0, s>>>(F);
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
+int sf_sixj_table_build(int table_id, const VtxDev* d_v, const SlotDesc* d_slots, int nslots, int64_t n,
+                        double* d_out, const dd* F, int* d_status, int num_sms, cudaStream_t s) {
+    if (n <= 0) return SF_OK;
+    int64_t blocks = (n + 255) / 256;
+    int64_t cap = (int64_t)num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    k_sixj_table<<<(unsigned)blocks, 256, 0, s>>>(table_id, d_v, d_slots, nslots, n, d_out, F, d_status);
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
