@@ -1,0 +1,397 @@
+"""Benchmark: EPRL vertex shells/s on one GB300 (and N GPUs by weak scaling).
+
+Workload (the homogeneous scaling sweep): sixteen vertices with all ten boundary spins
+j = lambda/2, lambda = 1..16, gamma = 1.2, dl = 10 (11^6 = 1,771,561 shells each), rapidity rule
+r_max = 40, 40 panels x 50 Gauss-Legendre nodes. One step runs the whole path through the C ABI:
+{6j} tables, d-tables and boosters of all sixteen vertices, then the shell sum over one slice of
+every vertex (the same 1/S range of its group-major shell index), so S consecutive steps cover the
+sweep exactly once. Ranks of a multi-GPU run take different slices (weak scaling, no collective on
+the data path).
+
+Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle on a bounded sample of
+the same workload instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+RULE = (40.0, 40, 50)
+SWEEP = [(lam, 10) for lam in range(1, 17)]
+GAMMA = 1.2
+# FP64 FMA pipe of the GB300: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.070 GHz (max SM clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# DRAM traffic of one shell-sum launch from ncu (profiles/shell_fp64_sweep_slice.md), valid for the
+# kernel source whose sha1 prefix is recorded beside it; None until captured.
+NCU_TRAFFIC = {"sha1": None, "bytes_per_launch": None}
+
+
+def kernel_sha1():
+    p = os.path.join(ROOT, "paper_2107_13952_gb300", "csrc", "sf_shell.cu")
+    return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
+
+
+# ------------------------------------------------------------------------------------------
+# executed FP64 FMA count of the shell-sum kernel (trip counts of its loops), for the roofline
+# ------------------------------------------------------------------------------------------
+def _pair(a, b, c, d):
+    import numpy as np
+    a, b, c, d = np.broadcast_arrays(a, b, c, d)
+    lo = np.maximum(np.abs(a - b), np.abs(c - d))
+    hi = np.minimum(a + b, c + d)
+    n = np.where(((a + b + c + d) % 2 == 0) & (hi >= lo), (hi - lo) // 2 + 1, 0)
+    return lo, n
+
+
+def executed_fmas(tj, dl, g0, g1):
+    """FP64 FMAs the shell kernel executes for groups [g0, g1) of one vertex (all tiles)."""
+    import numpy as np
+    from paper_2107_13952_gb300 import intertwiner_ranges
+    lo, dim = intertwiner_ranges(tj, GAMMA, dl)
+    D = dl + 1
+    j12, j13, j14, j15, j23, j24, j25, j34, j35, j45 = tj
+    d = np.arange(D)
+    # axes: 0 d25, 1 d35, 2 d45, 3 d24, 4 d34, 5 d23
+    sh = [1] * 6
+
+    def ax(i):
+        s = list(sh)
+        s[i] = D
+        return d.reshape(s)
+    l25, l35, l45, l24, l34, l23 = (j25 + 2 * ax(0), j35 + 2 * ax(1), j45 + 2 * ax(2), j24 + 2 * ax(3),
+                                    j34 + 2 * ax(4), j23 + 2 * ax(5))
+    k5lo, nk5 = _pair(j15, l25, l35, l45)
+    k4lo, nk4 = _pair(l45, j14, l24, l34)
+    k2lo, nk2 = _pair(l23, l24, l25, j12)
+    k3lo, nk3 = _pair(l34, l35, j13, l23)
+    valid = (nk2 > 0) & (nk3 > 0)
+    nk3v = np.where(valid, nk3, 0)
+    nk2v = np.where(valid, nk2, 0)
+    k3lo_v = np.where(valid, k3lo, 10 ** 6)
+    k3hi_v = np.where(valid, k3lo + 2 * (nk3 - 1), -1)
+    shape5 = (D, D, D, D, D)
+    k3u = np.broadcast_to((k3hi_v.max(axis=5) - k3lo_v.min(axis=5)) // 2 + 1, shape5)
+    anyv = np.broadcast_to(valid.any(axis=5), shape5)
+    sum_nk3 = np.broadcast_to(nk3v.sum(axis=5), shape5)
+    sum_nk3nk2 = np.broadcast_to((nk3v * nk2v).sum(axis=5), shape5)
+    nk5b = np.broadcast_to(nk5[..., 0], shape5)
+    nk4b = np.broadcast_to(nk4[..., 0], shape5)
+    k5lob = np.broadcast_to(k5lo[..., 0], shape5)
+    k4lob = np.broadcast_to(k4lo[..., 0], shape5)
+    l25b = np.broadcast_to(l25[..., 0], shape5)
+    l35b = np.broadcast_to(l35[..., 0], shape5)
+    gidx = (np.arange(D)[:, None, None] * D + np.arange(D)[None, :, None]) * D + np.arange(D)[None, None, :]
+    gmask = np.broadcast_to(((gidx >= g0) & (gidx < g1))[..., None, None], shape5)
+    di3, di4, di5 = dim[2], dim[3], dim[4]
+    total = 0
+    k5hi = k5lob + 2 * (nk5b - 1)
+    k4hi = k4lob + 2 * (nk4b - 1)
+
+    def mind(c, lo_, hi_):
+        return np.where(c < lo_, lo_ - c, np.where(c > hi_, c - hi_, (c + lo_) % 2))
+    xlo_b = mind(j14, k5lob, k5hi)
+    xlo_c = mind(l35b, k4lob, k4hi)
+    for ci1 in range(dim[0]):
+        i1 = lo[0] + 2 * ci1
+        xlo = np.maximum(np.abs(i1 - l25b), np.maximum(xlo_b, xlo_c))
+        xhi = np.minimum(i1 + l25b, np.minimum(k5hi + j14, k4hi + l35b))
+        xlo = xlo + ((xlo - np.abs(i1 - l25b)) % 2)
+        nx = np.where(xhi >= xlo, (xhi - xlo) // 2 + 1, 0)
+        live = gmask & anyv & (nk5b > 0) & (nk4b > 0) & (nx > 0)
+        per5 = (sum_nk3nk2 * nx + nx * di3 * sum_nk3 + nk4b * nx * di3 * k3u + nk4b * nk5b * di3 * nx
+                + di4 * nk5b * di3 * nk4b)
+        total += int(np.where(live, per5, 0).sum())
+    # H: once per group with a non-empty k5 range
+    g_live = ((gidx >= g0) & (gidx < g1)) & (nk5[..., 0, 0, 0] > 0)
+    total += int(dim[0] * np.where(g_live, di4 * di5 * di3 * nk5[..., 0, 0, 0], 0).sum())
+    return total * dim[1]
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ------------------------------------------------------------------------------------------
+def _oracle_worker(args):
+    seed, deadline, lam_list = args
+    import numpy as np
+    from oracle import vertex as ov
+    from oracle import wigner as ow
+    rng = np.random.default_rng(seed)
+    done = 0
+    cache = {}
+    six = ov.SixJCache()
+    while time.time() < deadline:
+        lam = int(lam_list[rng.integers(0, len(lam_list))])
+        tj, dl = (lam,) * 10, 10
+        if lam not in cache:
+            bs = {}
+            D = dl + 1
+            for e in (2, 3, 4, 5):
+                di = len(ow.pair_range(*ov.edge_spins(tj, tuple(tj[4:]))[e][0]))
+                klo = np.zeros(D ** 3, dtype=np.int64)
+                nk = np.zeros(D ** 3, dtype=np.int64)
+                for t in range(D ** 3):
+                    dd = (t // (D * D), (t // D) % D, t % D)
+                    tl6 = dict(zip(ov.FREE, [tj[ov.FACES.index(f)] for f in ov.FREE]))
+                    for f, df in zip(ov.EDGE_TRIPLES[e], dd):
+                        tl6[f] += 2 * df
+                    kr = ow.pair_range(*ov.edge_spins(tj, tuple(tl6[f] for f in ov.FREE))[e][1])
+                    klo[t] = kr[0] if kr else 0
+                    nk[t] = len(kr)
+                bs[e] = {"B": rng.standard_normal((D ** 3, di, max(1, int(nk.max())))), "klo": klo}
+            cache[lam] = bs
+        s = int(rng.integers(0, (dl + 1) ** 6))
+        ov.shell_contribution(tj, dl, s, cache[lam], six)
+        done += 1
+    return done
+
+
+def oracle_rate(seconds, seed=0):
+    """Oracle shell-sum throughput (shells/s) on all host cores for `seconds` of wall time."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    lam_list = [lam for lam, _ in SWEEP]
+    ctx = mp.get_context("spawn")
+    t0 = time.time()
+    deadline = t0 + seconds
+    with ctx.Pool(cores) as pool:
+        counts = pool.map(_oracle_worker, [(seed * 1000 + i, deadline, lam_list) for i in range(cores)])
+    el = time.time() - t0
+    n = sum(counts)
+    return n / el, cores, n, el
+
+
+# ------------------------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--slices", type=int, default=16, help="steps per full pass over the sweep")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    total_shells_per_vertex = 11 ** 6
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        rates = []
+        n_all, t_all = 0, 0.0
+        for i in range(args.warmup + args.steps):
+            r, cores, n, el = oracle_rate(max(2.0, args.cpu_seconds / max(1, args.steps)), seed=i)
+            if i >= args.warmup:
+                rates.append(r)
+                n_all += n
+                t_all += el
+        value = n_all / t_all
+        line = {"impl": "reference", "metric": "EPRL vertex shells/sec", "value": value, "unit": "shells/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * t_all / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "homogeneous sweep lambda=1..16 (j=lambda/2), gamma=1.2, dl=10, "
+                                       "shell-sum phase of the CPU oracle on uniformly sampled shells",
+                           "sample": "%d shells" % n_all},
+                "cpu_baseline": {"value": value, "unit": "shells/s", "cores": cores, "kind": "oracle",
+                                 "sample": "%d shells drawn uniformly from the sweep's %d shells, boosters "
+                                           "random (shell-sum phase only)" % (n_all, 16 * total_shells_per_vertex)},
+                "e2e": {"value": value, "unit": "shells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import paper_2107_13952_gb300 as sf
+    sf.load()
+    prec = sf.SF_FP64 if args.precision == "fp64" else sf.SF_MIXED
+    verts = [sf.vertex((lam,) * 10, GAMMA, dl) for lam, dl in SWEEP]
+    dims = [sf.intertwiner_ranges((lam,) * 10, GAMMA, dl)[1] for lam, dl in SWEEP]
+    S = args.slices
+    N = total_shells_per_vertex
+    G = 11 ** 3
+    outs = [torch.empty(d, dtype=torch.float64, device="cuda") for d in dims]
+    host = [torch.empty(d, dtype=torch.float64, pin_memory=True) for d in dims]
+    stream = torch.cuda.current_stream()
+
+    def slice_bounds(k):
+        g0, g1 = G * k // S, G * (k + 1) // S
+        return g0 * 121 * 11, g1 * 121 * 11, g0, g1
+
+    def step(k, to_host):
+        b, e, _, _ = slice_bounds(k % S)
+        t = sf.sf_6j_table(verts)
+        sf.sf_boosters(t, RULE)
+        sf.sf_vertex_amplitude(t, prec, b, e, out=outs)
+        kms = sf.last_kernel_ms()
+        if to_host:
+            for o, h in zip(outs, host):
+                h.copy_(o, non_blocking=True)
+        del t
+        return kms, 16 * (e - b)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # warm-up
+    for i in range(args.warmup):
+        step(i * world + rank, False)
+    torch.cuda.synchronize()
+
+    def timed(to_host, first):
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kms_all, shells, slices = [], 0, []
+        launches0 = sf.kernel_launches()
+        e0.record(stream)
+        for i in range(args.steps):
+            k = (first + i) * world + rank
+            kms, n = step(k, to_host)
+            kms_all.append(kms)
+            shells += n
+            slices.append(k % S)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        return ms, kms_all, shells, slices, sf.kernel_launches() - launches0
+
+    clk = ClockSampler(local)
+    clk.start()
+    ms, kms_all, shells, slices, launches = timed(False, args.warmup)
+    clocks = clk.stop()
+    ms_e2e, _, shells_e2e, _, _ = timed(True, args.warmup + args.steps)
+
+    # max over ranks
+    if world > 1:
+        tm = torch.tensor([ms, ms_e2e], device="cuda")
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = float(tm[0]), float(tm[1])
+    total_shells = shells * world
+    value = total_shells / (ms / 1e3)
+    e2e_value = shells_e2e * world / (ms_e2e / 1e3)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (the shell sum): executed FP64 flops / event-timed duration
+    flops = 0
+    for k in slices:
+        _, _, g0, g1 = slice_bounds(k)
+        for lam, dl in SWEEP:
+            flops += 2 * executed_fmas((lam,) * 10, dl, g0, g1)
+    kern_s = sum(kms_all) / 1e3
+    achieved = flops / kern_s / 1e12 if kern_s > 0 else None
+    traffic = None
+    if NCU_TRAFFIC["sha1"] == kernel_sha1() and NCU_TRAFFIC["bytes_per_launch"]:
+        traffic = NCU_TRAFFIC["bytes_per_launch"]
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        r, cores, n, el = oracle_rate(args.cpu_seconds)
+        cpu = {"value": r, "unit": "shells/s", "cores": cores, "kind": "oracle",
+               "sample": "%d shells drawn uniformly from the sweep (%.1f s on %d processes), boosters random "
+                         "(shell-sum phase only)" % (n, el, cores)}
+
+    d2h = sum(h.numel() * 8 for h in host)
+    h2d = len(verts) * 56
+    line = {
+        "metric": "EPRL vertex shells/sec (%s GPU path)" % args.precision.upper(),
+        "value": value, "unit": "shells/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f64+tf32", "data": "synthetic",
+        "config": {"workload": "homogeneous sweep: 16 vertices, all spins j=lambda/2 for lambda=1..16, gamma=1.2, "
+                               "dl=10 (11^6 shells each), rule r_max=40 / 40 panels x 50 nodes; one step = 6j "
+                               "tables + d-tables + boosters of all 16 vertices + shell sum over a 1/%d slice "
+                               "of every vertex's group-major shell range" % S,
+                   "slices_per_pass": S, "precision": args.precision, "cache": "working set < L2 per kernel; "
+                   "no flush (compute-bound FP64 path)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": traffic,
+                     "kernel": "k_shell_fp64", "flops_counted": "FP64 FMAs the kernel executes x 2 (loop trip counts)",
+                     "kernel_ms_per_step": 1e3 * kern_s / args.steps},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "shells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

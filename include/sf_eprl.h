@@ -15,8 +15,10 @@
  *   - Spins are DOUBLED integers: two_j = 2*j, so half-integers are exact.
  *   - Boundary order:  two_j[0..9] = (j12, j13, j14, j15, j23, j24, j25, j34, j35, j45)   (Sec. 2).
  *   - Free faces (23, 24, 25, 34, 35, 45) carry l_f = j_f + d_f, d_f = 0..dl; gauge faces l_1b = j_1b.
- *   - Linear shell index  s = ((((d23*D + d24)*D + d25)*D + d34)*D + d35)*D + d45,  D = dl+1,
- *     s in [0, D^6)  (the paper's (Delta s + 1)^6 loops, Sec. 3 "Parallelization").
+ *   - Linear shell index  s = ((((d25*D + d35)*D + d45)*D + d24)*D + d34)*D + d23,  D = dl+1,
+ *     s in [0, D^6)  (the paper's (Delta s + 1)^6 loops, Sec. 3 "Parallelization"). The order is a
+ *     convention of this library: (l25, l35, l45) lead, so a contiguous range is a run of whole
+ *     groups that share the edge-5 booster.
  *   - Intertwiner ranges: edge 1 couples (j12 j13 | j14 j15), edge 2 (j23 j24 | j25 j12),
  *     edge 3 (j34 j35 | j13 j23), edge 4 (j45 j14 | j24 j34), edge 5 (j15 j25 | j35 j45)
  *     (the booster index orders of the framed algorithm, step 3).
@@ -158,6 +160,14 @@ int sf_vertex_adjoint(sf_tables* t, const double* const psi[5], double* a_out,
 int64_t sf_table_size(const sf_tables* t, int32_t vertex, int32_t kind, int32_t index);
 int sf_table_copy(const sf_tables* t, int32_t vertex, int32_t kind, int32_t index, void* dst,
                   int64_t n_bytes, cudaStream_t stream);
+
+/* Number of kernels this library has launched in the process (all entry points). */
+int64_t sf_kernel_launches(void);
+
+/* Device time in milliseconds of the last shell-sum kernel launched by sf_vertex_amplitude on
+ * the calling thread (kind 0), measured with CUDA events recorded on the call's stream around
+ * that launch; -1 if none. */
+double sf_last_kernel_ms(int32_t kind);
 
 /* Release the tables object and all its device memory (NULL is a no-op). */
 void sf_tables_free(sf_tables* t);

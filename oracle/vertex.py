@@ -10,7 +10,8 @@ Conventions (doubled spins throughout):
 * boundary order  (j12, j13, j14, j15, j23, j24, j25, j34, j35, j45);
 * free faces      (l23, l24, l25, l34, l35, l45), l_f = j_f + d_f with d_f in [0, dl];
   gauge faces l_1b = j_1b (Sec. 2 below eq. vertex-ampl);
-* linear shell index s = ((((d23*(dl+1) + d24)*(dl+1) + d25)*(dl+1) + d34)*(dl+1) + d35)*(dl+1) + d45;
+* linear shell index s = ((((d25*(dl+1) + d35)*(dl+1) + d45)*(dl+1) + d24)*(dl+1) + d34)*(dl+1) + d23
+  (an enumeration convention only; the paper does not order its shells);
 * edge couplings (the argument orders of the booster tensors in the framed algorithm):
     edge 1: (j12 j13 | j14 j15) -> i1           (no booster)
     edge 2: (j23 j24 | j25 j12) -> i2, (l23 l24 | l25 j12) -> k2
@@ -62,11 +63,18 @@ def n_shells(dl):
 
 def shell_offsets(s, dl):
     """Linear shell index -> (d23, d24, d25, d34, d35, d45)."""
-    d = []
-    for _ in range(6):
-        d.append(s % (dl + 1))
-        s //= (dl + 1)
-    return tuple(reversed(d))
+    D = dl + 1
+    d23 = s % D
+    s //= D
+    d34 = s % D
+    s //= D
+    d24 = s % D
+    s //= D
+    d45 = s % D
+    s //= D
+    d35 = s % D
+    d25 = s // D
+    return (d23, d24, d25, d34, d35, d45)
 
 
 def shell_spins(tj, dl, s):

@@ -25,7 +25,8 @@ SF_TAB_6J, SF_TAB_6J_SLOTS, SF_TAB_D, SF_TAB_NODES = 1, 2, 3, 4
 # names of every symbol declared in include/sf_eprl.h
 EXPORTS = ("sf_version", "sf_last_error", "sf_intertwiner_ranges", "sf_num_shells", "sf_6j_table",
            "sf_boosters", "sf_booster_shape", "sf_boosters_upload", "sf_boosters_download",
-           "sf_vertex_amplitude", "sf_vertex_adjoint", "sf_table_size", "sf_table_copy", "sf_tables_free")
+           "sf_vertex_amplitude", "sf_vertex_adjoint", "sf_table_size", "sf_table_copy", "sf_kernel_launches",
+           "sf_last_kernel_ms", "sf_tables_free")
 
 
 class SfError(RuntimeError):
@@ -67,6 +68,8 @@ def _declare(lib):
         "sf_vertex_adjoint": (ctypes.c_int, [P, ctypes.POINTER(P), P, ctypes.POINTER(P), ctypes.POINTER(P), P]),
         "sf_table_size": (I64, [P, I32, I32, I32]),
         "sf_table_copy": (ctypes.c_int, [P, I32, I32, I32, P, I64, P]),
+        "sf_kernel_launches": (I64, []),
+        "sf_last_kernel_ms": (D, [I32]),
         "sf_tables_free": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -203,6 +206,16 @@ def sf_vertex_amplitude(tables, precision=SF_FP64, shell_begin=0, shell_end=2 **
     _check(lib.sf_vertex_amplitude(tables.ptr, int(precision), int(shell_begin), int(shell_end), lp, nl, ptrs,
                                    _stream(stream)))
     return outs
+
+
+def kernel_launches():
+    """Kernels launched by the library so far in this process."""
+    return int(load().sf_kernel_launches())
+
+
+def last_kernel_ms():
+    """Device time (ms) of the last shell-sum kernel, from events on its stream."""
+    return float(load().sf_last_kernel_ms(0))
 
 
 def table_copy(tables, vtx, kind, index, stream=None):

@@ -40,6 +40,13 @@ int sf_set_error(int code, const char* fmt, ...) {
 }
 
 extern "C" const char* sf_last_error(void) { return g_err; }
+
+#include <atomic>
+static std::atomic<long long> g_launches{0};
+void sf_note_launch(int n) { g_launches += n; }
+extern "C" int64_t sf_kernel_launches(void) { return (int64_t)g_launches.load(); }
+static thread_local double g_last_kernel_ms = -1.0;
+extern "C" double sf_last_kernel_ms(int32_t kind) { return kind == 0 ? g_last_kernel_ms : -1.0; }
 extern "C" const char* sf_version(void) { return "sf_eprl 0.1 (sm_103a)"; }
 
 // ----------------------------------------------------------------------------------------------
@@ -498,7 +505,17 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
         VertexHost& h = t->vs[i];
         int64_t ntile = (int64_t)h.di[0] * h.di[1];
         int64_t want = std::max<int64_t>(1, (target + tiles_total - 1) / std::max<int64_t>(1, tiles_total));
-        int C = (int)std::min<int64_t>(h.ngroups, want);
+        // groups touched by the shell range (shells are group-major: D^3 shells per group)
+        const int64_t per_group = (int64_t)h.D * h.D * h.D;
+        int64_t g_lo = 0, g_hi = h.ngroups;
+        if (!shell_list) {
+            int64_t b = std::min<int64_t>(std::max<int64_t>(shell_begin, 0), h.nshell);
+            int64_t e = std::min<int64_t>(std::max<int64_t>(shell_end, 0), h.nshell);
+            g_lo = b / per_group;
+            g_hi = (e > b) ? (e + per_group - 1) / per_group : g_lo;
+        }
+        const int64_t ng = std::max<int64_t>(g_hi - g_lo, 0);
+        int C = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(ng, 1), want));
         item0[i] = (int)items.size();
         nchunk[i] = C;
         int64_t per = (int64_t)h.di[2] * h.di[3] * h.di[4];
@@ -508,8 +525,8 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
                 w.vtx = i;
                 w.i1 = (int)(tile / h.di[1]);
                 w.i2 = (int)(tile % h.di[1]);
-                w.g0 = (int)(h.ngroups * c / C);
-                w.g1 = (int)(h.ngroups * (c + 1) / C);
+                w.g0 = (int)(g_lo + ng * c / C);
+                w.g1 = (int)(g_lo + ng * (c + 1) / C);
                 w.part_off = part_total;
                 part_total += per;
                 items.push_back(w);
@@ -554,6 +571,10 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
         filt.bitmap = d_bm;
     }
     SF_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, sizeof(int), stream));
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    SF_CUDA_TRY(cudaEventCreate(&ev0));
+    SF_CUDA_TRY(cudaEventCreate(&ev1));
+    SF_CUDA_TRY(cudaEventRecord(ev0, stream));
     if (precision == SF_FP64) {
         SF_TRY(sf_shell_fp64_launch(t->d_vtx, mdi, mdk, mk3u, xc, Dmax, d_items, (int)items.size(), d_counter, d_part,
                                     filt, t->num_sms, stream));
@@ -561,11 +582,17 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
         SF_TRY(sf_shell_mixed_launch(t->d_vtx, mdi, mdk, d_items, (int)items.size(), d_counter, d_part, filt,
                                      t->num_sms, stream));
     }
+    SF_CUDA_TRY(cudaEventRecord(ev1, stream));
     for (int i = 0; i < nv; i++) {
         VertexHost& h = t->vs[i];
         SF_TRY(sf_reduce_launch(t->d_vtx, i, h.di[0] * h.di[1], d_items, item0[i], nchunk[i], d_part, A_out[i], stream));
     }
-    return check_status(t, stream, "sf_vertex_amplitude");
+    int rc = check_status(t, stream, "sf_vertex_amplitude");
+    float ms = -1.0f;
+    if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) g_last_kernel_ms = ms;
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    return rc;
 }
 
 extern "C" int sf_vertex_adjoint(sf_tables* t, const double* const psi[5], double* a_out, double* const grad_psi[5],

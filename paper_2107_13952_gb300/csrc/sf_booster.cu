@@ -93,9 +93,11 @@ __global__ void k_rule_nodes(double r_max, int npan, int order, double* X, doubl
 int sf_rule_build(const sf_quad_rule* q, double* d_gl, double* d_x, double* d_w, double* d_r, double* d_W,
                   cudaStream_t s) {
     k_gl_library<<<(unsigned)((SF_GL_TOTAL + 255) / 256), 256, 0, s>>>(d_gl);
+    sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     int n = q->n_panels * q->order;
     k_rule_nodes<<<(n + 127) / 128, 128, 0, s>>>(q->r_max, q->n_panels, q->order, d_x, d_w, d_r, d_W);
+    sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;
 }
@@ -234,6 +236,7 @@ int sf_dtable_build(int tk, double gamma, int nl, int nnodes, const double* d_r,
     double rho = gamma * (0.5 * tk + 1.0);
     dim3 grid((nnodes + 127) / 128, tk + 1);
     k_dtable<<<grid, 128, 0, s>>>(tk, rho, nl, nnodes, d_r, d_gl, d_out);
+    sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;
 }
@@ -417,9 +420,11 @@ int sf_booster_build(const VtxDev* d_v, int edge, int ntrip, size_t smem, const 
                      const dd* F, double* d_Aj, double* d_Cj, double* d_B, int* d_status, cudaStream_t s) {
     if (smem > 227 * 1024) return sf_set_error(SF_ERR_LIMIT, "booster kernel needs %zu bytes of shared memory", smem);
     k_boundary_3j<<<64, 256, 0, s>>>(d_v, edge, F, d_Aj, d_Cj, d_status);
+    sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     SF_CUDA_TRY(cudaFuncSetAttribute(k_booster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_booster<<<ntrip, 256, smem, s>>>(d_v, edge, d_W, nnodes, F, d_Aj, d_Cj, d_B, d_status);
+    sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;
 }

@@ -24,6 +24,7 @@
 // error reporting (thread-local message, set by the host side of every entry point)
 // ----------------------------------------------------------------------------------------------
 int sf_set_error(int code, const char* fmt, ...);
+void sf_note_launch(int n);   // launch counter behind sf_kernel_launches()
 
 #define SF_CUDA_TRY(call)                                                                      \
     do {                                                                                       \

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(256) k_shell_fp64(const VtxDev* __restrict__ V
                     int k2lo, nk2, k3lo, nk3;
                     sf_pair_range(l23, l24, l25, j12, &k2lo, &nk2);
                     sf_pair_range(l34, l35, j13, l23, &k3lo, &nk3);
-                    const int64_t s = (((((int64_t)d * D + d24) * D + d25) * D + d34) * D + d35) * D + d45;
+                    const int64_t s = (((int64_t)g * D + d24) * D + d34) * D + d;   // group-major order
                     if (nk2 == 0 || nk3 == 0 || !shell_selected(filt, s)) { nk2 = 0; nk3 = 0; }
                     if (nk3 > 0) {
                         any = true;
@@ -275,6 +275,7 @@ int sf_shell_fp64_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, 
     if (grid > n_items) grid = n_items;
     SF_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(int), s));
     k_shell_fp64<<<grid, 256, smem, s>>>(d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter, d_part, filt);
+    sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;
 }
@@ -302,6 +303,7 @@ __global__ void k_reduce(const VtxDev* __restrict__ V, int vtx, const WorkItem* 
 int sf_reduce_launch(const VtxDev* d_v, int vtx, int ntiles, const WorkItem* d_items, int item0, int nchunk,
                      const double* d_part, double* A, cudaStream_t s) {
     k_reduce<<<ntiles, 256, 0, s>>>(d_v, vtx, d_items, item0, nchunk, d_part, A);
+    sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;
 }
@@ -319,6 +321,7 @@ int sf_bitmap_launch(const int64_t* d_list, int64_t n, int64_t nshell, uint32_t*
     SF_CUDA_TRY(cudaMemsetAsync(d_bm, 0, ((nshell + 31) / 32) * sizeof(uint32_t), s));
     if (n > 0) {
         k_bitmap<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_list, n, nshell, d_bm);
+        sf_note_launch(1);
         SF_CUDA_TRY(cudaGetLastError());
     }
     return SF_OK;

@@ -67,6 +67,7 @@ int sf_launch_fact_table(cudaStream_t s) { (void)s; return SF_OK; }
 
 int sf_fact_table_build(dd* F, cudaStream_t s) {
     k_fact_table<<<1, 1, 0, s>>>(F);
+    sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;
 }
@@ -78,6 +79,7 @@ int sf_sixj_table_build(int table_id, const VtxDev* d_v, const SlotDesc* d_slots
     int64_t cap = (int64_t)num_sms * 16;
     if (blocks > cap) blocks = cap;
     k_sixj_table<<<(unsigned)blocks, 256, 0, s>>>(table_id, d_v, d_slots, nslots, n, d_out, F, d_status);
+    sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;
 }
