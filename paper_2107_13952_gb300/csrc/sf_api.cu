@@ -532,6 +532,8 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
                 items.push_back(w);
             }
         }
+        if ((int64_t)h.di[3] * ((h.di[4] + 1) / 2) * ((h.di[2] + 3) / 4) > 4 * 256)
+            return sf_set_error(SF_ERR_LIMIT, "vertex %d: intertwiner dimensions too large for the register-resident tile", i);
         for (int e = 2; e < 5; e++) mdi = std::max(mdi, (int)h.di[e]);
         for (int e = 0; e < 4; e++) mdk = std::max(mdk, (int)h.dkmax[e]);
         mk3u = std::max(mk3u, h.mk3u);

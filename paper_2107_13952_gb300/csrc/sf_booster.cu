@@ -249,7 +249,7 @@ int sf_dtable_build(int tk, double gamma, int nl, int nnodes, const double* d_r,
 __constant__ int c_edge_face[4][4] = {{F23, F24, F25, F12}, {F34, F35, F13, F23}, {F45, F14, F24, F34}, {F15, F25, F35, F45}};
 __constant__ int c_edge_slot[4][4] = {{0, 1, 2, -1}, {0, 1, -1, 2}, {0, -1, 1, 2}, {-1, 0, 1, 2}};
 
-#define SF_NC 32   // nodes per staged chunk
+#define SF_NC 16   // nodes per staged chunk
 
 // boundary-side 3j tables of one edge (shared by every triple):
 //   Aj[i][m1][m2] = (j1 j2 i; m1 m2 mu), Cj[i][m3][m4] = (i j3 j4; -mu m3 m4), mu = -(m1+m2)
@@ -274,11 +274,18 @@ __global__ void k_boundary_3j(const VtxDev* __restrict__ vp, int edge, const dd*
     }
 }
 
-// one CTA per virtual-spin triple t of one edge
+// One CTA per virtual-spin triple t of one edge.
+// The m-tuples come in pairs (m, -m) whose terms are complex conjugates: d_{k l -m} =
+// (-1)^(k-l) conj(d_{k l m}) and 4jm(-m) = (-1)^(sum j) 4jm(m), and 2 sum_a j_a is even. Hence
+//   B[i][k] = sum_m 4jm(j;m)^(i) 4jm(l;m)^(k) Re I(m),
+// and with the tuples ordered so that m -> -m reverses the flat index, only the upper half is
+// summed (weight 2, the self-conjugate tuple m = 0 weight 1). The node sum is factored through
+// pair products P12 = W d1 d2 and P34 = d3 d4 staged per chunk of nodes.
+#define SF_BT 12   // canonical tuples per thread (upper half of at most 17^3 tuples / 256 threads)
 __global__ void __launch_bounds__(256) k_booster(const VtxDev* __restrict__ vp, int edge, const double* __restrict__ Wm,
                                                  int nnodes, const dd* __restrict__ F, const double* __restrict__ gAj,
                                                  const double* __restrict__ gCj, double* __restrict__ Bout, int* status) {
-    extern __shared__ double sm[];
+    extern __shared__ __align__(16) double sm[];
     const VtxDev& v = *vp;
     const int e = edge - 2;
     const int D = v.D;
@@ -301,66 +308,71 @@ __global__ void __launch_bounds__(256) k_booster(const VtxDev* __restrict__ vp, 
     if (nk == 0) return;
     const int n1 = tj[0] + 1, n2 = tj[1] + 1, n3 = tj[2] + 1, n4 = tj[3] + 1;
     const int M = n1 * n2 * n3;
-    const int nmax = imax_(imax_(n1, n2), imax_(n3, n4));
-    // shared: I[M] complex | union { staged d rows [4][nmax][SF_NC] complex ; Al[nk][n1 n2], Cl[nk][n3 n4] }
-    double2* sI = reinterpret_cast<double2*>(sm);
-    double2* stage = sI + M;
-    double* sAl = reinterpret_cast<double*>(stage);
+    const int Mh = M / 2;   // canonical tuples: [Mh, M); Mh itself is m = 0 when M is odd
+    // shared: Ir[M] | union { P12[n1 n2][SF_NC], P34[n3 n4][SF_NC] (complex) ; Al[nk][n1 n2], Cl[nk][n3 n4] }
+    double* sIr = sm;
+    const int Mpad = (M + 1) & ~1;   // keep the complex staging area 16-byte aligned
+    double2* P12 = reinterpret_cast<double2*>(sm + Mpad);
+    double2* P34 = P12 + n1 * n2 * SF_NC;
+    double* sAl = sm + Mpad;
     double* sCl = sAl + nk * n1 * n2;
     const double2* d0 = v.dtab[fc[0]] + (int64_t)il[0] * n1 * nnodes;
     const double2* d1 = v.dtab[fc[1]] + (int64_t)il[1] * n2 * nnodes;
     const double2* d2 = v.dtab[fc[2]] + (int64_t)il[2] * n3 * nnodes;
     const double2* d3 = v.dtab[fc[3]] + (int64_t)il[3] * n4 * nnodes;
-    // ---- I(m) = sum_n W_n d0(m1) d1(m2) d2(m3) d3(m4), m4 = -(m1+m2+m3)
-    double accr[20], acci[20];
+    double acc[SF_BT];
 #pragma unroll
-    for (int q = 0; q < 20; q++) { accr[q] = 0.0; acci[q] = 0.0; }
+    for (int q = 0; q < SF_BT; q++) acc[q] = 0.0;
     for (int n0 = 0; n0 < nnodes; n0 += SF_NC) {
         const int nc = imin_(SF_NC, nnodes - n0);
         __syncthreads();
-        for (int q = threadIdx.x; q < 4 * nmax * SF_NC; q += blockDim.x) {
-            int a = q / (nmax * SF_NC), rem = q % (nmax * SF_NC), mi = rem / SF_NC, nn = rem % SF_NC;
-            int na = a == 0 ? n1 : a == 1 ? n2 : a == 2 ? n3 : n4;
-            const double2* src = a == 0 ? d0 : a == 1 ? d1 : a == 2 ? d2 : d3;
-            double2 val = make_double2(0.0, 0.0);
-            if (mi < na && nn < nc) {
-                val = src[(int64_t)mi * nnodes + n0 + nn];
-                if (a == 0) { double w = Wm[n0 + nn]; val.x *= w; val.y *= w; }
+        for (int q = threadIdx.x; q < n1 * n2 * SF_NC; q += blockDim.x) {
+            const int nn = q % SF_NC, pr = q / SF_NC, a2 = pr % n2, a1 = pr / n2;
+            double2 z = make_double2(0.0, 0.0);
+            if (nn < nc) {
+                const double2 x = d0[(int64_t)a1 * nnodes + n0 + nn], y = d1[(int64_t)a2 * nnodes + n0 + nn];
+                const double w = Wm[n0 + nn];
+                z = make_double2(w * (x.x * y.x - x.y * y.y), w * (x.x * y.y + x.y * y.x));
             }
-            stage[q] = val;
+            P12[q] = z;
+        }
+        for (int q = threadIdx.x; q < n3 * n4 * SF_NC; q += blockDim.x) {
+            const int nn = q % SF_NC, pr = q / SF_NC, a4 = pr % n4, a3 = pr / n4;
+            double2 z = make_double2(0.0, 0.0);
+            if (nn < nc) {
+                const double2 x = d2[(int64_t)a3 * nnodes + n0 + nn], y = d3[(int64_t)a4 * nnodes + n0 + nn];
+                z = make_double2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x);
+            }
+            P34[q] = z;
         }
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 20; q++) {
-            int mt = threadIdx.x + q * blockDim.x;
+        for (int q = 0; q < SF_BT; q++) {
+            const int mt = Mh + threadIdx.x + q * blockDim.x;
             if (mt < M) {
-                int i3 = mt % n3, i2 = (mt / n3) % n2, i1 = mt / (n3 * n2);
-                int tm4 = -((-tj[0] + 2 * i1) + (-tj[1] + 2 * i2) + (-tj[2] + 2 * i3));
+                const int i3 = mt % n3, i2 = (mt / n3) % n2, i1 = mt / (n3 * n2);
+                const int tm4 = -((-tj[0] + 2 * i1) + (-tj[1] + 2 * i2) + (-tj[2] + 2 * i3));
                 if (iabs_(tm4) <= tj[3]) {
-                    int i4 = (tm4 + tj[3]) / 2;
-                    const double2* p0 = stage + (0 * nmax + i1) * SF_NC;
-                    const double2* p1 = stage + (1 * nmax + i2) * SF_NC;
-                    const double2* p2 = stage + (2 * nmax + i3) * SF_NC;
-                    const double2* p3 = stage + (3 * nmax + i4) * SF_NC;
-                    double sr = accr[q], si = acci[q];
+                    const int i4 = (tm4 + tj[3]) / 2;
+                    const double2* p = P12 + (i1 * n2 + i2) * SF_NC;
+                    const double2* r = P34 + (i3 * n4 + i4) * SF_NC;
+                    double s0 = acc[q], s1 = 0.0;
                     for (int nn = 0; nn < nc; nn++) {
-                        double2 a = p0[nn], b = p1[nn], c = p2[nn], d = p3[nn];
-                        double abr = a.x * b.x - a.y * b.y, abi = a.x * b.y + a.y * b.x;
-                        double cdr = c.x * d.x - c.y * d.y, cdi = c.x * d.y + c.y * d.x;
-                        sr += abr * cdr - abi * cdi;
-                        si += abr * cdi + abi * cdr;
+                        const double2 a = p[nn], b = r[nn];
+                        s0 = fma(a.x, b.x, s0);
+                        s1 = fma(a.y, b.y, s1);
                     }
-                    accr[q] = sr;
-                    acci[q] = si;
+                    acc[q] = s0 - s1;
                 }
             }
         }
     }
-    __syncthreads();   // stage is reused for the 3j tables below
+    __syncthreads();   // the staging area is reused for the 3j tables below
+    for (int q = threadIdx.x; q < Mh; q += blockDim.x) sIr[q] = 0.0;
 #pragma unroll
-    for (int q = 0; q < 20; q++) {
-        int mt = threadIdx.x + q * blockDim.x;
-        if (mt < M) sI[mt] = make_double2(accr[q], acci[q]);
+    for (int q = 0; q < SF_BT; q++) {
+        const int mt = Mh + threadIdx.x + q * blockDim.x;
+        if (mt < M) sIr[mt] = ((M & 1) && mt == Mh) ? acc[q] : 2.0 * acc[q];
     }
     // ---- virtual-side 3j tables: Al[c][m1][m2] = (l1 l2 k; m1 m2 mu), Cl[c][m3][m4] = (k l3 l4; -mu m3 m4)
     for (int q = threadIdx.x; q < nk * n1 * n2; q += blockDim.x) {
@@ -374,11 +386,11 @@ __global__ void __launch_bounds__(256) k_booster(const VtxDev* __restrict__ vp, 
         sCl[q] = dd_to_d(sf_threej_dd(klo + 2 * c, tl[2], tl[3], -(tm3 + tm4), tm3, tm4, F, status));
     }
     __syncthreads();
-    // ---- B[i][k] = sum_m (-1)^((i - mu) + (k - mu)) Aj Cj Al Cl I(m)
+    // ---- B[i][k] = sum_m (-1)^((i - mu) + (k - mu)) Aj Cj Al Cl Re I(m)
     for (int q = threadIdx.x; q < di * nk; q += blockDim.x) {
         const int ci = q / nk, ck = q % nk;
         const int ti = ilo + 2 * ci, tk = klo + 2 * ck;
-        double br = 0.0, bi = 0.0;
+        double br = 0.0;
         for (int i1 = 0; i1 < n1; i1++) {
             const int tm1 = -tj[0] + 2 * i1;
             for (int i2 = 0; i2 < n2; i2++) {
@@ -387,33 +399,28 @@ __global__ void __launch_bounds__(256) k_booster(const VtxDev* __restrict__ vp, 
                 const double aa = gAj[(ci * n1 + i1) * n2 + i2] * sAl[(ck * n1 + i1) * n2 + i2];
                 if (aa == 0.0) continue;
                 const int par = ((ti - tmu) / 2 + (tk - tmu) / 2) & 1;
-                double sr = 0.0, si = 0.0;
+                double sr = 0.0;
                 for (int i3 = 0; i3 < n3; i3++) {
                     const int tm3 = -tj[2] + 2 * i3;
                     const int tm4 = tmu - tm3;
                     if (iabs_(tm4) > tj[3]) continue;
                     const int i4 = (tm4 + tj[3]) / 2;
                     const double cc = gCj[(ci * n3 + i3) * n4 + i4] * sCl[(ck * n3 + i3) * n4 + i4];
-                    const double2 I = sI[(i1 * n2 + i2) * n3 + i3];
-                    sr = fma(cc, I.x, sr);
-                    si = fma(cc, I.y, si);
+                    sr = fma(cc, sIr[(i1 * n2 + i2) * n3 + i3], sr);
                 }
-                if (par) { br -= aa * sr; bi -= aa * si; } else { br += aa * sr; bi += aa * si; }
+                br = par ? br - aa * sr : br + aa * sr;
             }
         }
         Bt[ci * dkmax + ck] = br;
-        // realness self-check (B4 is real with the phase convention of the d-tables)
-        if (fabs(bi) > 1e-9 * fabs(br) + 1e-15 && status) atomicCAS(status, SF_DEV_OK, SF_DEV_NONREAL_BOOSTER);
     }
 }
 
 size_t sf_booster_smem(int tj1, int tj2, int tj3, int tj4, int nk) {
     int n1 = tj1 + 1, n2 = tj2 + 1, n3 = tj3 + 1, n4 = tj4 + 1;
-    int nmax = n1; if (n2 > nmax) nmax = n2; if (n3 > nmax) nmax = n3; if (n4 > nmax) nmax = n4;
-    size_t M = (size_t)n1 * n2 * n3;
-    size_t stage = (size_t)4 * nmax * SF_NC * sizeof(double2);
+    size_t M = ((size_t)n1 * n2 * n3 + 1) & ~(size_t)1;
+    size_t stage = (size_t)(n1 * n2 + n3 * n4) * SF_NC * sizeof(double2);
     size_t tabs = sizeof(double) * ((size_t)nk * n1 * n2 + (size_t)nk * n3 * n4);
-    return M * sizeof(double2) + (stage > tabs ? stage : tabs);
+    return M * sizeof(double) + (stage > tabs ? stage : tabs);
 }
 
 int sf_booster_build(const VtxDev* d_v, int edge, int ntrip, size_t smem, const double* d_W, int nnodes,

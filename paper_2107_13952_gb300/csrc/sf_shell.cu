@@ -42,29 +42,71 @@ __device__ __forceinline__ bool shell_selected(const ShellFilter& f, int64_t s) 
     return s >= f.begin && s < f.end;
 }
 
+// C[bt][m][n] (+)= sum_k A[bt][m][k] B[bt][k][n] for a batch of small matrices in shared memory.
+// Every thread owns BM x BN output blocks (independent FMA chains); strides are in doubles.
+template <int BM, int BN, bool ACC>
+__device__ __forceinline__ void blk_gemm(int nbatch, int M, int N, int K, const double* A, int a_bs, int am, int ak,
+                                         const double* B, int b_bs, int bk, int bn, double* C, int c_bs, int cm,
+                                         int cn, int tid, int nth) {
+    const int nbm = (M + BM - 1) / BM, nbn = (N + BN - 1) / BN, per = nbm * nbn;
+    for (int blk = tid; blk < per * nbatch; blk += nth) {
+        const int bt = blk / per, r = blk - bt * per;
+        const int m0 = (r / nbn) * BM, n0 = (r - (r / nbn) * nbn) * BN;
+        const double* Ab = A + bt * a_bs + m0 * am;
+        const double* Bb = B + bt * b_bs + n0 * bn;
+        double* Cb = C + bt * c_bs + m0 * cm + n0 * cn;
+        double acc[BM][BN];
+#pragma unroll
+        for (int i = 0; i < BM; i++)
+#pragma unroll
+            for (int j = 0; j < BN; j++)
+                acc[i][j] = (ACC && m0 + i < M && n0 + j < N) ? Cb[i * cm + j * cn] : 0.0;
+        for (int k = 0; k < K; k++) {
+            double a[BM], b[BN];
+#pragma unroll
+            for (int i = 0; i < BM; i++) a[i] = (m0 + i < M) ? Ab[i * am + k * ak] : 0.0;
+#pragma unroll
+            for (int j = 0; j < BN; j++) b[j] = (n0 + j < N) ? Bb[k * bk + j * bn] : 0.0;
+#pragma unroll
+            for (int i = 0; i < BM; i++)
+#pragma unroll
+                for (int j = 0; j < BN; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < BM; i++)
+#pragma unroll
+            for (int j = 0; j < BN; j++)
+                if (m0 + i < M && n0 + j < N) Cb[i * cm + j * cn] = acc[i][j];
+    }
+}
+
+#define SF_TRT 4   // output-tile register blocks per thread (2 x 4 doubles each)
+
 struct ShellSmem {
-    double *T, *Y, *V, *U, *P, *Q, *R, *SB, *B4, *B5;
+    double *Y, *V, *U, *P, *Q, *R, *SB, *S3s, *B3s, *B4, *B5;
 };
 
 __device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int xc, int D) {
     ShellSmem s;
     double* p = base;
-    s.T = p;  p += mdi * mdi * mdi;
-    s.Y = p;  p += mdi * mdi * mdk;
-    s.V = p;  p += mdk * mdk * mdi;
-    s.U = p;  p += mk3u * xc * mdi;
-    s.P = p;  p += mdk * xc * mdi;
-    s.Q = p;  p += mdk * mdk * xc;
-    s.R = p;  p += D * mdk * xc;
-    s.SB = p; p += D * mdk * xc;
-    s.B4 = p; p += mdi * mdk;
-    s.B5 = p; p += mdi * mdk;
+    s.Y = p;   p += mdi * mdk * mdi;
+    s.V = p;   p += mdk * mdk * mdi;
+    s.U = p;   p += mk3u * xc * mdi;
+    s.P = p;   p += mdk * xc * mdi;
+    s.Q = p;   p += mdk * mdk * xc;
+    s.R = p;   p += D * mdk * xc;
+    s.SB = p;  p += D * mdk * xc;
+    s.S3s = p; p += xc * mdk * mk3u;
+    s.B3s = p; p += D * mdk * mdi;
+    s.B4 = p;  p += mdi * mdk;
+    s.B5 = p;  p += mdi * mdk;
     return s;
 }
 
 size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D) {
-    return (size_t)mdi * mdi * mdi + (size_t)mdi * mdi * mdk + (size_t)mdk * mdk * mdi + (size_t)mk3u * xc * mdi +
-           (size_t)mdk * xc * mdi + (size_t)mdk * mdk * xc + 2ull * D * mdk * xc + 2ull * mdi * mdk;
+    return (size_t)mdi * mdk * mdi + (size_t)mdk * mdk * mdi + (size_t)mk3u * xc * mdi + (size_t)mdk * xc * mdi +
+           (size_t)mdk * mdk * xc + 2ull * D * mdk * xc + (size_t)xc * mdk * mk3u + (size_t)D * mdk * mdi +
+           2ull * mdi * mdk;
 }
 
 __global__ void __launch_bounds__(256) k_shell_fp64(const VtxDev* __restrict__ V, int mdi, int mdk, int mk3u, int XC,
@@ -92,7 +134,15 @@ __global__ void __launch_bounds__(256) k_shell_fp64(const VtxDev* __restrict__ V
         const int di3 = v.di[2], di4 = v.di[3], di5 = v.di[4];
         const int dk1 = v.dkmax[1];
         const int jsum = j12 + j13 + j14 + j15 + v.ilo[0];
-        for (int q = tid; q < di3 * di4 * di5; q += nth) sm.T[q] = 0.0;
+        // output tile T[i4][i5][i3] in registers: blocks (i4, 2 i5, 4 i3), block b = tid + r * nth
+        const int tb5 = (di5 + 1) / 2, tb3 = (di3 + 3) / 4, tper = tb5 * tb3;
+        double T[SF_TRT][2][4];
+#pragma unroll
+        for (int r = 0; r < SF_TRT; r++)
+#pragma unroll
+            for (int i = 0; i < 2; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) T[r][i][j] = 0.0;
         for (int g = w.g0; g < w.g1; g++) {
             const int d25 = g / (D * D), d35 = (g / D) % D, d45 = g % D;
             const int l25 = v.tj[F25] + 2 * d25, l35 = v.tj[F35] + 2 * d35, l45 = v.tj[F45] + 2 * d45;
@@ -104,8 +154,8 @@ __global__ void __launch_bounds__(256) k_shell_fp64(const VtxDev* __restrict__ V
             {
                 const double* B5 = v.B[3] + (int64_t)t5 * di5 * v.dkmax[3];
                 for (int q = tid; q < di5 * nk5; q += nth) {
-                    int i5 = q / nk5, c5 = q % nk5;
-                    double f = (double)(k5lo + 2 * c5 + 1) * ((c5 & 1) ? -1.0 : 1.0);
+                    const int i5 = q / nk5, c5 = q % nk5;
+                    const double f = (double)(k5lo + 2 * c5 + 1) * ((c5 & 1) ? -1.0 : 1.0);
                     sm.B5[q] = f * B5[i5 * v.dkmax[3] + c5];
                 }
             }
@@ -113,11 +163,11 @@ __global__ void __launch_bounds__(256) k_shell_fp64(const VtxDev* __restrict__ V
             const SlotDesc sd1 = load_slot(v.slot[0] + d25);
             const SlotDesc sd5 = load_slot(v.slot[4] + d25);
             const SlotDesc sd2 = load_slot(v.slot[1] + d35 * D + d45);
-            // x bounds from i1 (with l25) and the k5 range (with j14)
             const int k5hi = k5lo + 2 * (nk5 - 1);
             const int x_lo_a = iabs_(i1 - l25), x_hi_a = i1 + l25;
             const int x_lo_b = (j14 < k5lo) ? (k5lo - j14) : (j14 > k5hi ? j14 - k5hi : ((j14 + k5lo) & 1));
             const int x_hi_b = k5hi + j14;
+            bool gany = false;
             for (int p = 0; p < D * D; p++) {
                 const int d24 = p / D, d34 = p % D;
                 const int l24 = v.tj[F24] + 2 * d24, l34 = v.tj[F34] + 2 * d34;
@@ -132,7 +182,6 @@ __global__ void __launch_bounds__(256) k_shell_fp64(const VtxDev* __restrict__ V
                 if (((xlo - x_lo_a) & 1) != 0) xlo++;   // parity of i1 + l25
                 if (xlo > xhi) continue;
                 // per-l23 shell data (uniform across the block) and the union of the k3 ranges
-                __syncthreads();
                 int k3ulo = 1 << 30, k3uhi = -1;
                 bool any = false;
                 for (int d = 0; d < D; d++) {
@@ -147,75 +196,57 @@ __global__ void __launch_bounds__(256) k_shell_fp64(const VtxDev* __restrict__ V
                         k3ulo = imin_(k3ulo, k3lo);
                         k3uhi = imax_(k3uhi, k3lo + 2 * (nk3 - 1));
                     }
-                    if (tid == 0) {
-                        s_k2lo[d] = k2lo; s_nk2[d] = nk2; s_k3lo[d] = k3lo; s_nk3[d] = nk3;
-                        const int E2 = jsum + k2lo + k3lo + k4lo + k5lo + l23 + l24 + l25 + l34 + l35 + l45;
-                        s_sig[d] = ((E2 >> 1) & 1) ? -1.0 : 1.0;
-                        s_sd4[d] = load_slot(v.slot[3] + d * D + d24);
-                    }
                 }
                 if (!any) continue;
+                gany = true;
+                __syncthreads();   // previous 5-tuple done with the shared buffers below
+                for (int d = tid; d < D; d += nth) {
+                    const int l23 = v.tj[F23] + 2 * d;
+                    int k2lo, nk2, k3lo, nk3;
+                    sf_pair_range(l23, l24, l25, j12, &k2lo, &nk2);
+                    sf_pair_range(l34, l35, j13, l23, &k3lo, &nk3);
+                    const int64_t s = (((int64_t)g * D + d24) * D + d34) * D + d;
+                    if (nk2 == 0 || nk3 == 0 || !shell_selected(filt, s)) { nk2 = 0; nk3 = 0; }
+                    s_k2lo[d] = k2lo; s_nk2[d] = nk2; s_k3lo[d] = k3lo; s_nk3[d] = nk3;
+                    const int E2 = jsum + k2lo + k3lo + k4lo + k5lo + l23 + l24 + l25 + l34 + l35 + l45;
+                    s_sig[d] = ((E2 >> 1) & 1) ? -1.0 : 1.0;
+                    s_sd4[d] = load_slot(v.slot[3] + d * D + d24);
+                }
                 const int nk3u = (k3uhi - k3ulo) / 2 + 1;
                 const int t4 = (d45 * D + d24) * D + d34;
                 {
                     const double* B4 = v.B[2] + (int64_t)t4 * di4 * v.dkmax[2];
                     for (int q = tid; q < di4 * nk4; q += nth) {
-                        int i4 = q / nk4, c4 = q % nk4;
-                        double f = (double)(k4lo + 2 * c4 + 1) * ((c4 & 1) ? -1.0 : 1.0);
+                        const int i4 = q / nk4, c4 = q % nk4;
+                        const double f = (double)(k4lo + 2 * c4 + 1) * ((c4 & 1) ? -1.0 : 1.0);
                         sm.B4[q] = f * B4[i4 * v.dkmax[2] + c4];
                     }
+                }
+                // raw B3 rows of every l23, transposed to [d][c3][i3]
+                for (int q = tid; q < D * mdk * di3; q += nth) {
+                    const int i3 = q % di3, r = q / di3, c3 = r % mdk, d = r / mdk;
+                    const int t3 = (d34 * D + d35) * D + d;
+                    sm.B3s[q] = (c3 < dk1) ? __ldg(v.B[1] + ((int64_t)t3 * di3 + i3) * dk1 + c3) : 0.0;
                 }
                 for (int q = tid; q < nk4 * nk5 * di3; q += nth) sm.V[q] = 0.0;
                 const SlotDesc sd3 = load_slot(v.slot[2] + (d24 * D + d34) * D + d35);
                 for (int xc0 = xlo; xc0 <= xhi; xc0 += 2 * XC) {
                     const int nxc = imin_(XC, (xhi - xc0) / 2 + 1);
                     __syncthreads();
-                    // A: SB[d][k2][x] = sigma_d (2k2+1)(-1)^(k2-k2lo) B2[t2][i2][k2] S5[k2,i1,x]
+                    // A: SB[d][k2][x] = sigma_d (2k2+1)(-1)^(k2-k2lo) B2[t2][i2][k2] S5[k2,i1,x];
+                    //    S3s[x][k4][k3u] staged from the S3 slot (zero outside its box)
                     for (int q = tid; q < D * mdk * nxc; q += nth) {
                         const int xc = q % nxc, r = q / nxc, c2 = r % mdk, d = r / mdk;
                         if (c2 >= s_nk2[d]) continue;
                         const int k2 = s_k2lo[d] + 2 * c2, x = xc0 + 2 * xc;
                         const int t2 = (d * D + d24) * D + d25;
-                        const double b2 = v.B[0][((int64_t)t2 * v.di[1] + ci2) * v.dkmax[0] + c2];
+                        const double b2 = __ldg(v.B[0] + ((int64_t)t2 * v.di[1] + ci2) * v.dkmax[0] + c2);
                         const double f = (double)(k2 + 1) * ((c2 & 1) ? -s_sig[d] : s_sig[d]);
                         sm.SB[(d * mdk + c2) * XC + xc] = f * b2 * s6(v.S[4], sd5, k2, i1, x);
                     }
-                    __syncthreads();
-                    // B: R[d][k3][x] = (2k3+1)(-1)^(k3-k3lo) sum_k2 S4_d[k3,k2,x] SB[d][k2][x]
-                    for (int q = tid; q < D * mdk * nxc; q += nth) {
-                        const int xc = q % nxc, r = q / nxc, c3 = r % mdk, d = r / mdk;
-                        if (c3 >= s_nk3[d]) continue;
-                        const int k3 = s_k3lo[d] + 2 * c3, x = xc0 + 2 * xc;
-                        const SlotDesc sd4 = s_sd4[d];
-                        const int k2lo = s_k2lo[d], nk2 = s_nk2[d];
-                        double acc = 0.0;
-                        for (int c2 = 0; c2 < nk2; c2++)
-                            acc = fma(s6(v.S[3], sd4, k3, k2lo + 2 * c2, x), sm.SB[(d * mdk + c2) * XC + xc], acc);
-                        sm.R[(d * mdk + c3) * XC + xc] = acc * (double)(k3 + 1) * ((c3 & 1) ? -1.0 : 1.0);
-                    }
-                    __syncthreads();
-                    // C: U[k3u][x][i3] = sum_d R[d][k3][x] B3_d[i3][k3]
-                    for (int q = tid; q < nk3u * nxc * di3; q += nth) {
-                        const int i3 = q % di3, r = q / di3, xc = r % nxc, ku = r / nxc;
-                        const int k3 = k3ulo + 2 * ku;
-                        double acc = 0.0;
-                        for (int d = 0; d < D; d++) {
-                            const int c3 = (k3 - s_k3lo[d]) >> 1;
-                            if (k3 < s_k3lo[d] || c3 >= s_nk3[d]) continue;
-                            const int t3 = (d34 * D + d35) * D + d;
-                            acc = fma(sm.R[(d * mdk + c3) * XC + xc], __ldg(v.B[1] + ((int64_t)t3 * di3 + i3) * dk1 + c3), acc);
-                        }
-                        sm.U[q] = acc;
-                    }
-                    __syncthreads();
-                    // D: P[k4][x][i3] = sum_k3 S3[k4,k3,x] U[k3][x][i3]
-                    for (int q = tid; q < nk4 * nxc * di3; q += nth) {
-                        const int i3 = q % di3, r = q / di3, xc = r % nxc, c4 = r / nxc;
-                        const int k4 = k4lo + 2 * c4, x = xc0 + 2 * xc;
-                        double acc = 0.0;
-                        for (int ku = 0; ku < nk3u; ku++)
-                            acc = fma(s6(v.S[2], sd3, k4, k3ulo + 2 * ku, x), sm.U[(ku * nxc + xc) * di3 + i3], acc);
-                        sm.P[q] = acc;
+                    for (int q = tid; q < nxc * nk4 * nk3u; q += nth) {
+                        const int ku = q % nk3u, r = q / nk3u, c4 = r % nk4, xc = r / nk4;
+                        sm.S3s[q] = s6(v.S[2], sd3, k4lo + 2 * c4, k3ulo + 2 * ku, xc0 + 2 * xc);
                     }
                     // E: Q[k5][k4][x] = (2x+1) S1[i1,k5,x] S2[k5,k4,x]
                     for (int q = tid; q < nk5 * nk4 * nxc; q += nth) {
@@ -224,41 +255,106 @@ __global__ void __launch_bounds__(256) k_shell_fp64(const VtxDev* __restrict__ V
                         sm.Q[q] = (double)(x + 1) * s6(v.S[0], sd1, i1, k5, x) * s6(v.S[1], sd2, k5, k4, x);
                     }
                     __syncthreads();
-                    // F: V[k4][k5][i3] += sum_x Q[k5][k4][x] P[k4][x][i3]
-                    for (int q = tid; q < nk4 * nk5 * di3; q += nth) {
-                        const int i3 = q % di3, r = q / di3, c5 = r % nk5, c4 = r / nk5;
-                        double acc = sm.V[q];
-                        for (int xc = 0; xc < nxc; xc++)
-                            acc = fma(sm.Q[(c5 * nk4 + c4) * nxc + xc], sm.P[(c4 * nxc + xc) * di3 + i3], acc);
-                        sm.V[q] = acc;
+                    // B: R[d][k3][x] = (2k3+1)(-1)^(k3-k3lo) sum_k2 S4_d[k3,k2,x] SB[d][k2][x]
+                    for (int q = tid; q < D * mdk * nxc; q += nth) {
+                        const int xc = q % nxc, r = q / nxc, c3 = r % mdk, d = r / mdk;
+                        const int nk3 = s_nk3[d];
+                        if (c3 >= nk3) continue;
+                        const int k3 = s_k3lo[d] + 2 * c3, x = xc0 + 2 * xc;
+                        const SlotDesc sd4 = s_sd4[d];
+                        const int k2lo = s_k2lo[d], nk2 = s_nk2[d];
+                        double acc0 = 0.0, acc1 = 0.0;
+                        // the k3 and k2 ranges lie inside the slot box; only x can fall outside it
+                        const int ia = (k3 - sd4.alo) >> 1, ix = (x - sd4.xlo) >> 1, ib0 = (k2lo - sd4.blo) >> 1;
+                        if ((unsigned)ix < (unsigned)sd4.nx && ((x - sd4.xlo) & 1) == 0) {
+                            const double* s4p = v.S[3] + sd4.off + ((int64_t)ia * sd4.nb + ib0) * sd4.nx + ix;
+                            const double* sbp = sm.SB + (d * mdk) * XC + xc;
+                            int c2 = 0;
+                            for (; c2 + 1 < nk2; c2 += 2) {
+                                acc0 = fma(__ldg(s4p + (int64_t)c2 * sd4.nx), sbp[c2 * XC], acc0);
+                                acc1 = fma(__ldg(s4p + (int64_t)(c2 + 1) * sd4.nx), sbp[(c2 + 1) * XC], acc1);
+                            }
+                            if (c2 < nk2) acc0 = fma(__ldg(s4p + (int64_t)c2 * sd4.nx), sbp[c2 * XC], acc0);
+                        }
+                        sm.R[(d * mdk + c3) * XC + xc] = (acc0 + acc1) * (double)(k3 + 1) * ((c3 & 1) ? -1.0 : 1.0);
                     }
+                    __syncthreads();
+                    // C: U[k3u][x][i3] = sum_d R[d][k3][x] B3_d[i3][k3]   (4 consecutive i3 per thread)
+                    {
+                        const int nb3 = (di3 + 3) / 4;
+                        for (int q = tid; q < nk3u * nxc * nb3; q += nth) {
+                            const int b = q % nb3, r = q / nb3, xc = r % nxc, ku = r / nxc;
+                            const int i30 = 4 * b;
+                            const int k3 = k3ulo + 2 * ku;
+                            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+                            for (int d = 0; d < D; d++) {
+                                const int c3 = (k3 - s_k3lo[d]) >> 1;
+                                if (k3 < s_k3lo[d] || c3 >= s_nk3[d]) continue;
+                                const double rr = sm.R[(d * mdk + c3) * XC + xc];
+                                const double* bp = sm.B3s + (d * mdk + c3) * di3 + i30;
+                                a0 = fma(rr, bp[0], a0);
+                                if (i30 + 1 < di3) a1 = fma(rr, bp[1], a1);
+                                if (i30 + 2 < di3) a2 = fma(rr, bp[2], a2);
+                                if (i30 + 3 < di3) a3 = fma(rr, bp[3], a3);
+                            }
+                            double* up = sm.U + (ku * nxc + xc) * di3 + i30;
+                            up[0] = a0;
+                            if (i30 + 1 < di3) up[1] = a1;
+                            if (i30 + 2 < di3) up[2] = a2;
+                            if (i30 + 3 < di3) up[3] = a3;
+                        }
+                    }
+                    __syncthreads();
+                    // D: P[k4][x][i3] = sum_k3u S3s[x][k4][k3u] U[k3u][x][i3]        (batch over x)
+                    blk_gemm<2, 4, false>(nxc, nk4, di3, nk3u, sm.S3s, nk4 * nk3u, nk3u, 1, sm.U, di3, nxc * di3, 1,
+                                          sm.P, di3, nxc * di3, 1, tid, nth);
+                    __syncthreads();
+                    // F: V[k4][k5][i3] += sum_x Q[k5][k4][x] P[k4][x][i3]             (batch over k4)
+                    blk_gemm<2, 4, true>(nk4, nk5, di3, nxc, sm.Q, nxc, nk4 * nxc, 1, sm.P, nxc * di3, di3, 1,
+                                         sm.V, nk5 * di3, di3, 1, tid, nth);
                 }
                 __syncthreads();
-                // G: Y[i4][k5][i3] += sum_k4 V[k4][k5][i3] B4'[i4][k4]
-                for (int q = tid; q < di4 * nk5 * di3; q += nth) {
-                    const int i3 = q % di3, r = q / di3, c5 = r % nk5, i4 = r / nk5;
-                    double acc = sm.Y[q];
-                    for (int c4 = 0; c4 < nk4; c4++)
-                        acc = fma(sm.V[(c4 * nk5 + c5) * di3 + i3], sm.B4[i4 * nk4 + c4], acc);
-                    sm.Y[q] = acc;
+                // G: Y[i4][k5][i3] += sum_k4 B4'[i4][k4] V[k4][k5][i3]             (batch over k5)
+                blk_gemm<2, 4, true>(nk5, di4, di3, nk4, sm.B4, 0, nk4, 1, sm.V, di3, nk5 * di3, 1,
+                                     sm.Y, di3, nk5 * di3, 1, tid, nth);
+            }
+            if (!gany) continue;
+            __syncthreads();
+            // H: T[i4][i5][i3] += sum_k5 B5'[i5][k5] Y[i4][k5][i3]   (register-resident output tile)
+#pragma unroll
+            for (int rr = 0; rr < SF_TRT; rr++) {
+                const int b = tid + rr * nth;
+                if (b < di4 * tper) {
+                    const int i4 = b / tper, r = b - i4 * tper;
+                    const int m0 = (r / tb3) * 2, n0 = (r - (r / tb3) * tb3) * 4;
+                    for (int c5 = 0; c5 < nk5; c5++) {
+                        double a[2], y[4];
+#pragma unroll
+                        for (int i = 0; i < 2; i++) a[i] = (m0 + i < di5) ? sm.B5[(m0 + i) * nk5 + c5] : 0.0;
+#pragma unroll
+                        for (int j = 0; j < 4; j++) y[j] = (n0 + j < di3) ? sm.Y[(i4 * nk5 + c5) * di3 + n0 + j] : 0.0;
+#pragma unroll
+                        for (int i = 0; i < 2; i++)
+#pragma unroll
+                            for (int j = 0; j < 4; j++) T[rr][i][j] = fma(a[i], y[j], T[rr][i][j]);
+                    }
                 }
             }
-            __syncthreads();
-            // H: T[i4][i5][i3] += sum_k5 Y[i4][k5][i3] B5'[i5][k5]
-            for (int q = tid; q < di4 * di5 * di3; q += nth) {
-                const int i3 = q % di3, r = q / di3, i5 = r % di5, i4 = r / di5;
-                double acc = sm.T[q];
-                for (int c5 = 0; c5 < nk5; c5++)
-                    acc = fma(sm.Y[(i4 * nk5 + c5) * di3 + i3], sm.B5[i5 * nk5 + c5], acc);
-                sm.T[q] = acc;
-            }
         }
-        __syncthreads();
         // partial tile in [i3][i4][i5] order
         double* out = part + w.part_off;
-        for (int q = tid; q < di3 * di4 * di5; q += nth) {
-            const int i5 = q % di5, r = q / di5, i4 = r % di4, i3 = r / di4;
-            out[q] = sm.T[(i4 * di5 + i5) * di3 + i3];
+#pragma unroll
+        for (int rr = 0; rr < SF_TRT; rr++) {
+            const int b = tid + rr * nth;
+            if (b < di4 * tper) {
+                const int i4 = b / tper, r = b - i4 * tper;
+                const int m0 = (r / tb3) * 2, n0 = (r - (r / tb3) * tb3) * 4;
+#pragma unroll
+                for (int i = 0; i < 2; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++)
+                        if (m0 + i < di5 && n0 + j < di3) out[((n0 + j) * di4 + i4) * di5 + m0 + i] = T[rr][i][j];
+            }
         }
     }
 }
