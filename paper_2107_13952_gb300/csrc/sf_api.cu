@@ -2,6 +2,7 @@
 // device memory ownership and the launch sequence of the kernels.
 #include "sf_internal.cuh"
 #include <algorithm>
+#include <cmath>
 #include <string>
 
 // kernels' launchers (defined in the other translation units)
@@ -492,30 +493,43 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
         if (!t->vs[i].boosters_ready) return sf_set_error(SF_ERR_ARG, "boosters of vertex %zu were never computed or uploaded", i);
         if (!A_out[i]) return sf_set_error(SF_ERR_ARG, "null output for vertex %zu", i);
     }
-    // work items: per vertex, tiles (i1, i2) x chunks of the (l25, l35, l45) groups
+    // work items: per vertex, tiles (i1, i2) x chunks of the (l25, l35, l45) groups. Chunk counts
+    // scale with the estimated cost of a tile so items are of similar size, and the costliest
+    // vertices are queued first (the kernel takes items in order from an atomic counter).
     const int nv = (int)t->vs.size();
-    int64_t tiles_total = 0;
-    for (auto& h : t->vs) tiles_total += (int64_t)h.di[0] * h.di[1];
-    const int64_t target = (int64_t)t->num_sms * 6;
+    std::vector<int64_t> g_lo(nv), g_n(nv);
+    std::vector<double> tile_cost(nv);
+    double total_cost = 0.0;
+    for (int i = 0; i < nv; i++) {
+        VertexHost& h = t->vs[i];
+        const int64_t per_group = (int64_t)h.D * h.D * h.D;   // shells are group-major: D^3 per group
+        int64_t lo = 0, hi = h.ngroups;
+        if (!shell_list) {
+            int64_t b = std::min<int64_t>(std::max<int64_t>(shell_begin, 0), h.nshell);
+            int64_t e = std::min<int64_t>(std::max<int64_t>(shell_end, 0), h.nshell);
+            lo = b / per_group;
+            hi = (e > b) ? (e + per_group - 1) / per_group : lo;
+        }
+        g_lo[i] = lo;
+        g_n[i] = std::max<int64_t>(hi - lo, 0);
+        double dmax = std::max(std::max(h.di[2], h.di[3]), h.di[4]);
+        tile_cost[i] = (double)g_n[i] * per_group * dmax * dmax * dmax * dmax;
+        total_cost += tile_cost[i] * h.di[0] * h.di[1];
+    }
+    const double item_cost = std::max(1.0, total_cost / ((double)t->num_sms * 8.0));
+    std::vector<int> order(nv);
+    for (int i = 0; i < nv; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tile_cost[a] > tile_cost[b]; });
     std::vector<WorkItem> items;
     std::vector<int> item0(nv), nchunk(nv);
     int64_t part_total = 0;
     int mdi = 1, mdk = 1, mk3u = 1, Dmax = 1;
-    for (int i = 0; i < nv; i++) {
+    for (int i : order) {
         VertexHost& h = t->vs[i];
-        int64_t ntile = (int64_t)h.di[0] * h.di[1];
-        int64_t want = std::max<int64_t>(1, (target + tiles_total - 1) / std::max<int64_t>(1, tiles_total));
-        // groups touched by the shell range (shells are group-major: D^3 shells per group)
-        const int64_t per_group = (int64_t)h.D * h.D * h.D;
-        int64_t g_lo = 0, g_hi = h.ngroups;
-        if (!shell_list) {
-            int64_t b = std::min<int64_t>(std::max<int64_t>(shell_begin, 0), h.nshell);
-            int64_t e = std::min<int64_t>(std::max<int64_t>(shell_end, 0), h.nshell);
-            g_lo = b / per_group;
-            g_hi = (e > b) ? (e + per_group - 1) / per_group : g_lo;
-        }
-        const int64_t ng = std::max<int64_t>(g_hi - g_lo, 0);
-        int C = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(ng, 1), want));
+        const int64_t ntile = (int64_t)h.di[0] * h.di[1];
+        const int64_t ng = g_n[i];
+        int C = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(ng, 1),
+                                                            (int64_t)std::ceil(tile_cost[i] / item_cost)));
         item0[i] = (int)items.size();
         nchunk[i] = C;
         int64_t per = (int64_t)h.di[2] * h.di[3] * h.di[4];
@@ -525,8 +539,8 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
                 w.vtx = i;
                 w.i1 = (int)(tile / h.di[1]);
                 w.i2 = (int)(tile % h.di[1]);
-                w.g0 = (int)(g_lo + ng * c / C);
-                w.g1 = (int)(g_lo + ng * (c + 1) / C);
+                w.g0 = (int)(g_lo[i] + ng * c / C);
+                w.g1 = (int)(g_lo[i] + ng * (c + 1) / C);
                 w.part_off = part_total;
                 part_total += per;
                 items.push_back(w);

@@ -80,7 +80,8 @@ __device__ __forceinline__ void blk_gemm(int nbatch, int M, int N, int K, const 
     }
 }
 
-#define SF_TRT 4   // output-tile register blocks per thread (2 x 4 doubles each)
+#define SF_TRT 2   // output-tile register blocks per thread (2 x 4 doubles each)
+#define SF_SHELL_THREADS 512
 
 struct ShellSmem {
     double *Y, *V, *U, *P, *Q, *R, *SB, *S3s, *B3s, *B4, *B5;
@@ -109,7 +110,7 @@ size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D) {
            2ull * mdi * mdk;
 }
 
-__global__ void __launch_bounds__(256) k_shell_fp64(const VtxDev* __restrict__ V, int mdi, int mdk, int mk3u, int XC,
+__global__ void __launch_bounds__(SF_SHELL_THREADS, 1) k_shell_fp64(const VtxDev* __restrict__ V, int mdi, int mdk, int mk3u, int XC,
                                                     int Dmax, const WorkItem* __restrict__ items, int n_items,
                                                     int* counter, double* __restrict__ part, ShellFilter filt) {
     extern __shared__ double smem[];
@@ -365,12 +366,12 @@ int sf_shell_fp64_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, 
     if (smem > 200 * 1024) return sf_set_error(SF_ERR_LIMIT, "shell kernel needs %zu bytes of shared memory", smem);
     SF_CUDA_TRY(cudaFuncSetAttribute(k_shell_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    SF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shell_fp64, 256, smem));
+    SF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shell_fp64, SF_SHELL_THREADS, smem));
     if (per_sm < 1) per_sm = 1;
     int grid = num_sms * per_sm;
     if (grid > n_items) grid = n_items;
     SF_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(int), s));
-    k_shell_fp64<<<grid, 256, smem, s>>>(d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter, d_part, filt);
+    k_shell_fp64<<<grid, SF_SHELL_THREADS, smem, s>>>(d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter, d_part, filt);
     sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;
