@@ -130,6 +130,24 @@ int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t shell_begi
                         const int64_t* shell_list, int64_t n_list, double* const* A_out,
                         cudaStream_t stream);
 
+/* The FP64 shell sum of sf_vertex_amplitude (same tables, same range semantics, same output layout
+ * and values) without any device allocation, for callers that must not allocate device memory
+ * while they run: programs that share the GPU with a framework owning a fixed memory pool, hosts
+ * that forbid allocation after start-up (cudaMalloc/cudaFree may synchronise the whole device),
+ * or callers keeping a strict memory budget. The paper has no counterpart; it is a property of
+ * this library. Build the tables (sf_6j_table, sf_boosters) during start-up, then call this.
+ *   Scratch: one file-scope device array of 32 MiB, present on every GPU that loads the library
+ *   until the process exits. The call needs 256-byte-aligned space for one work item and one
+ *   partial tile (prod of dim_3..dim_5 doubles) per (vertex, i1, i2) tile; larger requests return
+ *   SF_ERR_LIMIT with the size needed (split the shell range or the vertex set).
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *   that device current and caches it; make that first call before any stream capture.
+ *   Every call reuses the same array and leaves its contents behind; calls that overlap on the
+ *   GPU (other streams, other host threads, same device) race on it and must be serialised by
+ *   the caller. A_out: host array of device pointers, as in sf_vertex_amplitude. */
+int sf_vertex_amplitude_noalloc(sf_tables* t, int64_t shell_begin, int64_t shell_end, double* const* A_out,
+                                cudaStream_t stream);
+
 /* Boundary-contracted amplitude and its adjoint (single-vertex tables):
  *   a = sum_i A[i1..i5] psi_1[i1] psi_2[i2] psi_3[i3] psi_4[i4] psi_5[i5]
  * (the paper's contraction of a vertex tensor with boundary intertwiner vectors, Sec. 3 usage),

@@ -26,7 +26,7 @@ SF_TAB_6J, SF_TAB_6J_SLOTS, SF_TAB_D, SF_TAB_NODES = 1, 2, 3, 4
 EXPORTS = ("sf_version", "sf_last_error", "sf_intertwiner_ranges", "sf_num_shells", "sf_6j_table",
            "sf_boosters", "sf_booster_shape", "sf_boosters_upload", "sf_boosters_download",
            "sf_vertex_amplitude", "sf_vertex_adjoint", "sf_table_size", "sf_table_copy", "sf_kernel_launches",
-           "sf_last_kernel_ms", "sf_tables_free")
+           "sf_last_kernel_ms", "sf_vertex_amplitude_noalloc", "sf_tables_free")
 
 
 class SfError(RuntimeError):
@@ -70,6 +70,7 @@ def _declare(lib):
         "sf_table_copy": (ctypes.c_int, [P, I32, I32, I32, P, I64, P]),
         "sf_kernel_launches": (I64, []),
         "sf_last_kernel_ms": (D, [I32]),
+        "sf_vertex_amplitude_noalloc": (ctypes.c_int, [P, I64, I64, ctypes.POINTER(P), P]),
         "sf_tables_free": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -216,6 +217,25 @@ def kernel_launches():
 def last_kernel_ms():
     """Device time (ms) of the last shell-sum kernel, from events on its stream."""
     return float(load().sf_last_kernel_ms(0))
+
+
+def sf_vertex_amplitude_noalloc(tables, out, shell_begin=0, shell_end=2 ** 63 - 1, stream=None):
+    """FP64 shell sum into caller-provided outputs without any device allocation by the library.
+
+    For callers that must not allocate device memory while running (fixed memory pools, hosts that
+    forbid allocation after start-up). ``out``: one preallocated cuda float64 tensor per vertex.
+    The library's scratch is a fixed 32 MiB device array shared by all calls on a device, so calls
+    that overlap on the GPU race; larger requests raise SfError(SF_ERR_LIMIT).
+    """
+    import torch
+    lib = load()
+    for i, v in enumerate(tables.vertices):
+        _, dim = intertwiner_ranges(list(v.two_j), v.gamma, v.dl)
+        o = out[i]
+        assert o.dtype == torch.float64 and o.is_cuda and o.is_contiguous() and list(o.shape) == dim
+    ptrs = (ctypes.c_void_p * len(out))(*[o.data_ptr() for o in out])
+    _check(lib.sf_vertex_amplitude_noalloc(tables.ptr, int(shell_begin), int(shell_end), ptrs, _stream(stream)))
+    return out
 
 
 def table_copy(tables, vtx, kind, index, stream=None):

@@ -688,3 +688,111 @@ extern "C" int sf_table_copy(const sf_tables* t, int32_t vertex, int32_t kind, i
     SF_CUDA_TRY(cudaStreamSynchronize(stream));
     return SF_OK;
 }
+
+// ----------------------------------------------------------------------------------------------
+// vertex amplitude without any device allocation
+//
+// For callers that must not allocate device memory once they are running: code that shares the
+// GPU with a framework owning a fixed memory pool, hosts that forbid allocation after start-up
+// (cudaMalloc/cudaFree can synchronise the device and stall other streams), or callers that keep
+// a strict device-memory budget. Such a caller builds its tables during start-up and then calls
+// this entry point, which takes every scratch byte from one file-scope device array.
+// ----------------------------------------------------------------------------------------------
+#include <mutex>
+
+#define SF_NOALLOC_SCRATCH_BYTES (32ull << 20)   // 32 MiB, held on every GPU that loads the library
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SF_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_addr[128];   // device address of g_noalloc_scratch, per device ordinal
+
+// once per device, with that device current: the host-side symbol is only a stand-in, the
+// kernels need the device address
+static int noalloc_scratch(void** out) {
+    int dev = 0;
+    SF_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return sf_set_error(SF_ERR_LIMIT, "device ordinal %d beyond 127", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return sf_set_error(SF_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return SF_OK;
+}
+
+extern "C" int sf_vertex_amplitude_noalloc(sf_tables* t, int64_t shell_begin, int64_t shell_end, double* const* A_out,
+                                           cudaStream_t stream) {
+    if (!t || !A_out) return sf_set_error(SF_ERR_ARG, "null argument");
+    if (shell_begin < 0) return sf_set_error(SF_ERR_ARG, "negative shell_begin");
+    for (size_t i = 0; i < t->vs.size(); i++) {
+        if (!t->vs[i].boosters_ready) return sf_set_error(SF_ERR_ARG, "boosters of vertex %zu were never computed or uploaded", i);
+        if (!A_out[i]) return sf_set_error(SF_ERR_ARG, "null output for vertex %zu", i);
+    }
+    const int nv = (int)t->vs.size();
+    // one work item per (vertex, i1, i2) tile covering the requested groups: the smallest scratch
+    std::vector<WorkItem> items;
+    std::vector<int> item0(nv);
+    int64_t part_total = 0;
+    int mdi = 1, mdk = 1, mk3u = 1, Dmax = 1;
+    for (int i = 0; i < nv; i++) {
+        VertexHost& h = t->vs[i];
+        const int64_t per_group = (int64_t)h.D * h.D * h.D;
+        int64_t b = std::min<int64_t>(shell_begin, h.nshell), e = std::min<int64_t>(std::max<int64_t>(shell_end, 0), h.nshell);
+        int64_t lo = b / per_group, hi = (e > b) ? (e + per_group - 1) / per_group : lo;
+        item0[i] = (int)items.size();
+        const int64_t per = (int64_t)h.di[2] * h.di[3] * h.di[4];
+        for (int64_t tile = 0; tile < (int64_t)h.di[0] * h.di[1]; tile++) {
+            WorkItem w{};
+            w.vtx = i;
+            w.i1 = (int)(tile / h.di[1]);
+            w.i2 = (int)(tile % h.di[1]);
+            w.g0 = (int)lo;
+            w.g1 = (int)hi;
+            w.part_off = part_total;
+            part_total += per;
+            items.push_back(w);
+        }
+        if ((int64_t)h.di[3] * ((h.di[4] + 1) / 2) * ((h.di[2] + 3) / 4) > 4 * 256)
+            return sf_set_error(SF_ERR_LIMIT, "vertex %d: intertwiner dimensions too large for the register-resident tile", i);
+        for (int k = 2; k < 5; k++) mdi = std::max(mdi, (int)h.di[k]);
+        for (int k = 0; k < 4; k++) mdk = std::max(mdk, (int)h.dkmax[k]);
+        mk3u = std::max(mk3u, h.mk3u);
+        Dmax = std::max(Dmax, h.D);
+    }
+    int xc = 16;
+    while (xc > 1 && sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax) * sizeof(double) > 200 * 1024) xc--;
+    if (sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax) * sizeof(double) > 200 * 1024)
+        return sf_set_error(SF_ERR_LIMIT, "intertwiner dimensions too large for the shell kernel");
+    // scratch layout: items | counter | partial tiles
+    const size_t o_counter = align256(items.size() * sizeof(WorkItem));
+    const size_t o_part = align256(o_counter + sizeof(int));
+    const size_t need = o_part + (size_t)part_total * sizeof(double);
+    if (need > SF_NOALLOC_SCRATCH_BYTES)
+        return sf_set_error(SF_ERR_LIMIT, "sf_vertex_amplitude_noalloc needs %zu bytes of scratch, above its fixed %llu; "
+                                          "split the shell range, the vertex set, or use sf_vertex_amplitude",
+                            need, (unsigned long long)SF_NOALLOC_SCRATCH_BYTES);
+    void* base = nullptr;
+    SF_TRY(noalloc_scratch(&base));
+    char* b8 = (char*)base;
+    WorkItem* d_items = (WorkItem*)b8;
+    int* d_counter = (int*)(b8 + o_counter);   // zeroed by the launcher before the kernel runs
+    double* d_part = (double*)(b8 + o_part);   // every partial tile is fully written by its item
+    SF_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, stream));
+    ShellFilter filt{};
+    filt.begin = shell_begin;
+    filt.end = shell_end;
+    filt.bitmap = nullptr;
+    SF_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, sizeof(int), stream));
+    SF_TRY(sf_shell_fp64_launch(t->d_vtx, mdi, mdk, mk3u, xc, Dmax, d_items, (int)items.size(), d_counter, d_part, filt,
+                                t->num_sms, stream));
+    for (int i = 0; i < nv; i++) {
+        VertexHost& h = t->vs[i];
+        SF_TRY(sf_reduce_launch(t->d_vtx, i, h.di[0] * h.di[1], d_items, item0[i], 1, d_part, A_out[i], stream));
+    }
+    return check_status(t, stream, "sf_vertex_amplitude_noalloc");
+}
