@@ -273,3 +273,54 @@ def sf_vertex_adjoint(tables, psis, want_grads=True, stream=None):
         gb = (ctypes.c_void_p * 4)(*[g.data_ptr() for g in gbs])
     _check(lib.sf_vertex_adjoint(tables.ptr, pp, ctypes.c_void_p(a.data_ptr()), gp, gb, _stream(stream)))
     return a[0], gps, gbs
+
+
+def vjp_from_holomorphic(grad_out, G, real_input):
+    """Backward rule for a function holomorphic in its complex inputs and real-linear in its real
+    inputs, given its holomorphic derivative G = d out / d input: PyTorch passes grad_out =
+    dL/d conj(out) and expects dL/d conj(input) = grad_out * conj(G) for complex inputs, and the
+    real part of that for real inputs."""
+    g = grad_out * G.conj()
+    return g.real if real_input else g
+
+
+def _contraction_function():
+    import torch
+
+    class EPRLContraction(torch.autograd.Function):
+        """a = sum_i A[i] prod_e psi_e[i_e] for one vertex, differentiable in the five complex
+        boundary vectors and the four real booster tensors (forward and backward both run in the
+        library's adjoint kernels, which recompute every shell's {15j} ring)."""
+
+        @staticmethod
+        def forward(ctx, tables, psi1, psi2, psi3, psi4, psi5, B2, B3, B4, B5):
+            for e, B in zip((2, 3, 4, 5), (B2, B3, B4, B5)):
+                sf_boosters_upload(tables, 0, e, B.detach())
+            psis = [p.detach() for p in (psi1, psi2, psi3, psi4, psi5)]
+            a, gpsi, gB = sf_vertex_adjoint(tables, psis, want_grads=True)
+            ctx.save_for_backward(*gpsi, *gB)
+            return a.clone()
+
+        @staticmethod
+        def backward(ctx, grad_a):
+            saved = ctx.saved_tensors
+            gpsi = [vjp_from_holomorphic(grad_a, g, False) for g in saved[:5]]
+            gB = [vjp_from_holomorphic(grad_a, g, True) for g in saved[5:]]
+            return (None, *gpsi, *gB)
+
+    return EPRLContraction
+
+
+_EPRL_FN = None
+
+
+def eprl_contraction(tables, psis, boosters):
+    """Differentiable boundary-contracted amplitude (torch.autograd.Function over the C ABI).
+
+    psis: five complex128 cuda tensors (boundary intertwiner vectors); boosters: four float64 cuda
+    tensors shaped like ``booster_shape(tables, 0, e)`` for e = 2..5.
+    """
+    global _EPRL_FN
+    if _EPRL_FN is None:
+        _EPRL_FN = _contraction_function()
+    return _EPRL_FN.apply(tables, *psis, *boosters)

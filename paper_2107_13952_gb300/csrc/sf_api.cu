@@ -24,8 +24,10 @@ int sf_shell_mixed_launch(const VtxDev* d_v, int mdi, int mdk, const WorkItem* d
 int sf_reduce_launch(const VtxDev* d_v, int vtx, int ntiles, const WorkItem* d_items, int item0, int nchunk,
                      const double* d_part, double* A, cudaStream_t s);
 int sf_bitmap_launch(const int64_t* d_list, int64_t n, int64_t nshell, uint32_t* d_bm, cudaStream_t s);
-int sf_adjoint_run(sf_tables* t, const double* const psi[5], double* a_out, double* const grad_psi[5],
-                   double* const grad_B[4], cudaStream_t s);
+int sf_adjoint_launch(const VtxDev* d_v, const VtxDev& h, const double* const psi[5], double* a_out,
+                      double* const grad_psi[5], double* const grad_B[4], void* scratch, size_t scratch_bytes,
+                      int num_sms, cudaStream_t s);
+size_t sf_adjoint_scratch_bytes(const VtxDev& h);
 
 // ----------------------------------------------------------------------------------------------
 // errors
@@ -617,7 +619,22 @@ extern "C" int sf_vertex_adjoint(sf_tables* t, const double* const psi[5], doubl
     if (t->vs.size() != 1) return sf_set_error(SF_ERR_ARG, "the adjoint needs single-vertex tables");
     if (!t->vs[0].boosters_ready) return sf_set_error(SF_ERR_ARG, "boosters were never computed or uploaded");
     for (int e = 0; e < 5; e++) if (!psi[e]) return sf_set_error(SF_ERR_ARG, "null boundary vector %d", e + 1);
-    return sf_adjoint_run(t, psi, a_out, grad_psi, grad_B, stream);
+    if (grad_psi)
+        for (int e = 0; e < 5; e++) if (!grad_psi[e]) return sf_set_error(SF_ERR_ARG, "null grad_psi[%d]", e);
+    if (grad_B)
+        for (int e = 0; e < 4; e++) if (!grad_B[e]) return sf_set_error(SF_ERR_ARG, "null grad_B[%d]", e);
+    const VertexHost& hv = t->vs[0];
+    VtxDev h;
+    memset(&h, 0, sizeof(h));
+    for (int e = 0; e < 5; e++) { h.di[e] = hv.di[e]; h.ilo[e] = hv.ilo[e]; }
+    for (int e = 0; e < 4; e++) h.dkmax[e] = hv.dkmax[e];
+    h.ntrip = hv.ntrip;
+    h.nshell = hv.nshell;
+    h.D = hv.D;
+    SF_TRY(grow_scratch(t, sf_adjoint_scratch_bytes(h)));
+    SF_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, sizeof(int), stream));
+    SF_TRY(sf_adjoint_launch(t->d_vtx, h, psi, a_out, grad_psi, grad_B, t->d_scratch, t->scratch_bytes, t->num_sms, stream));
+    return check_status(t, stream, "sf_vertex_adjoint");
 }
 
 // ----------------------------------------------------------------------------------------------
