@@ -404,10 +404,3 @@ size_t sf_adjoint_scratch_bytes(const VtxDev& h) {
     return (5 * 32 + 32) * sizeof(cplx) + 4 * (size_t)h.ntrip * 32 * sizeof(cplx) +
            (size_t)h.nshell * per_shell * sizeof(cplx) + 1024;
 }
-
-int sf_shell_mixed_launch(const VtxDev* d_v, int mdi, int mdk, const WorkItem* d_items, int n_items,
-                          int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s) {
-    (void)d_v; (void)mdi; (void)mdk; (void)d_items; (void)n_items; (void)d_counter; (void)d_part; (void)filt;
-    (void)num_sms; (void)s;
-    return sf_set_error(SF_ERR_ARG, "the mixed-precision path is not available in this build");
-}

@@ -16,11 +16,11 @@ int sf_dtable_build(int tk, double gamma, int nl, int nnodes, const double* d_r,
 size_t sf_booster_smem(int tj1, int tj2, int tj3, int tj4, int nk);
 int sf_booster_build(const VtxDev* d_v, int edge, int ntrip, size_t smem, const double* d_W, int nnodes,
                      const dd* F, double* d_Aj, double* d_Cj, double* d_B, int* d_status, cudaStream_t s);
-size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D);
+size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, bool mix = false);
 int sf_shell_fp64_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax, const WorkItem* d_items,
                          int n_items, int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s);
-int sf_shell_mixed_launch(const VtxDev* d_v, int mdi, int mdk, const WorkItem* d_items, int n_items,
-                          int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s);
+int sf_shell_mixed_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax, const WorkItem* d_items,
+                          int n_items, int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s);
 int sf_reduce_launch(const VtxDev* d_v, int vtx, int ntiles, const WorkItem* d_items, int item0, int nchunk,
                      const double* d_part, double* A, cudaStream_t s);
 int sf_bitmap_launch(const int64_t* d_list, int64_t n, int64_t nshell, uint32_t* d_bm, cudaStream_t s);
@@ -557,9 +557,10 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
     }
     if (items.size() > (size_t)0x7FFFFFFF) return sf_set_error(SF_ERR_LIMIT, "too many work items");
     // x chunk: keep the shared-memory footprint under ~200 KB
+    const bool mix = precision == SF_MIXED;
     int xc = 16;
-    while (xc > 1 && sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax) * sizeof(double) > 200 * 1024) xc--;
-    if (sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax) * sizeof(double) > 200 * 1024)
+    while (xc > 1 && sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax, mix) * sizeof(double) > 200 * 1024) xc--;
+    if (sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax, mix) * sizeof(double) > 200 * 1024)
         return sf_set_error(SF_ERR_LIMIT, "intertwiner dimensions too large for the shell kernel");
     // scratch: items | counter | bitmap | partials
     int64_t nshell0 = t->vs[0].nshell;
@@ -597,8 +598,8 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
         SF_TRY(sf_shell_fp64_launch(t->d_vtx, mdi, mdk, mk3u, xc, Dmax, d_items, (int)items.size(), d_counter, d_part,
                                     filt, t->num_sms, stream));
     } else {
-        SF_TRY(sf_shell_mixed_launch(t->d_vtx, mdi, mdk, d_items, (int)items.size(), d_counter, d_part, filt,
-                                     t->num_sms, stream));
+        SF_TRY(sf_shell_mixed_launch(t->d_vtx, mdi, mdk, mk3u, xc, Dmax, d_items, (int)items.size(), d_counter, d_part,
+                                     filt, t->num_sms, stream));
     }
     SF_CUDA_TRY(cudaEventRecord(ev1, stream));
     for (int i = 0; i < nv; i++) {

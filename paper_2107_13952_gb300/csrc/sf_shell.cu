@@ -85,6 +85,7 @@ __device__ __forceinline__ void blk_gemm(int nbatch, int M, int N, int K, const 
 
 struct ShellSmem {
     double *Y, *V, *U, *P, *Q, *R, *SB, *S3s, *B3s, *B4, *B5;
+    float *Vf, *B4f;   // mixed path: FP32 copies for the k4 booster contraction
 };
 
 __device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int xc, int D) {
@@ -101,16 +102,62 @@ __device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int 
     s.B3s = p; p += D * mdk * mdi;
     s.B4 = p;  p += mdi * mdk;
     s.B5 = p;  p += mdi * mdk;
+    s.Vf = reinterpret_cast<float*>(p);
+    s.B4f = s.Vf + ((mdk * mdk * mdi + 3) & ~3);
     return s;
 }
 
-size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D) {
-    return (size_t)mdi * mdk * mdi + (size_t)mdk * mdk * mdi + (size_t)mk3u * xc * mdi + (size_t)mdk * xc * mdi +
-           (size_t)mdk * mdk * xc + 2ull * D * mdk * xc + (size_t)xc * mdk * mk3u + (size_t)D * mdk * mdi +
-           2ull * mdi * mdk;
+size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, bool mix = false) {
+    size_t n = (size_t)mdi * mdk * mdi + (size_t)mdk * mdk * mdi + (size_t)mk3u * xc * mdi + (size_t)mdk * xc * mdi +
+               (size_t)mdk * mdk * xc + 2ull * D * mdk * xc + (size_t)xc * mdk * mk3u + (size_t)D * mdk * mdi +
+               2ull * mdi * mdk;
+    if (mix) n += (((size_t)mdk * mdk * mdi + 3) / 4) * 2 + ((size_t)mdi * mdk + 1) / 2 + 1;
+    return n;
 }
 
-__global__ void __launch_bounds__(SF_SHELL_THREADS, 1) k_shell_fp64(const VtxDev* __restrict__ V, int mdi, int mdk, int mk3u, int XC,
+// FP32 variant for the mixed path: C[bt][m][n] += (double) sum_k A[bt][m][k] B[bt][k][n], with the
+// products and the sum over k in FP32 and the accumulation into C in FP64
+template <int BM, int BN>
+__device__ __forceinline__ void blk_gemm_f32(int nbatch, int M, int N, int K, const float* A, int a_bs, int am, int ak,
+                                             const float* B, int b_bs, int bk, int bn, double* C, int c_bs, int cm,
+                                             int cn, int tid, int nth) {
+    const int nbm = (M + BM - 1) / BM, nbn = (N + BN - 1) / BN, per = nbm * nbn;
+    for (int blk = tid; blk < per * nbatch; blk += nth) {
+        const int bt = blk / per, r = blk - bt * per;
+        const int m0 = (r / nbn) * BM, n0 = (r - (r / nbn) * nbn) * BN;
+        const float* Ab = A + bt * a_bs + m0 * am;
+        const float* Bb = B + bt * b_bs + n0 * bn;
+        double* Cb = C + bt * c_bs + m0 * cm + n0 * cn;
+        float acc[BM][BN];
+#pragma unroll
+        for (int i = 0; i < BM; i++)
+#pragma unroll
+            for (int j = 0; j < BN; j++) acc[i][j] = 0.0f;
+        for (int k = 0; k < K; k++) {
+            float a[BM], b[BN];
+#pragma unroll
+            for (int i = 0; i < BM; i++) a[i] = (m0 + i < M) ? Ab[i * am + k * ak] : 0.0f;
+#pragma unroll
+            for (int j = 0; j < BN; j++) b[j] = (n0 + j < N) ? Bb[k * bk + j * bn] : 0.0f;
+#pragma unroll
+            for (int i = 0; i < BM; i++)
+#pragma unroll
+                for (int j = 0; j < BN; j++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < BM; i++)
+#pragma unroll
+            for (int j = 0; j < BN; j++)
+                if (m0 + i < M && n0 + j < N) Cb[i * cm + j * cn] += (double)acc[i][j];
+    }
+}
+
+// MIX = false: every phase in FP64 (the FP64 path). MIX = true (the mixed path): the booster
+// contractions over k2 (B2, with S4 S5), over k3 (B3, summed over l23) and over k4 (B4) take FP32
+// inputs and accumulate in FP32 within one (l24, l34) 5-tuple; the {6j} contractions (S3, and the
+// x-sum with S1 S2), every sum across 5-tuples and groups, and the k5 contraction stay FP64.
+template <bool MIX>
+__global__ void __launch_bounds__(SF_SHELL_THREADS, 1) k_shell(const VtxDev* __restrict__ V, int mdi, int mdk, int mk3u, int XC,
                                                     int Dmax, const WorkItem* __restrict__ items, int n_items,
                                                     int* counter, double* __restrict__ part, ShellFilter filt) {
     extern __shared__ double smem[];
@@ -227,7 +274,9 @@ __global__ void __launch_bounds__(SF_SHELL_THREADS, 1) k_shell_fp64(const VtxDev
                 for (int q = tid; q < D * mdk * di3; q += nth) {
                     const int i3 = q % di3, r = q / di3, c3 = r % mdk, d = r / mdk;
                     const int t3 = (d34 * D + d35) * D + d;
-                    sm.B3s[q] = (c3 < dk1) ? __ldg(v.B[1] + ((int64_t)t3 * di3 + i3) * dk1 + c3) : 0.0;
+                    const double b3 = (c3 < dk1) ? __ldg(v.B[1] + ((int64_t)t3 * di3 + i3) * dk1 + c3) : 0.0;
+                    if constexpr (MIX) reinterpret_cast<float*>(sm.B3s)[q] = (float)b3;
+                    else sm.B3s[q] = b3;
                 }
                 for (int q = tid; q < nk4 * nk5 * di3; q += nth) sm.V[q] = 0.0;
                 const SlotDesc sd3 = load_slot(v.slot[2] + (d24 * D + d34) * D + d35);
@@ -243,7 +292,9 @@ __global__ void __launch_bounds__(SF_SHELL_THREADS, 1) k_shell_fp64(const VtxDev
                         const int t2 = (d * D + d24) * D + d25;
                         const double b2 = __ldg(v.B[0] + ((int64_t)t2 * v.di[1] + ci2) * v.dkmax[0] + c2);
                         const double f = (double)(k2 + 1) * ((c2 & 1) ? -s_sig[d] : s_sig[d]);
-                        sm.SB[(d * mdk + c2) * XC + xc] = f * b2 * s6(v.S[4], sd5, k2, i1, x);
+                        const double sb = f * b2 * s6(v.S[4], sd5, k2, i1, x);
+                        if constexpr (MIX) reinterpret_cast<float*>(sm.SB)[(d * mdk + c2) * XC + xc] = (float)sb;
+                        else sm.SB[(d * mdk + c2) * XC + xc] = sb;
                     }
                     for (int q = tid; q < nxc * nk4 * nk3u; q += nth) {
                         const int ku = q % nk3u, r = q / nk3u, c4 = r % nk4, xc = r / nk4;
@@ -264,20 +315,36 @@ __global__ void __launch_bounds__(SF_SHELL_THREADS, 1) k_shell_fp64(const VtxDev
                         const int k3 = s_k3lo[d] + 2 * c3, x = xc0 + 2 * xc;
                         const SlotDesc sd4 = s_sd4[d];
                         const int k2lo = s_k2lo[d], nk2 = s_nk2[d];
-                        double acc0 = 0.0, acc1 = 0.0;
                         // the k3 and k2 ranges lie inside the slot box; only x can fall outside it
                         const int ia = (k3 - sd4.alo) >> 1, ix = (x - sd4.xlo) >> 1, ib0 = (k2lo - sd4.blo) >> 1;
-                        if ((unsigned)ix < (unsigned)sd4.nx && ((x - sd4.xlo) & 1) == 0) {
-                            const double* s4p = v.S[3] + sd4.off + ((int64_t)ia * sd4.nb + ib0) * sd4.nx + ix;
-                            const double* sbp = sm.SB + (d * mdk) * XC + xc;
-                            int c2 = 0;
-                            for (; c2 + 1 < nk2; c2 += 2) {
-                                acc0 = fma(__ldg(s4p + (int64_t)c2 * sd4.nx), sbp[c2 * XC], acc0);
-                                acc1 = fma(__ldg(s4p + (int64_t)(c2 + 1) * sd4.nx), sbp[(c2 + 1) * XC], acc1);
+                        const bool inbox = (unsigned)ix < (unsigned)sd4.nx && ((x - sd4.xlo) & 1) == 0;
+                        const double* s4p = v.S[3] + sd4.off + ((int64_t)ia * sd4.nb + ib0) * sd4.nx + ix;
+                        const double sgn3 = (double)(k3 + 1) * ((c3 & 1) ? -1.0 : 1.0);
+                        if constexpr (MIX) {
+                            const float* sbp = reinterpret_cast<const float*>(sm.SB) + (d * mdk) * XC + xc;
+                            float acc0 = 0.0f, acc1 = 0.0f;
+                            if (inbox) {
+                                int c2 = 0;
+                                for (; c2 + 1 < nk2; c2 += 2) {
+                                    acc0 = fmaf((float)__ldg(s4p + (int64_t)c2 * sd4.nx), sbp[c2 * XC], acc0);
+                                    acc1 = fmaf((float)__ldg(s4p + (int64_t)(c2 + 1) * sd4.nx), sbp[(c2 + 1) * XC], acc1);
+                                }
+                                if (c2 < nk2) acc0 = fmaf((float)__ldg(s4p + (int64_t)c2 * sd4.nx), sbp[c2 * XC], acc0);
                             }
-                            if (c2 < nk2) acc0 = fma(__ldg(s4p + (int64_t)c2 * sd4.nx), sbp[c2 * XC], acc0);
+                            reinterpret_cast<float*>(sm.R)[(d * mdk + c3) * XC + xc] = (acc0 + acc1) * (float)sgn3;
+                        } else {
+                            const double* sbp = sm.SB + (d * mdk) * XC + xc;
+                            double acc0 = 0.0, acc1 = 0.0;
+                            if (inbox) {
+                                int c2 = 0;
+                                for (; c2 + 1 < nk2; c2 += 2) {
+                                    acc0 = fma(__ldg(s4p + (int64_t)c2 * sd4.nx), sbp[c2 * XC], acc0);
+                                    acc1 = fma(__ldg(s4p + (int64_t)(c2 + 1) * sd4.nx), sbp[(c2 + 1) * XC], acc1);
+                                }
+                                if (c2 < nk2) acc0 = fma(__ldg(s4p + (int64_t)c2 * sd4.nx), sbp[c2 * XC], acc0);
+                            }
+                            sm.R[(d * mdk + c3) * XC + xc] = (acc0 + acc1) * sgn3;
                         }
-                        sm.R[(d * mdk + c3) * XC + xc] = (acc0 + acc1) * (double)(k3 + 1) * ((c3 & 1) ? -1.0 : 1.0);
                     }
                     __syncthreads();
                     // C: U[k3u][x][i3] = sum_d R[d][k3][x] B3_d[i3][k3]   (4 consecutive i3 per thread)
@@ -288,15 +355,32 @@ __global__ void __launch_bounds__(SF_SHELL_THREADS, 1) k_shell_fp64(const VtxDev
                             const int i30 = 4 * b;
                             const int k3 = k3ulo + 2 * ku;
                             double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-                            for (int d = 0; d < D; d++) {
-                                const int c3 = (k3 - s_k3lo[d]) >> 1;
-                                if (k3 < s_k3lo[d] || c3 >= s_nk3[d]) continue;
-                                const double rr = sm.R[(d * mdk + c3) * XC + xc];
-                                const double* bp = sm.B3s + (d * mdk + c3) * di3 + i30;
-                                a0 = fma(rr, bp[0], a0);
-                                if (i30 + 1 < di3) a1 = fma(rr, bp[1], a1);
-                                if (i30 + 2 < di3) a2 = fma(rr, bp[2], a2);
-                                if (i30 + 3 < di3) a3 = fma(rr, bp[3], a3);
+                            if constexpr (MIX) {
+                                const float* Rf = reinterpret_cast<const float*>(sm.R);
+                                const float* Bf = reinterpret_cast<const float*>(sm.B3s);
+                                float f0 = 0.0f, f1 = 0.0f, f2 = 0.0f, f3 = 0.0f;
+                                for (int d = 0; d < D; d++) {
+                                    const int c3 = (k3 - s_k3lo[d]) >> 1;
+                                    if (k3 < s_k3lo[d] || c3 >= s_nk3[d]) continue;
+                                    const float rr = Rf[(d * mdk + c3) * XC + xc];
+                                    const float* bp = Bf + (d * mdk + c3) * di3 + i30;
+                                    f0 = fmaf(rr, bp[0], f0);
+                                    if (i30 + 1 < di3) f1 = fmaf(rr, bp[1], f1);
+                                    if (i30 + 2 < di3) f2 = fmaf(rr, bp[2], f2);
+                                    if (i30 + 3 < di3) f3 = fmaf(rr, bp[3], f3);
+                                }
+                                a0 = f0; a1 = f1; a2 = f2; a3 = f3;
+                            } else {
+                                for (int d = 0; d < D; d++) {
+                                    const int c3 = (k3 - s_k3lo[d]) >> 1;
+                                    if (k3 < s_k3lo[d] || c3 >= s_nk3[d]) continue;
+                                    const double rr = sm.R[(d * mdk + c3) * XC + xc];
+                                    const double* bp = sm.B3s + (d * mdk + c3) * di3 + i30;
+                                    a0 = fma(rr, bp[0], a0);
+                                    if (i30 + 1 < di3) a1 = fma(rr, bp[1], a1);
+                                    if (i30 + 2 < di3) a2 = fma(rr, bp[2], a2);
+                                    if (i30 + 3 < di3) a3 = fma(rr, bp[3], a3);
+                                }
                             }
                             double* up = sm.U + (ku * nxc + xc) * di3 + i30;
                             up[0] = a0;
@@ -316,8 +400,16 @@ __global__ void __launch_bounds__(SF_SHELL_THREADS, 1) k_shell_fp64(const VtxDev
                 }
                 __syncthreads();
                 // G: Y[i4][k5][i3] += sum_k4 B4'[i4][k4] V[k4][k5][i3]             (batch over k5)
-                blk_gemm<2, 4, true>(nk5, di4, di3, nk4, sm.B4, 0, nk4, 1, sm.V, di3, nk5 * di3, 1,
-                                     sm.Y, di3, nk5 * di3, 1, tid, nth);
+                if constexpr (MIX) {
+                    for (int q = tid; q < nk4 * nk5 * di3; q += nth) sm.Vf[q] = (float)sm.V[q];
+                    for (int q = tid; q < di4 * nk4; q += nth) sm.B4f[q] = (float)sm.B4[q];
+                    __syncthreads();
+                    blk_gemm_f32<2, 4>(nk5, di4, di3, nk4, sm.B4f, 0, nk4, 1, sm.Vf, di3, nk5 * di3, 1,
+                                       sm.Y, di3, nk5 * di3, 1, tid, nth);
+                } else {
+                    blk_gemm<2, 4, true>(nk5, di4, di3, nk4, sm.B4, 0, nk4, 1, sm.V, di3, nk5 * di3, 1,
+                                         sm.Y, di3, nk5 * di3, 1, tid, nth);
+                }
             }
             if (!gany) continue;
             __syncthreads();
@@ -360,21 +452,32 @@ __global__ void __launch_bounds__(SF_SHELL_THREADS, 1) k_shell_fp64(const VtxDev
     }
 }
 
-int sf_shell_fp64_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax, const WorkItem* d_items,
-                         int n_items, int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s) {
-    size_t smem = sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax) * sizeof(double);
+template <bool MIX>
+static int shell_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax, const WorkItem* d_items,
+                        int n_items, int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s) {
+    size_t smem = sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax, MIX) * sizeof(double);
     if (smem > 200 * 1024) return sf_set_error(SF_ERR_LIMIT, "shell kernel needs %zu bytes of shared memory", smem);
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_shell_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SF_CUDA_TRY(cudaFuncSetAttribute(k_shell<MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    SF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shell_fp64, SF_SHELL_THREADS, smem));
+    SF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shell<MIX>, SF_SHELL_THREADS, smem));
     if (per_sm < 1) per_sm = 1;
     int grid = num_sms * per_sm;
     if (grid > n_items) grid = n_items;
     SF_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(int), s));
-    k_shell_fp64<<<grid, SF_SHELL_THREADS, smem, s>>>(d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter, d_part, filt);
+    k_shell<MIX><<<grid, SF_SHELL_THREADS, smem, s>>>(d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter, d_part, filt);
     sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;
+}
+
+int sf_shell_fp64_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax, const WorkItem* d_items,
+                         int n_items, int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s) {
+    return shell_launch<false>(d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter, d_part, filt, num_sms, s);
+}
+
+int sf_shell_mixed_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax, const WorkItem* d_items,
+                          int n_items, int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s) {
+    return shell_launch<true>(d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter, d_part, filt, num_sms, s);
 }
 
 // A[i1][i2][i3][i4][i5] = (-1)^(n_i1) prod_e sqrt(2 i_e + 1) * sum_{chunks} part[tile, chunk][i3][i4][i5]
