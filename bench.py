@@ -53,7 +53,7 @@ def _pair(a, b, c, d):
 
 
 def executed_fmas(tj, dl, g0, g1):
-    """FP64 FMAs the shell kernel executes for groups [g0, g1) of one vertex (all tiles)."""
+    """FMAs the shell kernel executes for groups [g0, g1) of one vertex (all tiles), per phase."""
     import numpy as np
     from paper_2107_13952_gb300 import intertwiner_ranges
     lo, dim = intertwiner_ranges(tj, GAMMA, dl)
@@ -92,7 +92,7 @@ def executed_fmas(tj, dl, g0, g1):
     gidx = (np.arange(D)[:, None, None] * D + np.arange(D)[None, :, None]) * D + np.arange(D)[None, None, :]
     gmask = np.broadcast_to(((gidx >= g0) & (gidx < g1))[..., None, None], shape5)
     di3, di4, di5 = dim[2], dim[3], dim[4]
-    total = 0
+    total = {k: 0 for k in "BCDFGH"}
     k5hi = k5lob + 2 * (nk5b - 1)
     k4hi = k4lob + 2 * (nk4b - 1)
 
@@ -107,13 +107,16 @@ def executed_fmas(tj, dl, g0, g1):
         xlo = xlo + ((xlo - np.abs(i1 - l25b)) % 2)
         nx = np.where(xhi >= xlo, (xhi - xlo) // 2 + 1, 0)
         live = gmask & anyv & (nk5b > 0) & (nk4b > 0) & (nx > 0)
-        per5 = (sum_nk3nk2 * nx + nx * di3 * sum_nk3 + nk4b * nx * di3 * k3u + nk4b * nk5b * di3 * nx
-                + di4 * nk5b * di3 * nk4b)
-        total += int(np.where(live, per5, 0).sum())
+        for name, per5 in (("B", sum_nk3nk2 * nx), ("C", nx * di3 * sum_nk3), ("D", nk4b * nx * di3 * k3u),
+                           ("F", nk4b * nk5b * di3 * nx), ("G", di4 * nk5b * di3 * nk4b)):
+            total[name] += int(np.where(live, per5, 0).sum())
     # H: once per group with a non-empty k5 range
     g_live = ((gidx >= g0) & (gidx < g1)) & (nk5[..., 0, 0, 0] > 0)
-    total += int(dim[0] * np.where(g_live, di4 * di5 * di3 * nk5[..., 0, 0, 0], 0).sum())
-    return total * dim[1]
+    total["H"] += int(dim[0] * np.where(g_live, di4 * di5 * di3 * nk5[..., 0, 0, 0], 0).sum())
+    return {k: v * dim[1] for k, v in total.items()}
+
+
+FP32_PHASES_MIXED = ("B", "C", "G")   # booster contractions the mixed path runs in FP32
 
 
 # ------------------------------------------------------------------------------------------
@@ -229,11 +232,25 @@ def main():
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
+                    help="path timed for `value`; the other path is timed for one step beside it")
     ap.add_argument("--slices", type=int, default=16, help="steps per full pass over the sweep")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default=None, help="lambda:groups:precision -- one shell-sum launch (profiling)")
     args = ap.parse_args()
+
+    if args.case:
+        # one shell-sum launch on a small range of one vertex (for profiler captures)
+        import torch
+        import paper_2107_13952_gb300 as sf
+        lam, ngroups, p = (int(v) for v in args.case.split(":"))
+        t = sf.sf_6j_table([sf.vertex((lam,) * 10, GAMMA, 10)])
+        sf.sf_boosters(t, RULE)
+        A = sf.sf_vertex_amplitude(t, p, 0, ngroups * 11 ** 3)[0]
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "norm": float(A.norm()), "kernel_ms": sf.last_kernel_ms()}))
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -287,11 +304,11 @@ def main():
         g0, g1 = G * k // S, G * (k + 1) // S
         return g0 * 121 * 11, g1 * 121 * 11, g0, g1
 
-    def step(k, to_host):
+    def step(k, to_host, p=None):
         b, e, _, _ = slice_bounds(k % S)
         t = sf.sf_6j_table(verts)
         sf.sf_boosters(t, RULE)
-        sf.sf_vertex_amplitude(t, prec, b, e, out=outs)
+        sf.sf_vertex_amplitude(t, prec if p is None else p, b, e, out=outs)
         kms = sf.last_kernel_ms()
         if to_host:
             for o, h in zip(outs, host):
@@ -333,6 +350,24 @@ def main():
     clocks = clk.stop()
     ms_e2e, _, shells_e2e, _, _ = timed(True, args.warmup + args.steps)
 
+    # the other precision on one slice, timed the same way, and the relative error between them
+    other = sf.SF_FP64 if prec == sf.SF_MIXED else sf.SF_MIXED
+    kk = (args.warmup + 2 * args.steps) * world + rank
+    step(kk, False, other)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    kms_o, n_o = step(kk, False, other)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_other = e0.elapsed_time(e1)
+    ref = [o.clone() for o in outs]
+    step(kk, False, prec)
+    torch.cuda.synchronize()
+    num = sum(float((o - r).norm()) ** 2 for o, r in zip(outs, ref)) ** 0.5
+    den = sum(float(r.norm()) ** 2 for r in ref) ** 0.5
+    rel_err = num / den if den > 0 else None
+
     # max over ranks
     if world > 1:
         tm = torch.tensor([ms, ms_e2e], device="cuda")
@@ -348,11 +383,16 @@ def main():
         return
 
     # roofline of the dominant kernel (the shell sum): executed FP64 flops / event-timed duration
-    flops = 0
+    flops, flops32 = 0, 0
     for k in slices:
         _, _, g0, g1 = slice_bounds(k)
         for lam, dl in SWEEP:
-            flops += 2 * executed_fmas((lam,) * 10, dl, g0, g1)
+            ph = executed_fmas((lam,) * 10, dl, g0, g1)
+            for name, n in ph.items():
+                if args.precision == "mixed" and name in FP32_PHASES_MIXED:
+                    flops32 += 2 * n
+                else:
+                    flops += 2 * n
     kern_s = sum(kms_all) / 1e3
     achieved = flops / kern_s / 1e12 if kern_s > 0 else None
     traffic = None
@@ -368,11 +408,12 @@ def main():
 
     d2h = sum(h.numel() * 8 for h in host)
     h2d = len(verts) * 56
+    other_name = "fp64" if args.precision == "mixed" else "mixed"
     line = {
-        "metric": "EPRL vertex shells/sec (%s GPU path)" % args.precision.upper(),
+        "metric": "EPRL vertex shells/sec (mixed vs FP64 GPU path) at stated relative error",
         "value": value, "unit": "shells/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f64+tf32", "data": "synthetic",
+        "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
         "config": {"workload": "homogeneous sweep: 16 vertices, all spins j=lambda/2 for lambda=1..16, gamma=1.2, "
                                "dl=10 (11^6 shells each), rule r_max=40 / 40 panels x 50 nodes; one step = 6j "
                                "tables + d-tables + boosters of all 16 vertices + shell sum over a 1/%d slice "
@@ -381,12 +422,20 @@ def main():
                    "no flush (compute-bound FP64 path)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": traffic,
-                     "kernel": "k_shell_fp64", "flops_counted": "FP64 FMAs the kernel executes x 2 (loop trip counts)",
+                     "kernel": "k_shell<%d>" % (1 if args.precision == "mixed" else 0),
+                     "flops_counted": "FP64-pipe FMAs the kernel executes x 2 (loop trip counts); the FP32 "
+                                      "phases of the mixed path are reported separately",
+                     "fp32_tflops": (flops32 / kern_s / 1e12) if kern_s > 0 else None,
                      "kernel_ms_per_step": 1e3 * kern_s / args.steps},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "shells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clocks,
+        "path": args.precision,
+        other_name: {"value": n_o * world / (ms_other / 1e3), "unit": "shells/s", "ms_per_step": ms_other,
+                     "kernel_ms_per_step": kms_o},
+        "mixed_vs_fp64": {"rel_err": rel_err, "stated_bound": 1e-6,
+                          "metric": "||A_mixed - A_fp64|| / ||A_fp64|| over the 16 vertices of one slice"},
     }
     print(json.dumps(line))
     if world > 1:

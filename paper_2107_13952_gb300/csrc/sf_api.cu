@@ -9,6 +9,7 @@
 int sf_fact_table_build(dd* F, cudaStream_t s);
 int sf_sixj_table_build(int table_id, const VtxDev* d_v, const SlotDesc* d_slots, int nslots, int64_t n,
                         double* d_out, const dd* F, int* d_status, int num_sms, cudaStream_t s);
+int sf_to_float(const double* d_in, float* d_out, int64_t n, int num_sms, cudaStream_t s);
 int sf_rule_build(const sf_quad_rule* q, double* d_gl, double* d_x, double* d_w, double* d_r, double* d_W,
                   cudaStream_t s);
 int sf_dtable_build(int tk, double gamma, int nl, int nnodes, const double* d_r, const double* d_gl, double2* d_out,
@@ -68,6 +69,7 @@ struct VertexHost {
     int32_t ilo[5], di[5];
     int64_t nshell = 0;
     Table6j S[5];
+    float* d_S4f = nullptr;
     int64_t ntrip = 0;
     int32_t dkmax[4];
     std::vector<int32_t> klo[4];
@@ -283,6 +285,7 @@ static int upload_vtxdev(sf_tables* t) {
         for (int e = 0; e < 5; e++) { d.ilo[e] = h.ilo[e]; d.di[e] = h.di[e]; }
         d.nshell = h.nshell;
         for (int k = 0; k < 5; k++) { d.S[k] = h.S[k].d_vals; d.slot[k] = h.S[k].d_slots; }
+        d.S4f = h.d_S4f;
         for (int e = 0; e < 4; e++) { d.B[e] = h.d_B[e]; d.klo[e] = h.d_klo[e]; d.dkmax[e] = h.dkmax[e]; }
         d.ntrip = h.ntrip;
         for (int f = 0; f < 10; f++) { d.dtab[f] = h.d_dtab[f]; d.nl[f] = h.nl[f]; }
@@ -341,6 +344,8 @@ extern "C" int sf_6j_table(const sf_vertex* v, int32_t n, sf_tables** out, cudaS
             plan_6j(h);
             plan_boosters(h);
             for (int k = 0; k < 5 && rc == SF_OK; k++) {
+                if (k == 3) rc = dev_alloc(t, (void**)&h.d_S4f, h.S[3].n * sizeof(float));
+                if (rc != SF_OK) break;
                 rc = dev_alloc(t, (void**)&h.S[k].d_slots, h.S[k].slots.size() * sizeof(SlotDesc));
                 if (rc == SF_OK) rc = dev_alloc(t, (void**)&h.S[k].d_vals, h.S[k].n * sizeof(double));
                 if (rc == SF_OK && cudaMemcpy(h.S[k].d_slots, h.S[k].slots.data(), h.S[k].slots.size() * sizeof(SlotDesc),
@@ -368,6 +373,7 @@ extern "C" int sf_6j_table(const sf_vertex* v, int32_t n, sf_tables** out, cudaS
             for (int k = 0; k < 5 && rc == SF_OK; k++)
                 rc = sf_sixj_table_build(k + 1, t->d_vtx + i, h.S[k].d_slots, (int)h.S[k].slots.size(), h.S[k].n,
                                          h.S[k].d_vals, t->d_fact, t->d_status, t->num_sms, stream);
+            if (rc == SF_OK) rc = sf_to_float(h.S[3].d_vals, h.d_S4f, h.S[3].n, t->num_sms, stream);
         }
         if (rc != SF_OK) break;
         rc = check_status(t, stream, "sf_6j_table");

@@ -219,6 +219,7 @@ struct VtxDev {
     int32_t ilo[5], di[5];     // intertwiner ranges
     int64_t nshell;            // D^6
     const double* S[5];        // {6j} tables S1..S5
+    const float* S4f;          // S4 rounded to FP32 once (mixed path)
     const SlotDesc* slot[5];
     const double* B[4];        // boosters of edges 2..5: [t][i][k - klo(t)], padded to dkmax
     const int32_t* klo[4];

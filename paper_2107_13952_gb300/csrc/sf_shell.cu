@@ -42,41 +42,38 @@ __device__ __forceinline__ bool shell_selected(const ShellFilter& f, int64_t s) 
     return s >= f.begin && s < f.end;
 }
 
-// C[bt][m][n] (+)= sum_k A[bt][m][k] B[bt][k][n] for a batch of small matrices in shared memory.
-// Every thread owns BM x BN output blocks (independent FMA chains); strides are in doubles.
-template <int BM, int BN, bool ACC>
-__device__ __forceinline__ void blk_gemm(int nbatch, int M, int N, int K, const double* A, int a_bs, int am, int ak,
-                                         const double* B, int b_bs, int bk, int bn, double* C, int c_bs, int cm,
-                                         int cn, int tid, int nth) {
-    const int nbm = (M + BM - 1) / BM, nbn = (N + BN - 1) / BN, per = nbm * nbn;
-    for (int blk = tid; blk < per * nbatch; blk += nth) {
-        const int bt = blk / per, r = blk - bt * per;
-        const int m0 = (r / nbn) * BM, n0 = (r - (r / nbn) * nbn) * BN;
-        const double* Ab = A + bt * a_bs + m0 * am;
-        const double* Bb = B + bt * b_bs + n0 * bn;
-        double* Cb = C + bt * c_bs + m0 * cm + n0 * cn;
-        double acc[BM][BN];
+// C[bt][m][n] (+)= sum_k A[bt][m][k] B[bt][k][n] for a batch of small matrices in shared memory,
+// each thread computing 4 consecutive outputs of the flattened [bt][m][n] index space (no padded
+// lanes for odd sizes; every output sums over k in increasing order). T: element type of A and B,
+// accumulation in T, result added to (ACC) or stored into the double C.
+template <typename T, bool ACC>
+__device__ __forceinline__ void flat_gemm(int nbatch, int M, int N, int K, const T* A, int a_bs, int am, int ak,
+                                          const T* B, int b_bs, int bk, int bn, double* C, int c_bs, int cm, int cn,
+                                          int tid, int nth) {
+    const int MN = M * N, L = nbatch * MN;
+    for (int o0 = 4 * tid; o0 < L; o0 += 4 * nth) {
+        int aoff[4], boff[4], coff[4];
+        T acc[4];
 #pragma unroll
-        for (int i = 0; i < BM; i++)
-#pragma unroll
-            for (int j = 0; j < BN; j++)
-                acc[i][j] = (ACC && m0 + i < M && n0 + j < N) ? Cb[i * cm + j * cn] : 0.0;
+        for (int j = 0; j < 4; j++) {
+            const int o = o0 + j < L ? o0 + j : L - 1;
+            const int bt = o / MN, r = o - bt * MN, m = r / N, n = r - m * N;
+            aoff[j] = bt * a_bs + m * am;
+            boff[j] = bt * b_bs + n * bn;
+            coff[j] = bt * c_bs + m * cm + n * cn;
+            acc[j] = T(0);
+        }
         for (int k = 0; k < K; k++) {
-            double a[BM], b[BN];
 #pragma unroll
-            for (int i = 0; i < BM; i++) a[i] = (m0 + i < M) ? Ab[i * am + k * ak] : 0.0;
-#pragma unroll
-            for (int j = 0; j < BN; j++) b[j] = (n0 + j < N) ? Bb[k * bk + j * bn] : 0.0;
-#pragma unroll
-            for (int i = 0; i < BM; i++)
-#pragma unroll
-                for (int j = 0; j < BN; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            for (int j = 0; j < 4; j++) acc[j] = fma(A[aoff[j] + k * ak], B[boff[j] + k * bk], acc[j]);
         }
 #pragma unroll
-        for (int i = 0; i < BM; i++)
-#pragma unroll
-            for (int j = 0; j < BN; j++)
-                if (m0 + i < M && n0 + j < N) Cb[i * cm + j * cn] = acc[i][j];
+        for (int j = 0; j < 4; j++) {
+            if (o0 + j < L) {
+                if (ACC) C[coff[j]] += (double)acc[j];
+                else C[coff[j]] = (double)acc[j];
+            }
+        }
     }
 }
 
@@ -113,43 +110,6 @@ size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, bool mix
                2ull * mdi * mdk;
     if (mix) n += (((size_t)mdk * mdk * mdi + 3) / 4) * 2 + ((size_t)mdi * mdk + 1) / 2 + 1;
     return n;
-}
-
-// FP32 variant for the mixed path: C[bt][m][n] += (double) sum_k A[bt][m][k] B[bt][k][n], with the
-// products and the sum over k in FP32 and the accumulation into C in FP64
-template <int BM, int BN>
-__device__ __forceinline__ void blk_gemm_f32(int nbatch, int M, int N, int K, const float* A, int a_bs, int am, int ak,
-                                             const float* B, int b_bs, int bk, int bn, double* C, int c_bs, int cm,
-                                             int cn, int tid, int nth) {
-    const int nbm = (M + BM - 1) / BM, nbn = (N + BN - 1) / BN, per = nbm * nbn;
-    for (int blk = tid; blk < per * nbatch; blk += nth) {
-        const int bt = blk / per, r = blk - bt * per;
-        const int m0 = (r / nbn) * BM, n0 = (r - (r / nbn) * nbn) * BN;
-        const float* Ab = A + bt * a_bs + m0 * am;
-        const float* Bb = B + bt * b_bs + n0 * bn;
-        double* Cb = C + bt * c_bs + m0 * cm + n0 * cn;
-        float acc[BM][BN];
-#pragma unroll
-        for (int i = 0; i < BM; i++)
-#pragma unroll
-            for (int j = 0; j < BN; j++) acc[i][j] = 0.0f;
-        for (int k = 0; k < K; k++) {
-            float a[BM], b[BN];
-#pragma unroll
-            for (int i = 0; i < BM; i++) a[i] = (m0 + i < M) ? Ab[i * am + k * ak] : 0.0f;
-#pragma unroll
-            for (int j = 0; j < BN; j++) b[j] = (n0 + j < N) ? Bb[k * bk + j * bn] : 0.0f;
-#pragma unroll
-            for (int i = 0; i < BM; i++)
-#pragma unroll
-                for (int j = 0; j < BN; j++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-        }
-#pragma unroll
-        for (int i = 0; i < BM; i++)
-#pragma unroll
-            for (int j = 0; j < BN; j++)
-                if (m0 + i < M && n0 + j < N) Cb[i * cm + j * cn] += (double)acc[i][j];
-    }
 }
 
 // MIX = false: every phase in FP64 (the FP64 path). MIX = true (the mixed path): the booster
@@ -322,14 +282,16 @@ __global__ void __launch_bounds__(SF_SHELL_THREADS, 1) k_shell(const VtxDev* __r
                         const double sgn3 = (double)(k3 + 1) * ((c3 & 1) ? -1.0 : 1.0);
                         if constexpr (MIX) {
                             const float* sbp = reinterpret_cast<const float*>(sm.SB) + (d * mdk) * XC + xc;
+                            // the FP32 copy of S4 holds the same roundings as converting each entry here
+                            const float* s4f = v.S4f + sd4.off + ((int64_t)ia * sd4.nb + ib0) * sd4.nx + ix;
                             float acc0 = 0.0f, acc1 = 0.0f;
                             if (inbox) {
                                 int c2 = 0;
                                 for (; c2 + 1 < nk2; c2 += 2) {
-                                    acc0 = fmaf((float)__ldg(s4p + (int64_t)c2 * sd4.nx), sbp[c2 * XC], acc0);
-                                    acc1 = fmaf((float)__ldg(s4p + (int64_t)(c2 + 1) * sd4.nx), sbp[(c2 + 1) * XC], acc1);
+                                    acc0 = fmaf(__ldg(s4f + (int64_t)c2 * sd4.nx), sbp[c2 * XC], acc0);
+                                    acc1 = fmaf(__ldg(s4f + (int64_t)(c2 + 1) * sd4.nx), sbp[(c2 + 1) * XC], acc1);
                                 }
-                                if (c2 < nk2) acc0 = fmaf((float)__ldg(s4p + (int64_t)c2 * sd4.nx), sbp[c2 * XC], acc0);
+                                if (c2 < nk2) acc0 = fmaf(__ldg(s4f + (int64_t)c2 * sd4.nx), sbp[c2 * XC], acc0);
                             }
                             reinterpret_cast<float*>(sm.R)[(d * mdk + c3) * XC + xc] = (acc0 + acc1) * (float)sgn3;
                         } else {
@@ -391,11 +353,11 @@ __global__ void __launch_bounds__(SF_SHELL_THREADS, 1) k_shell(const VtxDev* __r
                     }
                     __syncthreads();
                     // D: P[k4][x][i3] = sum_k3u S3s[x][k4][k3u] U[k3u][x][i3]        (batch over x)
-                    blk_gemm<2, 4, false>(nxc, nk4, di3, nk3u, sm.S3s, nk4 * nk3u, nk3u, 1, sm.U, di3, nxc * di3, 1,
+                    flat_gemm<double, false>(nxc, nk4, di3, nk3u, sm.S3s, nk4 * nk3u, nk3u, 1, sm.U, di3, nxc * di3, 1,
                                           sm.P, di3, nxc * di3, 1, tid, nth);
                     __syncthreads();
                     // F: V[k4][k5][i3] += sum_x Q[k5][k4][x] P[k4][x][i3]             (batch over k4)
-                    blk_gemm<2, 4, true>(nk4, nk5, di3, nxc, sm.Q, nxc, nk4 * nxc, 1, sm.P, nxc * di3, di3, 1,
+                    flat_gemm<double, true>(nk4, nk5, di3, nxc, sm.Q, nxc, nk4 * nxc, 1, sm.P, nxc * di3, di3, 1,
                                          sm.V, nk5 * di3, di3, 1, tid, nth);
                 }
                 __syncthreads();
@@ -404,10 +366,10 @@ __global__ void __launch_bounds__(SF_SHELL_THREADS, 1) k_shell(const VtxDev* __r
                     for (int q = tid; q < nk4 * nk5 * di3; q += nth) sm.Vf[q] = (float)sm.V[q];
                     for (int q = tid; q < di4 * nk4; q += nth) sm.B4f[q] = (float)sm.B4[q];
                     __syncthreads();
-                    blk_gemm_f32<2, 4>(nk5, di4, di3, nk4, sm.B4f, 0, nk4, 1, sm.Vf, di3, nk5 * di3, 1,
+                    flat_gemm<float, true>(nk5, di4, di3, nk4, sm.B4f, 0, nk4, 1, sm.Vf, di3, nk5 * di3, 1,
                                        sm.Y, di3, nk5 * di3, 1, tid, nth);
                 } else {
-                    blk_gemm<2, 4, true>(nk5, di4, di3, nk4, sm.B4, 0, nk4, 1, sm.V, di3, nk5 * di3, 1,
+                    flat_gemm<double, true>(nk5, di4, di3, nk4, sm.B4, 0, nk4, 1, sm.V, di3, nk5 * di3, 1,
                                          sm.Y, di3, nk5 * di3, 1, tid, nth);
                 }
             }
