@@ -128,6 +128,33 @@ def vertex_boosters(tj, dl, gamma, r_max, n_panels, order, tables=None):
     return out
 
 
+def random_boosters(tj, dl, seed):
+    """Seeded N(0,1) booster tensors in the layout of ``vertex_boosters``, for contraction tests
+    that bypass the quadrature. Entries outside each triple's k range are zero. One generator
+    ``default_rng(seed)`` draws the edges in the order 2, 3, 4, 5, each as one block
+    [(dl+1)^3, D_i, D_kmax].
+    """
+    from . import vertex
+    rng = np.random.default_rng(seed)
+    n3 = (dl + 1) ** 3
+    out = {}
+    for e in (2, 3, 4, 5):
+        kr = []
+        for t in range(n3):
+            d = (t // ((dl + 1) ** 2), (t // (dl + 1)) % (dl + 1), t % (dl + 1))
+            tl6 = dict(zip(vertex.FREE, [tj[vertex.FACES.index(f)] for f in vertex.FREE]))
+            for f, df in zip(vertex.EDGE_TRIPLES[e], d):
+                tl6[f] += 2 * df
+            kr.append(wigner.pair_range(*vertex.edge_spins(tj, tuple(tl6[f] for f in vertex.FREE))[e][1]))
+        di = len(wigner.pair_range(*vertex.edge_spins(tj, tuple(tj[4:]))[e][0]))
+        dk = max([len(k) for k in kr] + [1])
+        B = rng.standard_normal((n3, di, dk))
+        for t, k in enumerate(kr):
+            B[t, :, len(k):] = 0.0
+        out[e] = {"B": B, "klo": np.array([k[0] if k else 0 for k in kr], dtype=np.int64), "maxim": 0.0}
+    return out
+
+
 def identity_boosters(tj):
     """SU(2) BF limit at dl = 0: (2k+1) B_e[i, k] = delta_ik, so A_v = prod sqrt(2i+1) {15j}."""
     from . import vertex

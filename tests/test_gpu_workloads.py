@@ -1,0 +1,171 @@
+"""Parity on the benchmarked workloads at their full sizes, in the launch configuration of the
+benchmark, on outputs the oracle can compute; plus the small workload whole.
+
+* all spins 8, dl 10 (largest vertex of the homogeneous sweep) and all spins 4, dl 20 (85,766,121
+  shells): partial sums over seeded 10^4-shell subsets of the non-empty shells, through the
+  shell-list entry point, against the oracle's sums stored by ``tests/golden/make_subsets.py``;
+  FP64 path within 1e-10 and mixed path within its stated 1e-6 (normwise relative);
+* d-table entries of the spin-8 vertex on the full 2000-node rule against the closed form;
+* all spins 1, dl 0..3: boosters on the full 2000-node rule and the whole tensor, end to end;
+* 256 irregular vertices in one batched launch: small vertices against the oracle, sampled ones
+  against single-vertex launches, both precisions.
+
+Where the oracle's arbitrary-precision d-tables on the 2000-node rule would take hours (large
+spins), seeded random boosters are injected; the quadrature itself is checked on the full rule
+for spin 1 here and on shorter rules for larger spins in test_gpu_parity.py.
+"""
+import os
+
+import mpmath
+import numpy as np
+import pytest
+
+import paper_2107_13952_gb300 as sf
+from oracle import booster as ob
+from oracle import dfunc
+from oracle import quadrature as oq
+from oracle import vertex as ov
+from paper_2107_13952_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+FULL_RULE = inputs.RULE_DEFAULT
+FP64_BOUND = 1e-10
+MIXED_BOUND = 1e-6
+
+
+def _upload(t, vtx, bs):
+    for e in (2, 3, 4, 5):
+        assert tuple(sf.booster_shape(t, vtx, e)) == bs[e]["B"].shape
+        sf.sf_boosters_upload(t, vtx, e, bs[e]["B"])
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("name", ["sweep_j8_dl10_subset", "large_shell_j4_dl20_subset"])
+def test_full_size_shell_subsets(lib, name):
+    g = np.load(os.path.join(GOLDEN, name + ".npz"))
+    tj, dl, gamma = tuple(int(v) for v in g["two_j"]), int(g["dl"]), float(g["gamma"])
+    t = sf.sf_6j_table([sf.vertex(tj, gamma, dl)])
+    bs = ob.random_boosters(tj, dl, int(g["booster_seed"]))
+    _upload(t, 0, bs)
+    shells = g["shells"]
+    a64 = sf.sf_vertex_amplitude(t, shell_list=shells)[0].cpu().numpy()
+    amx = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED, shell_list=shells)[0].cpu().numpy()
+    if "idx" in g:      # large tensor: a seeded sample of entries plus the norm of the whole
+        for a, bound in ((a64, FP64_BOUND), (amx, MIXED_BOUND)):
+            assert abs(np.linalg.norm(a) - float(g["A_norm"])) <= bound * float(g["A_norm"])
+            assert _rel(a.reshape(-1)[g["idx"]], g["A"]) <= bound
+    else:
+        assert _rel(a64, g["A"]) <= FP64_BOUND
+        assert _rel(amx, g["A"]) <= MIXED_BOUND
+
+
+def test_dtable_entries_full_rule(lib):
+    tj, dl, gamma = (16,) * 10, 10, 1.2
+    t = sf.sf_6j_table([sf.vertex(tj, gamma, dl)])
+    sf.sf_boosters(t, FULL_RULE)
+    x = sf.table_copy(t, 0, sf.SF_TAB_NODES, 0).numpy()
+    nn = len(x)
+    assert nn == FULL_RULE[1] * FULL_RULE[2]
+    rho = gamma * (8 + 1)
+    rng = np.random.default_rng(5)
+    for f in (4, 8, 9):
+        tab = sf.table_copy(t, 0, sf.SF_TAB_D, f).numpy().reshape(dl + 1, 17, nn)
+        scale = np.abs(tab).max()
+        for _ in range(12):
+            p, im, n = int(rng.integers(0, dl + 1)), int(rng.integers(0, 17)), int(rng.integers(0, nn))
+            ref = complex(dfunc.DClosed(16, rho, 16 + 2 * p, -16 + 2 * im).eval(-mpmath.log(mpmath.mpf(x[n])), 20))
+            assert abs(tab[p, im, n] - ref) <= 1e-12 * scale, (f, p, im, n)
+
+
+@pytest.fixture(scope="module")
+def spin1_full_rule():
+    xs, ws = oq.rule_nodes(*FULL_RULE)
+    return xs, ws, ob.face_tables((2,) * 10, 3, 1.2, xs)
+
+
+def test_simplex_j1_full_rule_end_to_end(lib, spin1_full_rule):
+    # all spins 1: the oracle's boosters on the 2000-node rule for dl = 3 contain those of dl < 3
+    xs, ws, tabs = spin1_full_rule
+    tj, gamma = (2,) * 10, 1.2
+    ref_b = ob.vertex_boosters(tj, 3, gamma, *FULL_RULE, tables=tabs)
+    t3 = sf.sf_6j_table([sf.vertex(tj, gamma, 3)])
+    sf.sf_boosters(t3, FULL_RULE)
+    for e in (2, 3, 4, 5):
+        got = sf.sf_boosters_download(t3, 0, e).cpu().numpy()
+        ref = ref_b[e]["B"]
+        assert got.shape == ref.shape
+        assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max(), e
+    for dl in range(4):
+        spec = inputs.simplex_j1(dl)
+        t = sf.sf_6j_table([sf.vertex(spec["two_j"], spec["gamma"], dl)])
+        sf.sf_boosters(t, FULL_RULE)
+        A = sf.sf_vertex_amplitude(t)[0].cpu().numpy()
+        ref = ov.vertex_amplitude(tj, dl, ob.vertex_boosters(tj, dl, gamma, *FULL_RULE, tables=tabs))
+        assert _rel(A, ref) <= FP64_BOUND, dl
+
+
+BATCH_SHELL_END = 729     # per vertex: the first 729 group-major shells (all of them for dl <= 2)
+
+
+@pytest.fixture(scope="module")
+def batch256(lib):
+    batch = inputs.random_batch(256, seed=0)
+    verts = [sf.vertex(b["two_j"], b["gamma"], b["dl"]) for b in batch]
+    t = sf.sf_6j_table(verts)
+    bss = [ob.random_boosters(b["two_j"], b["dl"], 1000 + i) for i, b in enumerate(batch)]
+    for i in range(len(batch)):
+        _upload(t, i, bss[i])
+    return batch, verts, t, bss
+
+
+def test_random_batch_256_against_oracle(lib, batch256):
+    batch, verts, t, bss = batch256
+    out64 = sf.sf_vertex_amplitude(t, shell_end=BATCH_SHELL_END)
+    outmx = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED, shell_end=BATCH_SHELL_END)
+    small = [i for i, b in enumerate(batch) if b["dl"] <= 2]
+    assert small
+    rng = np.random.default_rng(7)
+    for i in rng.choice(small, size=min(8, len(small)), replace=False):
+        b = batch[int(i)]
+        ref = ov.vertex_amplitude(b["two_j"], b["dl"], bss[int(i)])
+        assert _rel(out64[int(i)].cpu().numpy(), ref) <= FP64_BOUND
+        assert _rel(outmx[int(i)].cpu().numpy(), ref) <= MIXED_BOUND
+
+
+def test_random_batch_256_against_single_launches(lib, batch256):
+    batch, verts, t, bss = batch256
+    out64 = sf.sf_vertex_amplitude(t, shell_end=BATCH_SHELL_END)
+    outmx = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED, shell_end=BATCH_SHELL_END)
+    rng = np.random.default_rng(8)
+    for i in (int(v) for v in rng.choice(len(batch), size=8, replace=False)):
+        t1 = sf.sf_6j_table([verts[i]])
+        _upload(t1, 0, bss[i])
+        s64 = sf.sf_vertex_amplitude(t1, shell_end=BATCH_SHELL_END)[0]
+        smx = sf.sf_vertex_amplitude(t1, precision=sf.SF_MIXED, shell_end=BATCH_SHELL_END)[0]
+        n = float(s64.norm())
+        if n == 0.0:
+            assert float(out64[i].abs().max()) == 0.0
+            continue
+        assert float((out64[i] - s64).norm()) <= 1e-13 * n
+        assert float((outmx[i] - smx).norm()) <= 1e-6 * n
+
+
+def test_random_batch_boosters_match_single(lib):
+    # batched quadrature (16 irregular vertices, short rule) equals per-vertex launches
+    batch = inputs.random_batch(16, seed=3)
+    verts = [sf.vertex(b["two_j"], b["gamma"], b["dl"]) for b in batch]
+    t = sf.sf_6j_table(verts)
+    rule = (40.0, 4, 10)
+    sf.sf_boosters(t, rule)
+    for i in (0, 5, 11):
+        t1 = sf.sf_6j_table([verts[i]])
+        sf.sf_boosters(t1, rule)
+        for e in (2, 3, 4, 5):
+            a = sf.sf_boosters_download(t, i, e)
+            b = sf.sf_boosters_download(t1, 0, e)
+            assert float((a - b).abs().max()) <= 1e-14 * max(float(b.abs().max()), 1e-300)
