@@ -30,14 +30,18 @@ SWEEP = [(lam, 10) for lam in range(1, 17)]
 GAMMA = 1.2
 # FP64 FMA pipe of the GB300: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.070 GHz (max SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-# DRAM traffic of one shell-sum launch from ncu (profiles/shell_fp64_sweep_slice.md), valid for the
-# kernel source whose sha1 prefix is recorded beside it; None until captured.
-NCU_TRAFFIC = {"sha1": None, "bytes_per_launch": None}
+# DRAM bytes (read + write) of the benchmark's shell-sum launch from one ncu capture per precision
+# (profiles/k_shell_mixed_sweep_traffic.md), valid while the kernel source hashes to "sha1".
+NCU_TRAFFIC = {"sha1": "f105b5962be0", "bytes_per_launch": {"mixed": 135627228928 + 161291776, "fp64": None}}
 
 
 def kernel_sha1():
+    """sha1 prefix of the shell kernel's source: sf_shell.cu up to its host-side launchers (the
+    kernel and the device helpers it uses)."""
     p = os.path.join(ROOT, "paper_2107_13952_gb300", "csrc", "sf_shell.cu")
-    return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
+    src = open(p, "rb").read()
+    cut = src.find(b"int sf_shell_prepare(")
+    return hashlib.sha1(src[:cut] if cut > 0 else src).hexdigest()[:12]
 
 
 # ------------------------------------------------------------------------------------------
@@ -226,6 +230,45 @@ def oracle_rate(seconds, seed=0):
 
 
 # ------------------------------------------------------------------------------------------
+def batched_measure(shells, steps=3):
+    """The batched workload: 256 irregular vertices (ten spins uniform in {1/2..6}, redrawn until all
+    five intertwiner ranges are non-empty; dl uniform in 0..12; gamma from {0.1, 1.2, 5.0}; seed 0),
+    the first ``shells`` shells of every vertex, as one planned launch (persistent shell kernel +
+    one reduction) replayed as a CUDA graph, tiling autotuned on a sample, in both precisions."""
+    import torch
+    import paper_2107_13952_gb300 as sf
+    from paper_2107_13952_gb300 import inputs
+    batch = inputs.random_batch(256, seed=0)
+    t = sf.sf_6j_table([sf.vertex(b["two_j"], b["gamma"], b["dl"]) for b in batch])
+    sf.sf_boosters(t, RULE)
+    n = sum(min(shells, (b["dl"] + 1) ** 6) for b in batch)
+    stream = torch.cuda.current_stream()
+    res, outs = {}, {}
+    for name, prec in (("fp64", sf.SF_FP64), ("mixed", sf.SF_MIXED)):
+        plan = sf.Plan(t, prec, 0, shells)
+        tiling = plan.autotune(min(shells, 2048))
+        plan.graph_launch()
+        plan.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.graph_launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[name] = {"value": n / (ms / 1e3), "unit": "shells/s", "ms_per_launch": ms,
+                     "tiling": {"x_chunk": tiling[0], "items_per_sm": tiling[1]}}
+        outs[name] = [o.clone() for o in plan.outputs]
+        del plan
+    num = sum(float((a - b).norm()) ** 2 for a, b in zip(outs["mixed"], outs["fp64"])) ** 0.5
+    den = sum(float(b.norm()) ** 2 for b in outs["fp64"]) ** 0.5
+    return {"workload": "256 irregular vertices (spins 1/2..6, dl 0..12, gamma 0.1/1.2/5.0, seed 0), shells "
+                        "[0, %d) of every vertex, %d shells in all; one CUDA-graph replay of a planned launch "
+                        "per step, %d steps" % (shells, n, steps),
+            "fp64": res["fp64"], "mixed": res["mixed"],
+            "mixed_vs_fp64_rel_err": num / den if den > 0 else None}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -237,6 +280,8 @@ def main():
     ap.add_argument("--slices", type=int, default=16, help="steps per full pass over the sweep")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched-shells", type=int, default=16384,
+                    help="shells per vertex of the 256-vertex batched measurement (0: skip)")
     ap.add_argument("--case", default=None, help="lambda:groups:precision -- one shell-sum launch (profiling)")
     args = ap.parse_args()
 
@@ -396,8 +441,8 @@ def main():
     kern_s = sum(kms_all) / 1e3
     achieved = flops / kern_s / 1e12 if kern_s > 0 else None
     traffic = None
-    if NCU_TRAFFIC["sha1"] == kernel_sha1() and NCU_TRAFFIC["bytes_per_launch"]:
-        traffic = NCU_TRAFFIC["bytes_per_launch"]
+    if NCU_TRAFFIC["sha1"] == kernel_sha1():
+        traffic = NCU_TRAFFIC["bytes_per_launch"].get(args.precision)
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
@@ -405,6 +450,10 @@ def main():
         cpu = {"value": r, "unit": "shells/s", "cores": cores, "kind": "oracle",
                "sample": "%d shells drawn uniformly from the sweep (%.1f s on %d processes), boosters random "
                          "(shell-sum phase only)" % (n, el, cores)}
+
+    batched = None
+    if args.batched_shells > 0 and world == 1:
+        batched = batched_measure(args.batched_shells)
 
     d2h = sum(h.numel() * 8 for h in host)
     h2d = len(verts) * 56
@@ -434,6 +483,7 @@ def main():
         "path": args.precision,
         other_name: {"value": n_o * world / (ms_other / 1e3), "unit": "shells/s", "ms_per_step": ms_other,
                      "kernel_ms_per_step": kms_o},
+        "batched": batched,
         "mixed_vs_fp64": {"rel_err": rel_err, "stated_bound": 1e-6,
                           "metric": "||A_mixed - A_fp64|| / ||A_fp64|| over the 16 vertices of one slice"},
     }

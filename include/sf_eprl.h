@@ -148,6 +148,60 @@ int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t shell_begi
 int sf_vertex_amplitude_noalloc(sf_tables* t, int64_t shell_begin, int64_t shell_end, double* const* A_out,
                                 cudaStream_t stream);
 
+/* Planned shell sums: many vertex tensors in one persistent launch, replayable as a CUDA graph.
+ * The paper distributes the shell loops of one vertex over nodes and cores (Sec. 3,
+ * "Parallelization") and names routines for many vertex tensors with few shells each as future
+ * work (Sec. 6); a plan serves both. It fixes what the host decides for one sf_vertex_amplitude
+ * call over a shell range (the tables, outputs, precision, range, work items and the kernel's
+ * tiling) and owns its device scratch, so that running it issues only asynchronous device work:
+ * one memset, the persistent shell kernel and one reduction kernel over every vertex's tiles.
+ *
+ * sf_tiling: x_chunk = auxiliary spins x per staged chunk of the {6j} contractions (1..16; the
+ *   shared-memory footprint grows with it); items_per_sm = target number of work items per SM
+ *   (granularity of the cost-balanced split of tiles x groups). 0 selects the default (largest
+ *   x_chunk that fits, 8 items per SM). */
+typedef struct sf_tiling {
+    int32_t x_chunk;
+    int32_t items_per_sm;
+} sf_tiling;
+typedef struct sf_plan sf_plan;
+
+/* Create a plan for the range [shell_begin, shell_end) of every vertex of t (as in
+ * sf_vertex_amplitude). tiling: host pointer or NULL (defaults). A_out: host array of device
+ * output pointers, fixed for the plan's lifetime. Allocates the plan's scratch and copies its
+ * schedule to the device synchronously. t must outlive the plan; tables and boosters are read at
+ * run time, so re-uploaded boosters of the same shapes are picked up by later runs.
+ * Errors: SF_ERR_ARG (null pointers, boosters missing, bad tiling), SF_ERR_LIMIT (dimensions or
+ * x_chunk do not fit the kernel), SF_ERR_OOM. */
+int sf_plan_create(sf_tables* t, sf_precision precision, int64_t shell_begin, int64_t shell_end,
+                   const sf_tiling* tiling, double* const* A_out, sf_plan** out);
+
+/* Time candidate tilings (x_chunk 16, 12, 8, 6, 4 x items_per_sm 4, 8, 16, 32) on the first
+ * sample_shells shells of the plan's range of every vertex (best of two runs after a warm-up,
+ * CUDA events on stream) and rebuild the plan with the fastest; *chosen (optional) receives it.
+ * Overwrites the plan's outputs; synchronises the stream; drops a captured graph. */
+int sf_plan_autotune(sf_plan* plan, int64_t sample_shells, sf_tiling* chosen, cudaStream_t stream);
+
+/* Run the plan on stream: stream work only (no allocation, no host copy, no synchronisation), so
+ * the call itself may be captured into a CUDA graph by the caller. Results: the outputs given at
+ * creation, overwritten, equal to sf_vertex_amplitude's over the same range (fixed-order
+ * reductions; bitwise reproducible for a fixed tiling). Launch errors are returned; errors
+ * during execution surface at the next synchronisation (sf_plan_sync). */
+int sf_plan_run(sf_plan* plan, cudaStream_t stream);
+
+/* The same run as one CUDA graph: the first call captures sf_plan_run on a private stream and
+ * instantiates it; every call launches the graph on stream. */
+int sf_plan_graph_launch(sf_plan* plan, cudaStream_t stream);
+
+/* Wait for stream and report any CUDA error of the plan's runs. */
+int sf_plan_sync(sf_plan* plan, cudaStream_t stream);
+
+/* The plan's effective tiling, work-item count, persistent grid size and scratch bytes (each
+ * output optional). */
+int sf_plan_info(const sf_plan* plan, sf_tiling* tiling, int64_t* n_items, int32_t* grid, int64_t* scratch_bytes);
+
+void sf_plan_free(sf_plan* plan);
+
 /* Boundary-contracted amplitude and its adjoint (single-vertex tables):
  *   a = sum_i A[i1..i5] psi_1[i1] psi_2[i2] psi_3[i3] psi_4[i4] psi_5[i5]
  * (the paper's contraction of a vertex tensor with boundary intertwiner vectors, Sec. 3 usage),

@@ -26,7 +26,9 @@ SF_TAB_6J, SF_TAB_6J_SLOTS, SF_TAB_D, SF_TAB_NODES = 1, 2, 3, 4
 EXPORTS = ("sf_version", "sf_last_error", "sf_intertwiner_ranges", "sf_num_shells", "sf_6j_table",
            "sf_boosters", "sf_booster_shape", "sf_boosters_upload", "sf_boosters_download",
            "sf_vertex_amplitude", "sf_vertex_adjoint", "sf_table_size", "sf_table_copy", "sf_kernel_launches",
-           "sf_last_kernel_ms", "sf_vertex_amplitude_noalloc", "sf_tables_free")
+           "sf_last_kernel_ms", "sf_vertex_amplitude_noalloc", "sf_plan_create", "sf_plan_autotune",
+           "sf_plan_run", "sf_plan_graph_launch", "sf_plan_sync", "sf_plan_info", "sf_plan_free",
+           "sf_tables_free")
 
 
 class SfError(RuntimeError):
@@ -41,6 +43,10 @@ class sf_vertex(ctypes.Structure):
 
 class sf_quad_rule(ctypes.Structure):
     _fields_ = [("r_max", ctypes.c_double), ("n_panels", ctypes.c_int32), ("order", ctypes.c_int32)]
+
+
+class sf_tiling(ctypes.Structure):
+    _fields_ = [("x_chunk", ctypes.c_int32), ("items_per_sm", ctypes.c_int32)]
 
 
 def vertex(two_j, gamma, dl):
@@ -71,6 +77,15 @@ def _declare(lib):
         "sf_kernel_launches": (I64, []),
         "sf_last_kernel_ms": (D, [I32]),
         "sf_vertex_amplitude_noalloc": (ctypes.c_int, [P, I64, I64, ctypes.POINTER(P), P]),
+        "sf_plan_create": (ctypes.c_int, [P, ctypes.c_int, I64, I64, ctypes.POINTER(sf_tiling), ctypes.POINTER(P),
+                                          ctypes.POINTER(P)]),
+        "sf_plan_autotune": (ctypes.c_int, [P, I64, ctypes.POINTER(sf_tiling), P]),
+        "sf_plan_run": (ctypes.c_int, [P, P]),
+        "sf_plan_graph_launch": (ctypes.c_int, [P, P]),
+        "sf_plan_sync": (ctypes.c_int, [P, P]),
+        "sf_plan_info": (ctypes.c_int, [P, ctypes.POINTER(sf_tiling), ctypes.POINTER(I64), ctypes.POINTER(I32),
+                                        ctypes.POINTER(I64)]),
+        "sf_plan_free": (None, [P]),
         "sf_tables_free": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -207,6 +222,54 @@ def sf_vertex_amplitude(tables, precision=SF_FP64, shell_begin=0, shell_end=2 **
     _check(lib.sf_vertex_amplitude(tables.ptr, int(precision), int(shell_begin), int(shell_end), lp, nl, ptrs,
                                    _stream(stream)))
     return outs
+
+
+class Plan:
+    """Owner of an ``sf_plan*``: one shell sum over a range of every vertex of ``tables``, set up
+    once and run many times (``run``), optionally as a CUDA graph (``graph_launch``). Keeps the
+    tables and the output tensors alive; ``outputs`` holds one float64 cuda tensor per vertex."""
+
+    def __init__(self, tables, precision=SF_FP64, shell_begin=0, shell_end=2 ** 63 - 1, tiling=None):
+        import torch
+        lib = load()
+        self.tables = tables
+        self.outputs = []
+        for v in tables.vertices:
+            _, dim = intertwiner_ranges(list(v.two_j), v.gamma, v.dl)
+            self.outputs.append(torch.empty(dim, dtype=torch.float64, device="cuda"))
+        ptrs = (ctypes.c_void_p * len(self.outputs))(*[o.data_ptr() for o in self.outputs])
+        tl = sf_tiling(*(tiling or (0, 0)))
+        out = ctypes.c_void_p()
+        _check(lib.sf_plan_create(tables.ptr, int(precision), int(shell_begin), int(shell_end), ctypes.byref(tl), ptrs,
+                                  ctypes.byref(out)))
+        self.ptr = out
+
+    def autotune(self, sample_shells, stream=None):
+        tl = sf_tiling()
+        _check(load().sf_plan_autotune(self.ptr, int(sample_shells), ctypes.byref(tl), _stream(stream)))
+        return (tl.x_chunk, tl.items_per_sm)
+
+    def run(self, stream=None):
+        _check(load().sf_plan_run(self.ptr, _stream(stream)))
+        return self.outputs
+
+    def graph_launch(self, stream=None):
+        _check(load().sf_plan_graph_launch(self.ptr, _stream(stream)))
+        return self.outputs
+
+    def sync(self, stream=None):
+        _check(load().sf_plan_sync(self.ptr, _stream(stream)))
+
+    def info(self):
+        tl, n, g, b = sf_tiling(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
+        _check(load().sf_plan_info(self.ptr, ctypes.byref(tl), ctypes.byref(n), ctypes.byref(g), ctypes.byref(b)))
+        return {"x_chunk": tl.x_chunk, "items_per_sm": tl.items_per_sm, "n_items": n.value, "grid": g.value,
+                "scratch_bytes": b.value}
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _LIB is not None:
+            _LIB.sf_plan_free(self.ptr)
+            self.ptr = None
 
 
 def kernel_launches():

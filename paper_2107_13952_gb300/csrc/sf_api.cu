@@ -5,31 +5,6 @@
 #include <cmath>
 #include <string>
 
-// kernels' launchers (defined in the other translation units)
-int sf_fact_table_build(dd* F, cudaStream_t s);
-int sf_sixj_table_build(int table_id, const VtxDev* d_v, const SlotDesc* d_slots, int nslots, int64_t n,
-                        double* d_out, const dd* F, int* d_status, int num_sms, cudaStream_t s);
-int sf_to_float(const double* d_in, float* d_out, int64_t n, int num_sms, cudaStream_t s);
-int sf_rule_build(const sf_quad_rule* q, double* d_gl, double* d_x, double* d_w, double* d_r, double* d_W,
-                  cudaStream_t s);
-int sf_dtable_build(int tk, double gamma, int nl, int nnodes, const double* d_r, const double* d_gl, double2* d_out,
-                    cudaStream_t s);
-size_t sf_booster_smem(int tj1, int tj2, int tj3, int tj4, int nk);
-int sf_booster_build(const VtxDev* d_v, int edge, int ntrip, size_t smem, const double* d_W, int nnodes,
-                     const dd* F, double* d_Aj, double* d_Cj, double* d_B, int* d_status, cudaStream_t s);
-size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, bool mix = false);
-int sf_shell_fp64_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax, const WorkItem* d_items,
-                         int n_items, int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s);
-int sf_shell_mixed_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax, const WorkItem* d_items,
-                          int n_items, int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s);
-int sf_reduce_launch(const VtxDev* d_v, int vtx, int ntiles, const WorkItem* d_items, int item0, int nchunk,
-                     const double* d_part, double* A, cudaStream_t s);
-int sf_bitmap_launch(const int64_t* d_list, int64_t n, int64_t nshell, uint32_t* d_bm, cudaStream_t s);
-int sf_adjoint_launch(const VtxDev* d_v, const VtxDev& h, const double* const psi[5], double* a_out,
-                      double* const grad_psi[5], double* const grad_B[4], void* scratch, size_t scratch_bytes,
-                      int num_sms, cudaStream_t s);
-size_t sf_adjoint_scratch_bytes(const VtxDev& h);
-
 // ----------------------------------------------------------------------------------------------
 // errors
 // ----------------------------------------------------------------------------------------------
@@ -111,8 +86,6 @@ static int dev_alloc(sf_tables* t, void** p, size_t bytes) {
     t->owned.push_back(*p);
     return SF_OK;
 }
-
-#define SF_TRY(x) do { int r_ = (x); if (r_ != SF_OK) return r_; } while (0)
 
 // ----------------------------------------------------------------------------------------------
 // argument checks and ranges
@@ -490,29 +463,29 @@ static int grow_scratch(sf_tables* t, size_t bytes) {
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t shell_begin, int64_t shell_end,
-                                   const int64_t* shell_list, int64_t n_list, double* const* A_out, cudaStream_t stream) {
-    if (!t || !A_out) return sf_set_error(SF_ERR_ARG, "null argument");
-    if (precision != SF_FP64 && precision != SF_MIXED) return sf_set_error(SF_ERR_ARG, "unknown precision");
-    if (shell_list && t->vs.size() != 1) return sf_set_error(SF_ERR_ARG, "a shell list needs single-vertex tables");
-    if (shell_list && n_list < 0) return sf_set_error(SF_ERR_ARG, "negative list length");
-    if (!shell_list && shell_begin < 0) return sf_set_error(SF_ERR_ARG, "negative shell_begin");
-    for (size_t i = 0; i < t->vs.size(); i++) {
-        if (!t->vs[i].boosters_ready) return sf_set_error(SF_ERR_ARG, "boosters of vertex %zu were never computed or uploaded", i);
-        if (!A_out[i]) return sf_set_error(SF_ERR_ARG, "null output for vertex %zu", i);
-    }
-    // work items: per vertex, tiles (i1, i2) x chunks of the (l25, l35, l45) groups. Chunk counts
-    // scale with the estimated cost of a tile so items are of similar size, and the costliest
-    // vertices are queued first (the kernel takes items in order from an atomic counter).
+// Work decomposition of one shell sum: per vertex, output tiles (i1, i2) x chunks of the
+// (l25, l35, l45) groups in the requested range. Chunk counts scale with the estimated cost of a
+// tile so that items are of similar size (about items_per_sm of them per SM overall), and the
+// costliest vertices are queued first (the kernel takes items in order from an atomic counter).
+// One ReduceJob per output tile names its chunks, which are consecutive items.
+struct ShellSchedule {
+    std::vector<WorkItem> items;
+    std::vector<ReduceJob> jobs;
+    int64_t part_total = 0;
+    int mdi = 1, mdk = 1, mk3u = 1, Dmax = 1;
+};
+
+static int schedule_shells(const sf_tables* t, bool whole_range, int64_t shell_begin, int64_t shell_end,
+                           int items_per_sm, double* const* A_out, ShellSchedule* sc) {
     const int nv = (int)t->vs.size();
     std::vector<int64_t> g_lo(nv), g_n(nv);
     std::vector<double> tile_cost(nv);
     double total_cost = 0.0;
     for (int i = 0; i < nv; i++) {
-        VertexHost& h = t->vs[i];
+        const VertexHost& h = t->vs[i];
         const int64_t per_group = (int64_t)h.D * h.D * h.D;   // shells are group-major: D^3 per group
         int64_t lo = 0, hi = h.ngroups;
-        if (!shell_list) {
+        if (!whole_range) {
             int64_t b = std::min<int64_t>(std::max<int64_t>(shell_begin, 0), h.nshell);
             int64_t e = std::min<int64_t>(std::max<int64_t>(shell_end, 0), h.nshell);
             lo = b / per_group;
@@ -524,23 +497,20 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
         tile_cost[i] = (double)g_n[i] * per_group * dmax * dmax * dmax * dmax;
         total_cost += tile_cost[i] * h.di[0] * h.di[1];
     }
-    const double item_cost = std::max(1.0, total_cost / ((double)t->num_sms * 8.0));
+    const double item_cost = std::max(1.0, total_cost / ((double)t->num_sms * std::max(1, items_per_sm)));
     std::vector<int> order(nv);
     for (int i = 0; i < nv; i++) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tile_cost[a] > tile_cost[b]; });
-    std::vector<WorkItem> items;
     std::vector<int> item0(nv), nchunk(nv);
-    int64_t part_total = 0;
-    int mdi = 1, mdk = 1, mk3u = 1, Dmax = 1;
     for (int i : order) {
-        VertexHost& h = t->vs[i];
+        const VertexHost& h = t->vs[i];
         const int64_t ntile = (int64_t)h.di[0] * h.di[1];
         const int64_t ng = g_n[i];
         int C = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(ng, 1),
                                                             (int64_t)std::ceil(tile_cost[i] / item_cost)));
-        item0[i] = (int)items.size();
+        item0[i] = (int)sc->items.size();
         nchunk[i] = C;
-        int64_t per = (int64_t)h.di[2] * h.di[3] * h.di[4];
+        const int64_t per = (int64_t)h.di[2] * h.di[3] * h.di[4];
         for (int64_t tile = 0; tile < ntile; tile++) {
             for (int c = 0; c < C; c++) {
                 WorkItem w{};
@@ -549,41 +519,78 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
                 w.i2 = (int)(tile % h.di[1]);
                 w.g0 = (int)(g_lo[i] + ng * c / C);
                 w.g1 = (int)(g_lo[i] + ng * (c + 1) / C);
-                w.part_off = part_total;
-                part_total += per;
-                items.push_back(w);
+                w.part_off = sc->part_total;
+                sc->part_total += per;
+                sc->items.push_back(w);
             }
         }
         if ((int64_t)h.di[3] * ((h.di[4] + 1) / 2) * ((h.di[2] + 3) / 4) > 4 * 256)
             return sf_set_error(SF_ERR_LIMIT, "vertex %d: intertwiner dimensions too large for the register-resident tile", i);
-        for (int e = 2; e < 5; e++) mdi = std::max(mdi, (int)h.di[e]);
-        for (int e = 0; e < 4; e++) mdk = std::max(mdk, (int)h.dkmax[e]);
-        mk3u = std::max(mk3u, h.mk3u);
-        Dmax = std::max(Dmax, h.D);
+        for (int e = 2; e < 5; e++) sc->mdi = std::max(sc->mdi, (int)h.di[e]);
+        for (int e = 0; e < 4; e++) sc->mdk = std::max(sc->mdk, (int)h.dkmax[e]);
+        sc->mk3u = std::max(sc->mk3u, h.mk3u);
+        sc->Dmax = std::max(sc->Dmax, h.D);
     }
-    if (items.size() > (size_t)0x7FFFFFFF) return sf_set_error(SF_ERR_LIMIT, "too many work items");
-    // x chunk: keep the shared-memory footprint under ~200 KB
+    if (sc->items.size() > (size_t)0x7FFFFFFF) return sf_set_error(SF_ERR_LIMIT, "too many work items");
+    for (int i = 0; i < nv; i++) {
+        const VertexHost& h = t->vs[i];
+        const int64_t n3 = (int64_t)h.di[2] * h.di[3] * h.di[4];
+        for (int tile = 0; tile < h.di[0] * h.di[1]; tile++) {
+            ReduceJob j{};
+            j.vtx = i;
+            j.tile = tile;
+            j.item0 = item0[i] + tile * nchunk[i];
+            j.nchunk = nchunk[i];
+            j.A = A_out[i] + tile * n3;
+            sc->jobs.push_back(j);
+        }
+    }
+    return SF_OK;
+}
+
+// largest x chunk (<= max_xc) whose shared-memory footprint stays under ~200 KB; 0 if none
+static int choose_xc(const ShellSchedule& sc, bool mix, int max_xc) {
+    for (int xc = std::max(1, std::min(max_xc, 16)); xc >= 1; xc--)
+        if (sf_shell_smem_doubles(sc.mdi, sc.mdk, sc.mk3u, xc, sc.Dmax, mix) * sizeof(double) <= 200 * 1024) return xc;
+    return 0;
+}
+
+#define SF_DEFAULT_ITEMS_PER_SM 8
+
+extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t shell_begin, int64_t shell_end,
+                                   const int64_t* shell_list, int64_t n_list, double* const* A_out, cudaStream_t stream) {
+    if (!t || !A_out) return sf_set_error(SF_ERR_ARG, "null argument");
+    if (precision != SF_FP64 && precision != SF_MIXED) return sf_set_error(SF_ERR_ARG, "unknown precision");
+    if (shell_list && t->vs.size() != 1) return sf_set_error(SF_ERR_ARG, "a shell list needs single-vertex tables");
+    if (shell_list && n_list < 0) return sf_set_error(SF_ERR_ARG, "negative list length");
+    if (!shell_list && shell_begin < 0) return sf_set_error(SF_ERR_ARG, "negative shell_begin");
+    for (size_t i = 0; i < t->vs.size(); i++) {
+        if (!t->vs[i].boosters_ready) return sf_set_error(SF_ERR_ARG, "boosters of vertex %zu were never computed or uploaded", i);
+        if (!A_out[i]) return sf_set_error(SF_ERR_ARG, "null output for vertex %zu", i);
+    }
+    ShellSchedule sc;
+    SF_TRY(schedule_shells(t, shell_list != nullptr, shell_begin, shell_end, SF_DEFAULT_ITEMS_PER_SM, A_out, &sc));
     const bool mix = precision == SF_MIXED;
-    int xc = 16;
-    while (xc > 1 && sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax, mix) * sizeof(double) > 200 * 1024) xc--;
-    if (sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax, mix) * sizeof(double) > 200 * 1024)
-        return sf_set_error(SF_ERR_LIMIT, "intertwiner dimensions too large for the shell kernel");
-    // scratch: items | counter | bitmap | partials
-    int64_t nshell0 = t->vs[0].nshell;
-    size_t o_items = 0;
-    size_t o_counter = align256(o_items + items.size() * sizeof(WorkItem));
-    size_t o_bitmap = align256(o_counter + sizeof(int));
-    size_t bm_bytes = shell_list ? (size_t)((nshell0 + 31) / 32) * sizeof(uint32_t) : 0;
-    size_t o_list = align256(o_bitmap + bm_bytes);
-    size_t list_bytes = shell_list ? (size_t)std::max<int64_t>(1, n_list) * sizeof(int64_t) : 0;
-    size_t o_part = align256(o_list + list_bytes);
-    size_t total = align256(o_part + (size_t)part_total * sizeof(double));
+    const int xc = choose_xc(sc, mix, 16);
+    if (xc == 0) return sf_set_error(SF_ERR_LIMIT, "intertwiner dimensions too large for the shell kernel");
+    // scratch: items | jobs | counter | bitmap | list | partials
+    const int64_t nshell0 = t->vs[0].nshell;
+    const size_t o_jobs = align256(sc.items.size() * sizeof(WorkItem));
+    const size_t o_counter = align256(o_jobs + sc.jobs.size() * sizeof(ReduceJob));
+    const size_t o_bitmap = align256(o_counter + sizeof(int));
+    const size_t bm_bytes = shell_list ? (size_t)((nshell0 + 31) / 32) * sizeof(uint32_t) : 0;
+    const size_t o_list = align256(o_bitmap + bm_bytes);
+    const size_t list_bytes = shell_list ? (size_t)std::max<int64_t>(1, n_list) * sizeof(int64_t) : 0;
+    const size_t o_part = align256(o_list + list_bytes);
+    const size_t total = align256(o_part + (size_t)sc.part_total * sizeof(double));
     SF_TRY(grow_scratch(t, total));
     char* base = (char*)t->d_scratch;
-    WorkItem* d_items = (WorkItem*)(base + o_items);
+    WorkItem* d_items = (WorkItem*)base;
+    ReduceJob* d_jobs = (ReduceJob*)(base + o_jobs);
     int* d_counter = (int*)(base + o_counter);
     double* d_part = (double*)(base + o_part);
-    SF_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, stream));
+    SF_CUDA_TRY(cudaMemcpyAsync(d_items, sc.items.data(), sc.items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, stream));
+    SF_CUDA_TRY(cudaMemcpyAsync(d_jobs, sc.jobs.data(), sc.jobs.size() * sizeof(ReduceJob), cudaMemcpyHostToDevice, stream));
     ShellFilter filt{};
     filt.begin = shell_begin;
     filt.end = shell_end;
@@ -595,29 +602,240 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
         SF_TRY(sf_bitmap_launch(d_list, n_list, nshell0, d_bm, stream));
         filt.bitmap = d_bm;
     }
+    int grid = 0;
+    size_t smem = 0;
+    SF_TRY(sf_shell_prepare(mix, sc.mdi, sc.mdk, sc.mk3u, xc, sc.Dmax, (int)sc.items.size(), t->num_sms, &grid, &smem));
     SF_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, sizeof(int), stream));
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     SF_CUDA_TRY(cudaEventCreate(&ev0));
     SF_CUDA_TRY(cudaEventCreate(&ev1));
     SF_CUDA_TRY(cudaEventRecord(ev0, stream));
-    if (precision == SF_FP64) {
-        SF_TRY(sf_shell_fp64_launch(t->d_vtx, mdi, mdk, mk3u, xc, Dmax, d_items, (int)items.size(), d_counter, d_part,
-                                    filt, t->num_sms, stream));
-    } else {
-        SF_TRY(sf_shell_mixed_launch(t->d_vtx, mdi, mdk, mk3u, xc, Dmax, d_items, (int)items.size(), d_counter, d_part,
-                                     filt, t->num_sms, stream));
-    }
+    SF_TRY(sf_shell_launch_prepared(mix, grid, smem, t->d_vtx, sc.mdi, sc.mdk, sc.mk3u, xc, sc.Dmax, d_items,
+                                    (int)sc.items.size(), d_counter, d_part, filt, stream));
     SF_CUDA_TRY(cudaEventRecord(ev1, stream));
-    for (int i = 0; i < nv; i++) {
-        VertexHost& h = t->vs[i];
-        SF_TRY(sf_reduce_launch(t->d_vtx, i, h.di[0] * h.di[1], d_items, item0[i], nchunk[i], d_part, A_out[i], stream));
-    }
+    SF_TRY(sf_reduce_jobs_launch(t->d_vtx, d_jobs, (int)sc.jobs.size(), d_items, d_part, stream));
     int rc = check_status(t, stream, "sf_vertex_amplitude");
     float ms = -1.0f;
     if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) g_last_kernel_ms = ms;
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
     return rc;
+}
+
+// ----------------------------------------------------------------------------------------------
+// planned shell sums: host decisions once, then stream-only runs (capturable in a CUDA graph)
+// ----------------------------------------------------------------------------------------------
+struct sf_plan {
+    sf_tables* t = nullptr;
+    bool mix = false;
+    int64_t begin = 0, end = 0;
+    std::vector<double*> A;
+    sf_tiling tiling{};
+    ShellSchedule sc;
+    int xc = 0, grid = 0;
+    size_t smem = 0;
+    void* d_buf = nullptr;
+    size_t buf_bytes = 0;
+    WorkItem* d_items = nullptr;
+    ReduceJob* d_jobs = nullptr;
+    int* d_counter = nullptr;
+    double* d_part = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+static void plan_drop_graph(sf_plan* p) {
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->exec = nullptr;
+    p->graph = nullptr;
+}
+
+// (re)build the schedule, kernel configuration and device buffer of a plan for a tiling
+static int plan_build(sf_plan* p, const sf_tiling& req) {
+    plan_drop_graph(p);
+    sf_tiling tl = req;
+    if (tl.items_per_sm <= 0) tl.items_per_sm = SF_DEFAULT_ITEMS_PER_SM;
+    if (tl.items_per_sm > 256) return sf_set_error(SF_ERR_ARG, "items_per_sm above 256");
+    if (tl.x_chunk < 0 || tl.x_chunk > 16) return sf_set_error(SF_ERR_ARG, "x_chunk must be 0 (default) or 1..16");
+    ShellSchedule sc;
+    SF_TRY(schedule_shells(p->t, false, p->begin, p->end, tl.items_per_sm, p->A.data(), &sc));
+    const int xc = choose_xc(sc, p->mix, tl.x_chunk > 0 ? tl.x_chunk : 16);
+    if (xc == 0) return sf_set_error(SF_ERR_LIMIT, "intertwiner dimensions too large for the shell kernel");
+    tl.x_chunk = xc;
+    int grid = 0;
+    size_t smem = 0;
+    SF_TRY(sf_shell_prepare(p->mix, sc.mdi, sc.mdk, sc.mk3u, xc, sc.Dmax, (int)sc.items.size(), p->t->num_sms, &grid,
+                            &smem));
+    const size_t o_jobs = align256(sc.items.size() * sizeof(WorkItem));
+    const size_t o_counter = align256(o_jobs + sc.jobs.size() * sizeof(ReduceJob));
+    const size_t o_part = align256(o_counter + sizeof(int));
+    const size_t total = align256(o_part + (size_t)sc.part_total * sizeof(double));
+    if (total > p->buf_bytes) {
+        if (p->d_buf) cudaFree(p->d_buf);
+        p->d_buf = nullptr;
+        p->buf_bytes = 0;
+        cudaError_t e = cudaMalloc(&p->d_buf, total);
+        if (e != cudaSuccess) return sf_set_error(SF_ERR_OOM, "plan buffer of %zu bytes: %s", total, cudaGetErrorString(e));
+        p->buf_bytes = total;
+    }
+    char* base = (char*)p->d_buf;
+    p->d_items = (WorkItem*)base;
+    p->d_jobs = (ReduceJob*)(base + o_jobs);
+    p->d_counter = (int*)(base + o_counter);
+    p->d_part = (double*)(base + o_part);
+    // synchronous copies: a later run needs nothing from the host
+    SF_CUDA_TRY(cudaMemcpy(p->d_items, sc.items.data(), sc.items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+    SF_CUDA_TRY(cudaMemcpy(p->d_jobs, sc.jobs.data(), sc.jobs.size() * sizeof(ReduceJob), cudaMemcpyHostToDevice));
+    p->sc = std::move(sc);
+    p->xc = xc;
+    p->grid = grid;
+    p->smem = smem;
+    p->tiling = tl;
+    return SF_OK;
+}
+
+static int plan_run(sf_plan* p, cudaStream_t s) {
+    ShellFilter filt{};
+    filt.begin = p->begin;
+    filt.end = p->end;
+    filt.bitmap = nullptr;
+    SF_TRY(sf_shell_launch_prepared(p->mix, p->grid, p->smem, p->t->d_vtx, p->sc.mdi, p->sc.mdk, p->sc.mk3u, p->xc,
+                                    p->sc.Dmax, p->d_items, (int)p->sc.items.size(), p->d_counter, p->d_part, filt, s));
+    return sf_reduce_jobs_launch(p->t->d_vtx, p->d_jobs, (int)p->sc.jobs.size(), p->d_items, p->d_part, s);
+}
+
+extern "C" void sf_plan_free(sf_plan* p) {
+    if (!p) return;
+    plan_drop_graph(p);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    if (p->d_buf) cudaFree(p->d_buf);
+    delete p;
+}
+
+extern "C" int sf_plan_create(sf_tables* t, sf_precision precision, int64_t shell_begin, int64_t shell_end,
+                              const sf_tiling* tiling, double* const* A_out, sf_plan** out) {
+    if (!out) return sf_set_error(SF_ERR_ARG, "null output pointer");
+    *out = nullptr;
+    if (!t || !A_out) return sf_set_error(SF_ERR_ARG, "null argument");
+    if (precision != SF_FP64 && precision != SF_MIXED) return sf_set_error(SF_ERR_ARG, "unknown precision");
+    if (shell_begin < 0) return sf_set_error(SF_ERR_ARG, "negative shell_begin");
+    for (size_t i = 0; i < t->vs.size(); i++) {
+        if (!t->vs[i].boosters_ready) return sf_set_error(SF_ERR_ARG, "boosters of vertex %zu were never computed or uploaded", i);
+        if (!A_out[i]) return sf_set_error(SF_ERR_ARG, "null output for vertex %zu", i);
+    }
+    sf_plan* p = new sf_plan();
+    p->t = t;
+    p->mix = precision == SF_MIXED;
+    p->begin = shell_begin;
+    p->end = shell_end;
+    p->A.assign(A_out, A_out + t->vs.size());
+    sf_tiling req{};
+    if (tiling) req = *tiling;
+    int rc = plan_build(p, req);
+    if (rc != SF_OK) { sf_plan_free(p); return rc; }
+    *out = p;
+    return SF_OK;
+}
+
+extern "C" int sf_plan_run(sf_plan* p, cudaStream_t s) {
+    if (!p) return sf_set_error(SF_ERR_ARG, "null plan");
+    return plan_run(p, s);
+}
+
+extern "C" int sf_plan_graph_launch(sf_plan* p, cudaStream_t s) {
+    if (!p) return sf_set_error(SF_ERR_ARG, "null plan");
+    if (!p->exec) {
+        if (!p->cap) SF_CUDA_TRY(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+        const int64_t before = sf_kernel_launches();
+        SF_CUDA_TRY(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+        int rc = plan_run(p, p->cap);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(p->cap, &g);
+        sf_note_launch(-(int)(sf_kernel_launches() - before));   // capture records, it does not launch
+        if (rc != SF_OK) { if (g) cudaGraphDestroy(g); return rc; }
+        if (e != cudaSuccess) return sf_set_error(SF_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        p->graph = g;
+        e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+        if (e != cudaSuccess) { plan_drop_graph(p); return sf_set_error(SF_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
+    }
+    SF_CUDA_TRY(cudaGraphLaunch(p->exec, s));
+    sf_note_launch(p->sc.jobs.empty() ? 1 : 2);
+    return SF_OK;
+}
+
+extern "C" int sf_plan_sync(sf_plan* p, cudaStream_t s) {
+    if (!p) return sf_set_error(SF_ERR_ARG, "null plan");
+    SF_CUDA_TRY(cudaStreamSynchronize(s));
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
+extern "C" int sf_plan_info(const sf_plan* p, sf_tiling* tiling, int64_t* n_items, int32_t* grid, int64_t* scratch_bytes) {
+    if (!p) return sf_set_error(SF_ERR_ARG, "null plan");
+    if (tiling) *tiling = p->tiling;
+    if (n_items) *n_items = (int64_t)p->sc.items.size();
+    if (grid) *grid = p->grid;
+    if (scratch_bytes) *scratch_bytes = (int64_t)p->buf_bytes;
+    return SF_OK;
+}
+
+extern "C" int sf_plan_autotune(sf_plan* p, int64_t sample_shells, sf_tiling* chosen, cudaStream_t s) {
+    if (!p) return sf_set_error(SF_ERR_ARG, "null plan");
+    if (sample_shells <= 0) return sf_set_error(SF_ERR_ARG, "sample_shells must be positive");
+    // candidates: x chunks and work granularities, each timed on the first sample_shells shells of
+    // the plan's range (every vertex), best of two runs after one warm-up
+    static const int xcs[] = {16, 12, 8, 6, 4};
+    static const int ipss[] = {4, 8, 16, 32};
+    sf_plan probe;
+    probe.t = p->t;
+    probe.mix = p->mix;
+    probe.begin = p->begin;
+    probe.end = std::min<int64_t>(p->end, p->begin + sample_shells);
+    probe.A = p->A;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SF_CUDA_TRY(cudaEventCreate(&e0));
+    SF_CUDA_TRY(cudaEventCreate(&e1));
+    sf_tiling best{};
+    float best_ms = 1e30f;
+    int last_xc = -1;
+    int rc = SF_OK;
+    for (int xc : xcs) {
+        for (int ips : ipss) {
+            sf_tiling tl{};
+            tl.x_chunk = xc;
+            tl.items_per_sm = ips;
+            rc = plan_build(&probe, tl);
+            if (rc == SF_ERR_LIMIT) { rc = SF_OK; continue; }
+            if (rc != SF_OK) break;
+            if (probe.tiling.x_chunk != xc && probe.tiling.x_chunk == last_xc) continue;   // clamped duplicate
+            float tmin = 1e30f;
+            for (int rep = 0; rep < 3 && rc == SF_OK; rep++) {
+                cudaEventRecord(e0, s);
+                rc = plan_run(&probe, s);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = sf_set_error(SF_ERR_CUDA, "autotune run failed");
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tmin = std::min(tmin, ms);
+            }
+            if (rc != SF_OK) break;
+            if (tmin < best_ms) { best_ms = tmin; best = probe.tiling; }
+        }
+        if (rc != SF_OK) break;
+        last_xc = probe.tiling.x_chunk;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (probe.d_buf) cudaFree(probe.d_buf);
+    probe.d_buf = nullptr;
+    plan_drop_graph(&probe);
+    if (rc != SF_OK) return rc;
+    if (best_ms >= 1e30f) return sf_set_error(SF_ERR_LIMIT, "no tiling fits the plan's vertices");
+    SF_TRY(plan_build(p, best));
+    if (chosen) *chosen = p->tiling;
+    return SF_OK;
 }
 
 extern "C" int sf_vertex_adjoint(sf_tables* t, const double* const psi[5], double* a_out, double* const grad_psi[5],

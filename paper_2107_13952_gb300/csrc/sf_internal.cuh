@@ -26,6 +26,8 @@
 int sf_set_error(int code, const char* fmt, ...);
 void sf_note_launch(int n);   // launch counter behind sf_kernel_launches()
 
+#define SF_TRY(x) do { int r_ = (x); if (r_ != SF_OK) return r_; } while (0)
+
 #define SF_CUDA_TRY(call)                                                                      \
     do {                                                                                       \
         cudaError_t e_ = (call);                                                               \
@@ -233,38 +235,55 @@ struct VtxDev {
 enum { F12 = 0, F13, F14, F15, F23, F24, F25, F34, F35, F45 };
 
 // ----------------------------------------------------------------------------------------------
-// launch wrappers implemented in the kernel translation units (return SF_OK or an error code)
+// shell-sum scheduling records
 // ----------------------------------------------------------------------------------------------
-int sf_launch_fact_table(cudaStream_t s);
-int sf_launch_6j_table(const int32_t* tj6args_unused, double* out, const SlotDesc* d_slots, int nslots,
-                       int64_t n_entries, int table_id, const VtxDev* d_v, int* d_status, cudaStream_t s);
-
-// rapidity rule and d-tables
-int sf_launch_gl_library(double* d_gl, int64_t* d_gl_off, cudaStream_t s);
-int sf_launch_rule_nodes(const sf_quad_rule* q, double* d_x, double* d_w, double* d_r, double* d_W,
-                         double* d_glrule, cudaStream_t s);
-int sf_launch_dtable(const VtxDev* h_v, int face, double2* d_out, const double* d_r, int nnodes,
-                     const double* d_gl, cudaStream_t s);
-int sf_launch_boosters(const VtxDev* h_v, const VtxDev* d_v, int edge, double* d_B, const double* d_W,
-                       int nnodes, int* d_status, cudaStream_t s);
-
-// shell sums
-struct WorkItem {
+struct WorkItem {              // one output tile (i1, i2) of one vertex over a range of groups
     int32_t vtx, i1, i2, g0, g1;
     int32_t pad;
-    int64_t part_off;
+    int64_t part_off;          // its partial tile [i3][i4][i5] in the partials buffer
 };
 struct ShellFilter {
     int64_t begin, end;          // linear shell range
     const uint32_t* bitmap;      // optional membership bitmap (single vertex), overrides the range
 };
-int sf_launch_shell_fp64(const VtxDev* d_v, int max_di, int max_dk, int max_nx, const WorkItem* d_items,
-                         int n_items, int* d_counter, double* d_part, ShellFilter filt, int* d_status,
-                         cudaStream_t s);
-int sf_launch_shell_mixed(const VtxDev* d_v, int max_di, int max_dk, int max_nx, const WorkItem* d_items,
-                          int n_items, int* d_counter, double* d_part, ShellFilter filt, int* d_status,
-                          cudaStream_t s);
-int sf_launch_reduce(const VtxDev* d_v, int vtx, const VtxDev* h_v, const WorkItem* d_items, int item_begin,
-                     int item_end, const double* d_part, double* A, cudaStream_t s);
-int sf_launch_adjoint(const VtxDev* d_v, const VtxDev* h_v, const double2* const* psi, double2* d_scr_a,
-                      double2* d_scr_gphi, int64_t nshell, cudaStream_t s);
+struct ReduceJob {             // one output tile: the nchunk consecutive items from item0
+    int32_t vtx, tile, item0, nchunk;
+    double* A;                 // the tile's first output entry
+};
+
+// ----------------------------------------------------------------------------------------------
+// launchers implemented in the kernel translation units (return SF_OK or an error code)
+// ----------------------------------------------------------------------------------------------
+int sf_fact_table_build(dd* F, cudaStream_t s);
+int sf_sixj_table_build(int table_id, const VtxDev* d_v, const SlotDesc* d_slots, int nslots, int64_t n,
+                        double* d_out, const dd* F, int* d_status, int num_sms, cudaStream_t s);
+int sf_to_float(const double* d_in, float* d_out, int64_t n, int num_sms, cudaStream_t s);
+int sf_rule_build(const sf_quad_rule* q, double* d_gl, double* d_x, double* d_w, double* d_r, double* d_W,
+                  cudaStream_t s);
+int sf_dtable_build(int tk, double gamma, int nl, int nnodes, const double* d_r, const double* d_gl, double2* d_out,
+                    cudaStream_t s);
+size_t sf_booster_smem(int tj1, int tj2, int tj3, int tj4, int nk);
+int sf_booster_build(const VtxDev* d_v, int edge, int ntrip, size_t smem, const double* d_W, int nnodes,
+                     const dd* F, double* d_Aj, double* d_Cj, double* d_B, int* d_status, cudaStream_t s);
+size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, bool mix = false);
+// sets the kernel's shared-memory attribute and returns its grid (resident CTAs, at most n_items);
+// host-only, so a capturable launch sequence calls it beforehand
+int sf_shell_prepare(bool mix, int mdi, int mdk, int mk3u, int xc, int Dmax, int n_items, int num_sms, int* grid,
+                     size_t* smem);
+// zeroes the work counter and launches the persistent shell kernel (stream work only)
+int sf_shell_launch_prepared(bool mix, int grid, size_t smem, const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc,
+                             int Dmax, const WorkItem* d_items, int n_items, int* d_counter, double* d_part,
+                             ShellFilter filt, cudaStream_t s);
+int sf_shell_fp64_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax, const WorkItem* d_items,
+                         int n_items, int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s);
+int sf_shell_mixed_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax, const WorkItem* d_items,
+                          int n_items, int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s);
+int sf_reduce_launch(const VtxDev* d_v, int vtx, int ntiles, const WorkItem* d_items, int item0, int nchunk,
+                     const double* d_part, double* A, cudaStream_t s);
+int sf_reduce_jobs_launch(const VtxDev* d_v, const ReduceJob* d_jobs, int njobs, const WorkItem* d_items,
+                          const double* d_part, cudaStream_t s);
+int sf_bitmap_launch(const int64_t* d_list, int64_t n, int64_t nshell, uint32_t* d_bm, cudaStream_t s);
+int sf_adjoint_launch(const VtxDev* d_v, const VtxDev& h, const double* const psi[5], double* a_out,
+                      double* const grad_psi[5], double* const grad_B[4], void* scratch, size_t scratch_bytes,
+                      int num_sms, cudaStream_t s);
+size_t sf_adjoint_scratch_bytes(const VtxDev& h);

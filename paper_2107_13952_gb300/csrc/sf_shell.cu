@@ -104,7 +104,7 @@ __device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int 
     return s;
 }
 
-size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, bool mix = false) {
+size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, bool mix) {
     size_t n = (size_t)mdi * mdk * mdi + (size_t)mdk * mdk * mdi + (size_t)mk3u * xc * mdi + (size_t)mdk * xc * mdi +
                (size_t)mdk * mdk * xc + 2ull * D * mdk * xc + (size_t)xc * mdk * mk3u + (size_t)D * mdk * mdi +
                2ull * mdi * mdk;
@@ -414,32 +414,55 @@ __global__ void __launch_bounds__(SF_SHELL_THREADS, 1) k_shell(const VtxDev* __r
     }
 }
 
-template <bool MIX>
-static int shell_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax, const WorkItem* d_items,
-                        int n_items, int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s) {
-    size_t smem = sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax, MIX) * sizeof(double);
-    if (smem > 200 * 1024) return sf_set_error(SF_ERR_LIMIT, "shell kernel needs %zu bytes of shared memory", smem);
-    SF_CUDA_TRY(cudaFuncSetAttribute(k_shell<MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+int sf_shell_prepare(bool mix, int mdi, int mdk, int mk3u, int xc, int Dmax, int n_items, int num_sms, int* grid,
+                     size_t* smem) {
+    const size_t bytes = sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax, mix) * sizeof(double);
+    if (bytes > 200 * 1024) return sf_set_error(SF_ERR_LIMIT, "shell kernel needs %zu bytes of shared memory", bytes);
+    const void* fn = mix ? (const void*)k_shell<true> : (const void*)k_shell<false>;
+    SF_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     int per_sm = 0;
-    SF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shell<MIX>, SF_SHELL_THREADS, smem));
+    SF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SF_SHELL_THREADS, bytes));
     if (per_sm < 1) per_sm = 1;
-    int grid = num_sms * per_sm;
-    if (grid > n_items) grid = n_items;
+    int g = num_sms * per_sm;
+    if (g > n_items) g = n_items;
+    *grid = g < 1 ? 1 : g;
+    *smem = bytes;
+    return SF_OK;
+}
+
+int sf_shell_launch_prepared(bool mix, int grid, size_t smem, const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc,
+                             int Dmax, const WorkItem* d_items, int n_items, int* d_counter, double* d_part,
+                             ShellFilter filt, cudaStream_t s) {
     SF_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(int), s));
-    k_shell<MIX><<<grid, SF_SHELL_THREADS, smem, s>>>(d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter, d_part, filt);
+    if (mix)
+        k_shell<true><<<grid, SF_SHELL_THREADS, smem, s>>>(d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter,
+                                                           d_part, filt);
+    else
+        k_shell<false><<<grid, SF_SHELL_THREADS, smem, s>>>(d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter,
+                                                            d_part, filt);
     sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;
 }
 
+static int shell_launch(bool mix, const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax,
+                        const WorkItem* d_items, int n_items, int* d_counter, double* d_part, ShellFilter filt,
+                        int num_sms, cudaStream_t s) {
+    int grid = 0;
+    size_t smem = 0;
+    SF_TRY(sf_shell_prepare(mix, mdi, mdk, mk3u, xc, Dmax, n_items, num_sms, &grid, &smem));
+    return sf_shell_launch_prepared(mix, grid, smem, d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter, d_part,
+                                    filt, s);
+}
+
 int sf_shell_fp64_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax, const WorkItem* d_items,
                          int n_items, int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s) {
-    return shell_launch<false>(d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter, d_part, filt, num_sms, s);
+    return shell_launch(false, d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter, d_part, filt, num_sms, s);
 }
 
 int sf_shell_mixed_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax, const WorkItem* d_items,
                           int n_items, int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s) {
-    return shell_launch<true>(d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter, d_part, filt, num_sms, s);
+    return shell_launch(true, d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter, d_part, filt, num_sms, s);
 }
 
 // A[i1][i2][i3][i4][i5] = (-1)^(n_i1) prod_e sqrt(2 i_e + 1) * sum_{chunks} part[tile, chunk][i3][i4][i5]
@@ -465,6 +488,34 @@ __global__ void k_reduce(const VtxDev* __restrict__ V, int vtx, const WorkItem* 
 int sf_reduce_launch(const VtxDev* d_v, int vtx, int ntiles, const WorkItem* d_items, int item0, int nchunk,
                      const double* d_part, double* A, cudaStream_t s) {
     k_reduce<<<ntiles, 256, 0, s>>>(d_v, vtx, d_items, item0, nchunk, d_part, A);
+    sf_note_launch(1);
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
+// the same reduction for many vertices in one launch: one CTA per output tile (ReduceJob)
+__global__ void k_reduce_jobs(const VtxDev* __restrict__ V, const ReduceJob* __restrict__ jobs,
+                              const WorkItem* __restrict__ items, const double* __restrict__ part) {
+    const ReduceJob jb = jobs[blockIdx.x];
+    const VtxDev& v = V[jb.vtx];
+    const int ci1 = jb.tile / v.di[1], ci2 = jb.tile % v.di[1];
+    const int n3 = v.di[2] * v.di[3] * v.di[4];
+    const double s12 = sqrt((double)(v.ilo[0] + 2 * ci1 + 1)) * sqrt((double)(v.ilo[1] + 2 * ci2 + 1)) *
+                       ((ci1 & 1) ? -1.0 : 1.0);
+    for (int q = threadIdx.x; q < n3; q += blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < jb.nchunk; c++) acc += part[items[jb.item0 + c].part_off + q];
+        const int c5 = q % v.di[4], c4 = (q / v.di[4]) % v.di[3], c3 = q / (v.di[4] * v.di[3]);
+        const double s = s12 * sqrt((double)(v.ilo[2] + 2 * c3 + 1)) * sqrt((double)(v.ilo[3] + 2 * c4 + 1)) *
+                         sqrt((double)(v.ilo[4] + 2 * c5 + 1));
+        jb.A[q] = s * acc;
+    }
+}
+
+int sf_reduce_jobs_launch(const VtxDev* d_v, const ReduceJob* d_jobs, int njobs, const WorkItem* d_items,
+                          const double* d_part, cudaStream_t s) {
+    if (njobs <= 0) return SF_OK;
+    k_reduce_jobs<<<njobs, 256, 0, s>>>(d_v, d_jobs, d_items, d_part);
     sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;

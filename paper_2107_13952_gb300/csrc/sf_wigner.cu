@@ -63,8 +63,6 @@ __global__ void __launch_bounds__(256) k_sixj_table(int table_id, const VtxDev* 
     }
 }
 
-int sf_launch_fact_table(cudaStream_t s) { (void)s; return SF_OK; }
-
 int sf_fact_table_build(dd* F, cudaStream_t s) {
     k_fact_table<<<1, 1, 0, s>>>(F);
     sf_note_launch(1);
