@@ -75,8 +75,9 @@ typedef struct {
 
 typedef enum {
     SF_FP64  = 0,   /* every step in FP64                                                         */
-    SF_MIXED = 1    /* {6j}/{15j} blocks in FP64; booster contractions on tensor cores with
-                       FP32-class accuracy and FP32 accumulation per shell; FP64 across shells */
+    SF_MIXED = 1    /* booster contractions over k2, k3, k4 with FP32 inputs and FP32 accumulation
+                       within one (l24, l34) set of shells; the {6j} contractions, the k5 contraction
+                       and every sum across shells in FP64                                        */
 } sf_precision;
 
 typedef struct sf_tables sf_tables;
@@ -156,13 +157,21 @@ int sf_vertex_amplitude_noalloc(sf_tables* t, int64_t shell_begin, int64_t shell
  * tiling) and owns its device scratch, so that running it issues only asynchronous device work:
  * one memset, the persistent shell kernel and one reduction kernel over every vertex's tiles.
  *
- * sf_tiling: x_chunk = auxiliary spins x per staged chunk of the {6j} contractions (1..16; the
- *   shared-memory footprint grows with it); items_per_sm = target number of work items per SM
- *   (granularity of the cost-balanced split of tiles x groups). 0 selects the default (largest
- *   x_chunk that fits, 8 items per SM). */
+ * sf_tiling (0 in a field selects the library's choice):
+ *   x_chunk = auxiliary spins x per staged chunk of the {6j} contractions (1..16; the shared-memory
+ *     footprint grows with it; default the largest that fits);
+ *   items_per_sm = target number of work items per SM (granularity of the cost-balanced split of
+ *     tiles x groups; default 8);
+ *   threads = CTA size, 512 (one CTA per SM) or 256 (two CTAs per SM whose phases interleave);
+ *   i3_split = 1 or 2 pieces of i3 per output tile (2 halves the per-CTA buffers and register
+ *     tile so that two CTAs fit per SM, and stages the i3-independent operands twice; 256
+ *     threads only). Default: 256 threads on whole tiles when they fit with an x chunk of at
+ *     least 4, else (mixed path) 256 threads on half tiles, else 512 threads. */
 typedef struct sf_tiling {
     int32_t x_chunk;
     int32_t items_per_sm;
+    int32_t threads;
+    int32_t i3_split;
 } sf_tiling;
 typedef struct sf_plan sf_plan;
 
@@ -176,10 +185,11 @@ typedef struct sf_plan sf_plan;
 int sf_plan_create(sf_tables* t, sf_precision precision, int64_t shell_begin, int64_t shell_end,
                    const sf_tiling* tiling, double* const* A_out, sf_plan** out);
 
-/* Time candidate tilings (x_chunk 16, 12, 8, 6, 4 x items_per_sm 4, 8, 16, 32) on the first
- * sample_shells shells of the plan's range of every vertex (best of two runs after a warm-up,
- * CUDA events on stream) and rebuild the plan with the fastest; *chosen (optional) receives it.
- * Overwrites the plan's outputs; synchronises the stream; drops a captured graph. */
+/* Time candidate tilings ((threads, i3_split) in (512, 1), (256, 1), (256, 2) x x_chunk 16, 8, 4
+ * (clamped to what fits) x items_per_sm 4, 8, 16) on the first sample_shells shells of the plan's
+ * range of every vertex (best of two runs after a warm-up, CUDA events on stream) and rebuild the
+ * plan with the fastest; *chosen (optional) receives it. Overwrites the plan's outputs;
+ * synchronises the stream; drops a captured graph. */
 int sf_plan_autotune(sf_plan* plan, int64_t sample_shells, sf_tiling* chosen, cudaStream_t stream);
 
 /* Run the plan on stream: stream work only (no allocation, no host copy, no synchronisation), so

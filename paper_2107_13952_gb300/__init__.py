@@ -46,7 +46,8 @@ class sf_quad_rule(ctypes.Structure):
 
 
 class sf_tiling(ctypes.Structure):
-    _fields_ = [("x_chunk", ctypes.c_int32), ("items_per_sm", ctypes.c_int32)]
+    _fields_ = [("x_chunk", ctypes.c_int32), ("items_per_sm", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("i3_split", ctypes.c_int32)]
 
 
 def vertex(two_j, gamma, dl):
@@ -238,7 +239,7 @@ class Plan:
             _, dim = intertwiner_ranges(list(v.two_j), v.gamma, v.dl)
             self.outputs.append(torch.empty(dim, dtype=torch.float64, device="cuda"))
         ptrs = (ctypes.c_void_p * len(self.outputs))(*[o.data_ptr() for o in self.outputs])
-        tl = sf_tiling(*(tiling or (0, 0)))
+        tl = sf_tiling(*(tuple(tiling or ()) + (0, 0, 0, 0))[:4])
         out = ctypes.c_void_p()
         _check(lib.sf_plan_create(tables.ptr, int(precision), int(shell_begin), int(shell_end), ctypes.byref(tl), ptrs,
                                   ctypes.byref(out)))
@@ -247,7 +248,7 @@ class Plan:
     def autotune(self, sample_shells, stream=None):
         tl = sf_tiling()
         _check(load().sf_plan_autotune(self.ptr, int(sample_shells), ctypes.byref(tl), _stream(stream)))
-        return (tl.x_chunk, tl.items_per_sm)
+        return (tl.x_chunk, tl.items_per_sm, tl.threads, tl.i3_split)
 
     def run(self, stream=None):
         _check(load().sf_plan_run(self.ptr, _stream(stream)))
@@ -263,8 +264,8 @@ class Plan:
     def info(self):
         tl, n, g, b = sf_tiling(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
         _check(load().sf_plan_info(self.ptr, ctypes.byref(tl), ctypes.byref(n), ctypes.byref(g), ctypes.byref(b)))
-        return {"x_chunk": tl.x_chunk, "items_per_sm": tl.items_per_sm, "n_items": n.value, "grid": g.value,
-                "scratch_bytes": b.value}
+        return {"x_chunk": tl.x_chunk, "items_per_sm": tl.items_per_sm, "threads": tl.threads,
+                "i3_split": tl.i3_split, "n_items": n.value, "grid": g.value, "scratch_bytes": b.value}
 
     def __del__(self):
         if getattr(self, "ptr", None) and _LIB is not None:

@@ -463,23 +463,104 @@ static int grow_scratch(sf_tables* t, size_t bytes) {
 
 static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Work decomposition of one shell sum: per vertex, output tiles (i1, i2) x chunks of the
-// (l25, l35, l45) groups in the requested range. Chunk counts scale with the estimated cost of a
-// tile so that items are of similar size (about items_per_sm of them per SM overall), and the
+// Launch configuration of the shell kernel: threads per CTA (512: one CTA per SM; 256: two CTAs
+// per SM, so that one CTA's staging and FP32 phases overlap the other's FP64 phases), the number
+// of i3 pieces per output tile (2 halves the i3-indexed buffers and the register tile, at the cost
+// of staging the i3-independent operands twice), the x chunk and the work granularity.
+struct ShellConfig {
+    int nt = 512, split = 1, xc = 0, items_per_sm = 8;
+};
+
+struct ShellDims {
+    int mdi = 1, mdk = 1, mk3u = 1, Dmax = 1, mdi3 = 1;
+};
+
+static ShellDims shell_dims(const sf_tables* t) {
+    ShellDims d;
+    for (const VertexHost& h : t->vs) {
+        for (int e = 2; e < 5; e++) d.mdi = std::max(d.mdi, (int)h.di[e]);
+        for (int e = 0; e < 4; e++) d.mdk = std::max(d.mdk, (int)h.dkmax[e]);
+        d.mk3u = std::max(d.mk3u, h.mk3u);
+        d.Dmax = std::max(d.Dmax, h.D);
+        d.mdi3 = std::max(d.mdi3, (int)h.di[2]);
+    }
+    return d;
+}
+
+static size_t shell_smem_limit(int nt) { return nt == 256 ? 110 * 1024 : 200 * 1024; }
+
+// the register-resident output tile (blocks of 2 i5 x 4 i3 per i4) fits SF_TRT blocks per thread
+static bool shell_tile_fits(const sf_tables* t, int nt, int split) {
+    for (const VertexHost& h : t->vs) {
+        const int ni3 = (h.di[2] + split - 1) / split;
+        if ((int64_t)h.di[3] * ((h.di[4] + 1) / 2) * ((ni3 + 3) / 4) > 2 * (int64_t)nt) return false;
+    }
+    return true;
+}
+
+// largest x chunk <= cap whose shared memory fits the CTA size's limit; 0 if none
+static int shell_max_xc(const ShellDims& d, bool mix, int nt, int split, int cap) {
+    const int mni3 = (d.mdi3 + split - 1) / split;
+    for (int xc = std::max(1, std::min(cap, 16)); xc >= 1; xc--)
+        if (sf_shell_smem_doubles(d.mdi, d.mdk, d.mk3u, xc, d.Dmax, mni3, mix) * sizeof(double) <= shell_smem_limit(nt))
+            return xc;
+    return 0;
+}
+
+// Resolve a requested tiling (0 fields = choose) into a configuration. Default: two CTAs per SM
+// on whole tiles when the tile fits with an x chunk of at least 4, else one CTA of 512 threads.
+// Half tiles (measured slower at spin 8, where only they give two CTAs per SM: the duplicated
+// staging costs more than the overlap gains) are used only when requested.
+static int shell_config(const sf_tables* t, bool mix, const sf_tiling& req, ShellConfig* out) {
+    if (req.x_chunk < 0 || req.x_chunk > 16) return sf_set_error(SF_ERR_ARG, "x_chunk must be 0 (default) or 1..16");
+    if (req.items_per_sm < 0 || req.items_per_sm > 256) return sf_set_error(SF_ERR_ARG, "items_per_sm must be 0..256");
+    if (req.threads != 0 && req.threads != 256 && req.threads != 512)
+        return sf_set_error(SF_ERR_ARG, "threads must be 0 (default), 256 or 512");
+    if (req.i3_split < 0 || req.i3_split > 2) return sf_set_error(SF_ERR_ARG, "i3_split must be 0 (default), 1 or 2");
+    const ShellDims d = shell_dims(t);
+    const int cap = req.x_chunk > 0 ? req.x_chunk : 16;
+    const int cands[3][2] = {{256, 1}, {256, 2}, {512, 1}};
+    const bool explicit_cfg = req.threads != 0 || req.i3_split != 0;
+    for (const auto& c : cands) {
+        const int nt = c[0], split = c[1];
+        if (req.threads != 0 && req.threads != nt) continue;
+        if (req.i3_split != 0 && req.i3_split != split) continue;
+        if (req.i3_split == 0 && split == 2) continue;   // half tiles only on request (duplicated staging)
+        if (!shell_tile_fits(t, nt, split)) continue;
+        const int xc = shell_max_xc(d, mix, nt, split, cap);
+        if (xc == 0) continue;
+        if (!explicit_cfg && nt == 256 && xc < std::min(4, cap)) continue;
+        out->nt = nt;
+        out->split = split;
+        out->xc = xc;
+        out->items_per_sm = req.items_per_sm > 0 ? req.items_per_sm : 8;
+        return SF_OK;
+    }
+    if (req.threads == 512 && req.i3_split == 2) return sf_set_error(SF_ERR_ARG, "i3_split 2 needs threads 256");
+    return sf_set_error(SF_ERR_LIMIT, "intertwiner dimensions too large for the shell kernel with this tiling");
+}
+
+// Work decomposition of one shell sum: per vertex, output tiles (i1, i2) x i3 pieces x chunks of
+// the (l25, l35, l45) groups in the requested range. Chunk counts scale with the estimated cost of
+// an item so that items are of similar size (about items_per_sm of them per SM overall), and the
 // costliest vertices are queued first (the kernel takes items in order from an atomic counter).
-// One ReduceJob per output tile names its chunks, which are consecutive items.
+// Within a vertex the items are chunk-major (all tiles of chunk 0, then chunk 1, ...), so the
+// CTAs running at one time read the {6j} slots of the same groups and share them in L2. One
+// ReduceJob per (tile, i3 piece) names its chunks (items spaced by tiles x pieces).
 struct ShellSchedule {
     std::vector<WorkItem> items;
     std::vector<ReduceJob> jobs;
     int64_t part_total = 0;
-    int mdi = 1, mdk = 1, mk3u = 1, Dmax = 1;
+    ShellDims dims;
+    int mni3 = 1;
 };
 
 static int schedule_shells(const sf_tables* t, bool whole_range, int64_t shell_begin, int64_t shell_end,
-                           int items_per_sm, double* const* A_out, ShellSchedule* sc) {
+                           const ShellConfig& cfg, double* const* A_out, ShellSchedule* sc) {
     const int nv = (int)t->vs.size();
     std::vector<int64_t> g_lo(nv), g_n(nv);
-    std::vector<double> tile_cost(nv);
+    std::vector<double> item_cost_v(nv);
+    std::vector<int> ns(nv);
     double total_cost = 0.0;
     for (int i = 0; i < nv; i++) {
         const VertexHost& h = t->vs[i];
@@ -493,69 +574,67 @@ static int schedule_shells(const sf_tables* t, bool whole_range, int64_t shell_b
         }
         g_lo[i] = lo;
         g_n[i] = std::max<int64_t>(hi - lo, 0);
+        ns[i] = std::min(cfg.split, (int)h.di[2]);
         double dmax = std::max(std::max(h.di[2], h.di[3]), h.di[4]);
-        tile_cost[i] = (double)g_n[i] * per_group * dmax * dmax * dmax * dmax;
-        total_cost += tile_cost[i] * h.di[0] * h.di[1];
+        item_cost_v[i] = (double)g_n[i] * per_group * dmax * dmax * dmax * dmax / ns[i];
+        total_cost += item_cost_v[i] * h.di[0] * h.di[1] * ns[i];
     }
-    const double item_cost = std::max(1.0, total_cost / ((double)t->num_sms * std::max(1, items_per_sm)));
+    const double item_cost = std::max(1.0, total_cost / ((double)t->num_sms * std::max(1, cfg.items_per_sm)));
     std::vector<int> order(nv);
     for (int i = 0; i < nv; i++) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return tile_cost[a] > tile_cost[b]; });
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return item_cost_v[a] > item_cost_v[b]; });
     std::vector<int> item0(nv), nchunk(nv);
     for (int i : order) {
         const VertexHost& h = t->vs[i];
         const int64_t ntile = (int64_t)h.di[0] * h.di[1];
         const int64_t ng = g_n[i];
         int C = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(ng, 1),
-                                                            (int64_t)std::ceil(tile_cost[i] / item_cost)));
+                                                            (int64_t)std::ceil(item_cost_v[i] / item_cost)));
         item0[i] = (int)sc->items.size();
         nchunk[i] = C;
-        const int64_t per = (int64_t)h.di[2] * h.di[3] * h.di[4];
-        for (int64_t tile = 0; tile < ntile; tile++) {
-            for (int c = 0; c < C; c++) {
-                WorkItem w{};
-                w.vtx = i;
-                w.i1 = (int)(tile / h.di[1]);
-                w.i2 = (int)(tile % h.di[1]);
-                w.g0 = (int)(g_lo[i] + ng * c / C);
-                w.g1 = (int)(g_lo[i] + ng * (c + 1) / C);
-                w.part_off = sc->part_total;
-                sc->part_total += per;
-                sc->items.push_back(w);
+        for (int c = 0; c < C; c++) {
+            for (int64_t tile = 0; tile < ntile; tile++) {
+                for (int hp = 0; hp < ns[i]; hp++) {
+                    WorkItem w{};
+                    w.vtx = i;
+                    w.i1 = (int)(tile / h.di[1]);
+                    w.i2 = (int)(tile % h.di[1]);
+                    w.g0 = (int)(g_lo[i] + ng * c / C);
+                    w.g1 = (int)(g_lo[i] + ng * (c + 1) / C);
+                    w.i3b = (int16_t)(h.di[2] * hp / ns[i]);
+                    w.ni3 = (int16_t)(h.di[2] * (hp + 1) / ns[i] - w.i3b);
+                    w.part_off = sc->part_total;
+                    sc->part_total += (int64_t)w.ni3 * h.di[3] * h.di[4];
+                    sc->items.push_back(w);
+                }
             }
         }
-        if ((int64_t)h.di[3] * ((h.di[4] + 1) / 2) * ((h.di[2] + 3) / 4) > 4 * 256)
-            return sf_set_error(SF_ERR_LIMIT, "vertex %d: intertwiner dimensions too large for the register-resident tile", i);
-        for (int e = 2; e < 5; e++) sc->mdi = std::max(sc->mdi, (int)h.di[e]);
-        for (int e = 0; e < 4; e++) sc->mdk = std::max(sc->mdk, (int)h.dkmax[e]);
-        sc->mk3u = std::max(sc->mk3u, h.mk3u);
-        sc->Dmax = std::max(sc->Dmax, h.D);
+        if (sc->items.size() > (size_t)0x7FFFFFFF) return sf_set_error(SF_ERR_LIMIT, "too many work items");
     }
-    if (sc->items.size() > (size_t)0x7FFFFFFF) return sf_set_error(SF_ERR_LIMIT, "too many work items");
+    if (!shell_tile_fits(t, cfg.nt, cfg.split))
+        return sf_set_error(SF_ERR_LIMIT, "intertwiner dimensions too large for the register-resident tile");
+    sc->dims = shell_dims(t);
+    sc->mni3 = (sc->dims.mdi3 + cfg.split - 1) / cfg.split;
     for (int i = 0; i < nv; i++) {
         const VertexHost& h = t->vs[i];
         const int64_t n3 = (int64_t)h.di[2] * h.di[3] * h.di[4];
         for (int tile = 0; tile < h.di[0] * h.di[1]; tile++) {
-            ReduceJob j{};
-            j.vtx = i;
-            j.tile = tile;
-            j.item0 = item0[i] + tile * nchunk[i];
-            j.nchunk = nchunk[i];
-            j.A = A_out[i] + tile * n3;
-            sc->jobs.push_back(j);
+            for (int hp = 0; hp < ns[i]; hp++) {
+                ReduceJob j{};
+                j.vtx = i;
+                j.tile = tile;
+                j.item0 = item0[i] + tile * ns[i] + hp;
+                j.nchunk = nchunk[i];
+                j.stride = h.di[0] * h.di[1] * ns[i];
+                j.i3b = h.di[2] * hp / ns[i];
+                j.ni3 = h.di[2] * (hp + 1) / ns[i] - j.i3b;
+                j.A = A_out[i] + tile * n3 + (int64_t)j.i3b * h.di[3] * h.di[4];
+                sc->jobs.push_back(j);
+            }
         }
     }
     return SF_OK;
 }
-
-// largest x chunk (<= max_xc) whose shared-memory footprint stays under ~200 KB; 0 if none
-static int choose_xc(const ShellSchedule& sc, bool mix, int max_xc) {
-    for (int xc = std::max(1, std::min(max_xc, 16)); xc >= 1; xc--)
-        if (sf_shell_smem_doubles(sc.mdi, sc.mdk, sc.mk3u, xc, sc.Dmax, mix) * sizeof(double) <= 200 * 1024) return xc;
-    return 0;
-}
-
-#define SF_DEFAULT_ITEMS_PER_SM 8
 
 extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t shell_begin, int64_t shell_end,
                                    const int64_t* shell_list, int64_t n_list, double* const* A_out, cudaStream_t stream) {
@@ -568,11 +647,12 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
         if (!t->vs[i].boosters_ready) return sf_set_error(SF_ERR_ARG, "boosters of vertex %zu were never computed or uploaded", i);
         if (!A_out[i]) return sf_set_error(SF_ERR_ARG, "null output for vertex %zu", i);
     }
-    ShellSchedule sc;
-    SF_TRY(schedule_shells(t, shell_list != nullptr, shell_begin, shell_end, SF_DEFAULT_ITEMS_PER_SM, A_out, &sc));
     const bool mix = precision == SF_MIXED;
-    const int xc = choose_xc(sc, mix, 16);
-    if (xc == 0) return sf_set_error(SF_ERR_LIMIT, "intertwiner dimensions too large for the shell kernel");
+    ShellConfig cfg;
+    SF_TRY(shell_config(t, mix, sf_tiling{}, &cfg));
+    ShellSchedule sc;
+    SF_TRY(schedule_shells(t, shell_list != nullptr, shell_begin, shell_end, cfg, A_out, &sc));
+    const ShellDims& dm = sc.dims;
     // scratch: items | jobs | counter | bitmap | list | partials
     const int64_t nshell0 = t->vs[0].nshell;
     const size_t o_jobs = align256(sc.items.size() * sizeof(WorkItem));
@@ -604,14 +684,15 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
     }
     int grid = 0;
     size_t smem = 0;
-    SF_TRY(sf_shell_prepare(mix, sc.mdi, sc.mdk, sc.mk3u, xc, sc.Dmax, (int)sc.items.size(), t->num_sms, &grid, &smem));
+    SF_TRY(sf_shell_prepare(mix, cfg.nt, dm.mdi, dm.mdk, dm.mk3u, cfg.xc, dm.Dmax, sc.mni3, (int)sc.items.size(),
+                            t->num_sms, &grid, &smem));
     SF_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, sizeof(int), stream));
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     SF_CUDA_TRY(cudaEventCreate(&ev0));
     SF_CUDA_TRY(cudaEventCreate(&ev1));
     SF_CUDA_TRY(cudaEventRecord(ev0, stream));
-    SF_TRY(sf_shell_launch_prepared(mix, grid, smem, t->d_vtx, sc.mdi, sc.mdk, sc.mk3u, xc, sc.Dmax, d_items,
-                                    (int)sc.items.size(), d_counter, d_part, filt, stream));
+    SF_TRY(sf_shell_launch_prepared(mix, cfg.nt, grid, smem, t->d_vtx, dm.mdi, dm.mdk, dm.mk3u, cfg.xc, dm.Dmax, sc.mni3,
+                                    d_items, (int)sc.items.size(), d_counter, d_part, filt, stream));
     SF_CUDA_TRY(cudaEventRecord(ev1, stream));
     SF_TRY(sf_reduce_jobs_launch(t->d_vtx, d_jobs, (int)sc.jobs.size(), d_items, d_part, stream));
     int rc = check_status(t, stream, "sf_vertex_amplitude");
@@ -631,8 +712,9 @@ struct sf_plan {
     int64_t begin = 0, end = 0;
     std::vector<double*> A;
     sf_tiling tiling{};
+    ShellConfig cfg;
     ShellSchedule sc;
-    int xc = 0, grid = 0;
+    int grid = 0;
     size_t smem = 0;
     void* d_buf = nullptr;
     size_t buf_bytes = 0;
@@ -655,19 +737,15 @@ static void plan_drop_graph(sf_plan* p) {
 // (re)build the schedule, kernel configuration and device buffer of a plan for a tiling
 static int plan_build(sf_plan* p, const sf_tiling& req) {
     plan_drop_graph(p);
-    sf_tiling tl = req;
-    if (tl.items_per_sm <= 0) tl.items_per_sm = SF_DEFAULT_ITEMS_PER_SM;
-    if (tl.items_per_sm > 256) return sf_set_error(SF_ERR_ARG, "items_per_sm above 256");
-    if (tl.x_chunk < 0 || tl.x_chunk > 16) return sf_set_error(SF_ERR_ARG, "x_chunk must be 0 (default) or 1..16");
+    ShellConfig cfg;
+    SF_TRY(shell_config(p->t, p->mix, req, &cfg));
     ShellSchedule sc;
-    SF_TRY(schedule_shells(p->t, false, p->begin, p->end, tl.items_per_sm, p->A.data(), &sc));
-    const int xc = choose_xc(sc, p->mix, tl.x_chunk > 0 ? tl.x_chunk : 16);
-    if (xc == 0) return sf_set_error(SF_ERR_LIMIT, "intertwiner dimensions too large for the shell kernel");
-    tl.x_chunk = xc;
+    SF_TRY(schedule_shells(p->t, false, p->begin, p->end, cfg, p->A.data(), &sc));
     int grid = 0;
     size_t smem = 0;
-    SF_TRY(sf_shell_prepare(p->mix, sc.mdi, sc.mdk, sc.mk3u, xc, sc.Dmax, (int)sc.items.size(), p->t->num_sms, &grid,
-                            &smem));
+    const ShellDims& dm = sc.dims;
+    SF_TRY(sf_shell_prepare(p->mix, cfg.nt, dm.mdi, dm.mdk, dm.mk3u, cfg.xc, dm.Dmax, sc.mni3, (int)sc.items.size(),
+                            p->t->num_sms, &grid, &smem));
     const size_t o_jobs = align256(sc.items.size() * sizeof(WorkItem));
     const size_t o_counter = align256(o_jobs + sc.jobs.size() * sizeof(ReduceJob));
     const size_t o_part = align256(o_counter + sizeof(int));
@@ -689,10 +767,13 @@ static int plan_build(sf_plan* p, const sf_tiling& req) {
     SF_CUDA_TRY(cudaMemcpy(p->d_items, sc.items.data(), sc.items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
     SF_CUDA_TRY(cudaMemcpy(p->d_jobs, sc.jobs.data(), sc.jobs.size() * sizeof(ReduceJob), cudaMemcpyHostToDevice));
     p->sc = std::move(sc);
-    p->xc = xc;
+    p->cfg = cfg;
     p->grid = grid;
     p->smem = smem;
-    p->tiling = tl;
+    p->tiling.x_chunk = cfg.xc;
+    p->tiling.items_per_sm = cfg.items_per_sm;
+    p->tiling.threads = cfg.nt;
+    p->tiling.i3_split = cfg.split;
     return SF_OK;
 }
 
@@ -701,8 +782,10 @@ static int plan_run(sf_plan* p, cudaStream_t s) {
     filt.begin = p->begin;
     filt.end = p->end;
     filt.bitmap = nullptr;
-    SF_TRY(sf_shell_launch_prepared(p->mix, p->grid, p->smem, p->t->d_vtx, p->sc.mdi, p->sc.mdk, p->sc.mk3u, p->xc,
-                                    p->sc.Dmax, p->d_items, (int)p->sc.items.size(), p->d_counter, p->d_part, filt, s));
+    const ShellDims& dm = p->sc.dims;
+    SF_TRY(sf_shell_launch_prepared(p->mix, p->cfg.nt, p->grid, p->smem, p->t->d_vtx, dm.mdi, dm.mdk, dm.mk3u, p->cfg.xc,
+                                    dm.Dmax, p->sc.mni3, p->d_items, (int)p->sc.items.size(), p->d_counter, p->d_part,
+                                    filt, s));
     return sf_reduce_jobs_launch(p->t->d_vtx, p->d_jobs, (int)p->sc.jobs.size(), p->d_items, p->d_part, s);
 }
 
@@ -784,10 +867,11 @@ extern "C" int sf_plan_info(const sf_plan* p, sf_tiling* tiling, int64_t* n_item
 extern "C" int sf_plan_autotune(sf_plan* p, int64_t sample_shells, sf_tiling* chosen, cudaStream_t s) {
     if (!p) return sf_set_error(SF_ERR_ARG, "null plan");
     if (sample_shells <= 0) return sf_set_error(SF_ERR_ARG, "sample_shells must be positive");
-    // candidates: x chunks and work granularities, each timed on the first sample_shells shells of
-    // the plan's range (every vertex), best of two runs after one warm-up
-    static const int xcs[] = {16, 12, 8, 6, 4};
-    static const int ipss[] = {4, 8, 16, 32};
+    // candidates: CTA shapes (threads, i3 pieces) x x chunks x work granularities, each timed on the
+    // first sample_shells shells of the plan's range (every vertex), best of two runs after a warm-up
+    static const int shapes[3][2] = {{512, 1}, {256, 1}, {256, 2}};
+    static const int xcs[] = {16, 8, 4};
+    static const int ipss[] = {4, 8, 16};
     sf_plan probe;
     probe.t = p->t;
     probe.mix = p->mix;
@@ -799,32 +883,41 @@ extern "C" int sf_plan_autotune(sf_plan* p, int64_t sample_shells, sf_tiling* ch
     SF_CUDA_TRY(cudaEventCreate(&e1));
     sf_tiling best{};
     float best_ms = 1e30f;
-    int last_xc = -1;
     int rc = SF_OK;
-    for (int xc : xcs) {
-        for (int ips : ipss) {
-            sf_tiling tl{};
-            tl.x_chunk = xc;
-            tl.items_per_sm = ips;
-            rc = plan_build(&probe, tl);
-            if (rc == SF_ERR_LIMIT) { rc = SF_OK; continue; }
-            if (rc != SF_OK) break;
-            if (probe.tiling.x_chunk != xc && probe.tiling.x_chunk == last_xc) continue;   // clamped duplicate
-            float tmin = 1e30f;
-            for (int rep = 0; rep < 3 && rc == SF_OK; rep++) {
-                cudaEventRecord(e0, s);
-                rc = plan_run(&probe, s);
-                cudaEventRecord(e1, s);
-                if (cudaEventSynchronize(e1) != cudaSuccess) rc = sf_set_error(SF_ERR_CUDA, "autotune run failed");
-                float ms = 0.0f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (rep > 0) tmin = std::min(tmin, ms);
+    std::vector<sf_tiling> tried;
+    for (const auto& sh : shapes) {
+        for (int xc : xcs) {
+            for (int ips : ipss) {
+                sf_tiling tl{};
+                tl.threads = sh[0];
+                tl.i3_split = sh[1];
+                tl.x_chunk = xc;
+                tl.items_per_sm = ips;
+                rc = plan_build(&probe, tl);
+                if (rc == SF_ERR_LIMIT || rc == SF_ERR_ARG) { rc = SF_OK; continue; }   // shape does not fit
+                if (rc != SF_OK) break;
+                bool dup = false;                   // x chunk clamped to one already timed
+                for (const sf_tiling& q : tried)
+                    dup = dup || (q.threads == probe.tiling.threads && q.i3_split == probe.tiling.i3_split &&
+                                  q.x_chunk == probe.tiling.x_chunk && q.items_per_sm == probe.tiling.items_per_sm);
+                if (dup) continue;
+                tried.push_back(probe.tiling);
+                float tmin = 1e30f;
+                for (int rep = 0; rep < 3 && rc == SF_OK; rep++) {
+                    cudaEventRecord(e0, s);
+                    rc = plan_run(&probe, s);
+                    cudaEventRecord(e1, s);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) rc = sf_set_error(SF_ERR_CUDA, "autotune run failed");
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) tmin = std::min(tmin, ms);
+                }
+                if (rc != SF_OK) break;
+                if (tmin < best_ms) { best_ms = tmin; best = probe.tiling; }
             }
             if (rc != SF_OK) break;
-            if (tmin < best_ms) { best_ms = tmin; best = probe.tiling; }
         }
         if (rc != SF_OK) break;
-        last_xc = probe.tiling.x_chunk;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -995,6 +1088,8 @@ extern "C" int sf_vertex_amplitude_noalloc(sf_tables* t, int64_t shell_begin, in
             w.i2 = (int)(tile % h.di[1]);
             w.g0 = (int)lo;
             w.g1 = (int)hi;
+            w.i3b = 0;
+            w.ni3 = (int16_t)h.di[2];
             w.part_off = part_total;
             part_total += per;
             items.push_back(w);
@@ -1007,8 +1102,8 @@ extern "C" int sf_vertex_amplitude_noalloc(sf_tables* t, int64_t shell_begin, in
         Dmax = std::max(Dmax, h.D);
     }
     int xc = 16;
-    while (xc > 1 && sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax) * sizeof(double) > 200 * 1024) xc--;
-    if (sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax) * sizeof(double) > 200 * 1024)
+    while (xc > 1 && sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax, mdi, false) * sizeof(double) > 200 * 1024) xc--;
+    if (sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax, mdi, false) * sizeof(double) > 200 * 1024)
         return sf_set_error(SF_ERR_LIMIT, "intertwiner dimensions too large for the shell kernel");
     // scratch layout: items | counter | partial tiles
     const size_t o_counter = align256(items.size() * sizeof(WorkItem));

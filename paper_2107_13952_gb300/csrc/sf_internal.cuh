@@ -237,18 +237,18 @@ enum { F12 = 0, F13, F14, F15, F23, F24, F25, F34, F35, F45 };
 // ----------------------------------------------------------------------------------------------
 // shell-sum scheduling records
 // ----------------------------------------------------------------------------------------------
-struct WorkItem {              // one output tile (i1, i2) of one vertex over a range of groups
+struct WorkItem {              // output tile (i1, i2), i3 in [i3b, i3b + ni3), of one vertex, over groups [g0, g1)
     int32_t vtx, i1, i2, g0, g1;
-    int32_t pad;
-    int64_t part_off;          // its partial tile [i3][i4][i5] in the partials buffer
+    int16_t i3b, ni3;
+    int64_t part_off;          // its partial tile [i3 - i3b][i4][i5] in the partials buffer
 };
 struct ShellFilter {
     int64_t begin, end;          // linear shell range
     const uint32_t* bitmap;      // optional membership bitmap (single vertex), overrides the range
 };
-struct ReduceJob {             // one output tile: the nchunk consecutive items from item0
-    int32_t vtx, tile, item0, nchunk;
-    double* A;                 // the tile's first output entry
+struct ReduceJob {             // one output tile's i3 range: items item0 + c * stride, c = 0..nchunk-1
+    int32_t vtx, tile, item0, nchunk, stride, i3b, ni3, pad;
+    double* A;                 // the first output entry of the range
 };
 
 // ----------------------------------------------------------------------------------------------
@@ -265,19 +265,19 @@ int sf_dtable_build(int tk, double gamma, int nl, int nnodes, const double* d_r,
 size_t sf_booster_smem(int tj1, int tj2, int tj3, int tj4, int nk);
 int sf_booster_build(const VtxDev* d_v, int edge, int ntrip, size_t smem, const double* d_W, int nnodes,
                      const dd* F, double* d_Aj, double* d_Cj, double* d_B, int* d_status, cudaStream_t s);
-size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, bool mix = false);
+// shared memory (in doubles) of the shell kernel; mni3 = largest i3 extent of a work item
+size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, int mni3, bool mix);
 // sets the kernel's shared-memory attribute and returns its grid (resident CTAs, at most n_items);
-// host-only, so a capturable launch sequence calls it beforehand
-int sf_shell_prepare(bool mix, int mdi, int mdk, int mk3u, int xc, int Dmax, int n_items, int num_sms, int* grid,
-                     size_t* smem);
+// host-only, so a capturable launch sequence calls it beforehand. nt: 256 or 512 threads per CTA.
+int sf_shell_prepare(bool mix, int nt, int mdi, int mdk, int mk3u, int xc, int Dmax, int mni3, int n_items, int num_sms,
+                     int* grid, size_t* smem);
 // zeroes the work counter and launches the persistent shell kernel (stream work only)
-int sf_shell_launch_prepared(bool mix, int grid, size_t smem, const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc,
-                             int Dmax, const WorkItem* d_items, int n_items, int* d_counter, double* d_part,
-                             ShellFilter filt, cudaStream_t s);
+int sf_shell_launch_prepared(bool mix, int nt, int grid, size_t smem, const VtxDev* d_v, int mdi, int mdk, int mk3u,
+                             int xc, int Dmax, int mni3, const WorkItem* d_items, int n_items, int* d_counter,
+                             double* d_part, ShellFilter filt, cudaStream_t s);
+// FP64 shell kernel with 512 threads over whole-tile items (i3b = 0, ni3 = di3), one call
 int sf_shell_fp64_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax, const WorkItem* d_items,
                          int n_items, int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s);
-int sf_shell_mixed_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax, const WorkItem* d_items,
-                          int n_items, int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s);
 int sf_reduce_launch(const VtxDev* d_v, int vtx, int ntiles, const WorkItem* d_items, int item0, int nchunk,
                      const double* d_part, double* A, cudaStream_t s);
 int sf_reduce_jobs_launch(const VtxDev* d_v, const ReduceJob* d_jobs, int njobs, const WorkItem* d_items,

@@ -78,55 +78,69 @@ __device__ __forceinline__ void flat_gemm(int nbatch, int M, int N, int K, const
 }
 
 #define SF_TRT 2   // output-tile register blocks per thread (2 x 4 doubles each)
-#define SF_SHELL_THREADS 512
 
 struct ShellSmem {
-    double *Y, *V, *U, *P, *Q, *R, *SB, *S3s, *B3s, *B4, *B5;
+    double *Y, *V, *B3s, *B4, *B5, *S3s, *Q, *R, *P, *SB, *U;
     float *Vf, *B4f;   // mixed path: FP32 copies for the k4 booster contraction
 };
 
-__device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int xc, int D) {
+// Shared-memory layout of one CTA. mni3: largest i3 extent of a work item. Buffers whose
+// lifetimes within an x chunk do not overlap share space: R (written in B, read in C) with P
+// (written in D, read in F), SB (A -> B) with U (C -> D); the FP32 copy Vf of V (used after the
+// x loop) lies over the chunk buffers.
+__host__ __device__ inline size_t shell_chunk_doubles(int mdk, int mk3u, int xc, int D, int mni3) {
+    const size_t rp = (size_t)D * mdk * xc > (size_t)mdk * xc * mni3 ? (size_t)D * mdk * xc : (size_t)mdk * xc * mni3;
+    const size_t su = (size_t)D * mdk * xc > (size_t)mk3u * xc * mni3 ? (size_t)D * mdk * xc : (size_t)mk3u * xc * mni3;
+    return (size_t)xc * mdk * mk3u + (size_t)mdk * mdk * xc + rp + su;
+}
+
+__device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int xc, int D, int mni3) {
     ShellSmem s;
     double* p = base;
-    s.Y = p;   p += mdi * mdk * mdi;
-    s.V = p;   p += mdk * mdk * mdi;
-    s.U = p;   p += mk3u * xc * mdi;
-    s.P = p;   p += mdk * xc * mdi;
-    s.Q = p;   p += mdk * mdk * xc;
-    s.R = p;   p += D * mdk * xc;
-    s.SB = p;  p += D * mdk * xc;
-    s.S3s = p; p += xc * mdk * mk3u;
-    s.B3s = p; p += D * mdk * mdi;
+    s.Y = p;   p += mdi * mdk * mni3;
+    s.V = p;   p += mdk * mdk * mni3;
+    s.B3s = p; p += D * mdk * mni3;
     s.B4 = p;  p += mdi * mdk;
     s.B5 = p;  p += mdi * mdk;
-    s.Vf = reinterpret_cast<float*>(p);
-    s.B4f = s.Vf + ((mdk * mdk * mdi + 3) & ~3);
+    s.B4f = reinterpret_cast<float*>(p);
+    p += (mdi * mdk + 1) / 2;
+    double* chunk = p;
+    s.S3s = p; p += xc * mdk * mk3u;
+    s.Q = p;   p += mdk * mdk * xc;
+    s.R = p;
+    s.P = p;
+    p += (D * mdk * xc > mdk * xc * mni3) ? D * mdk * xc : mdk * xc * mni3;
+    s.SB = p;
+    s.U = p;
+    s.Vf = reinterpret_cast<float*>(chunk);
     return s;
 }
 
-size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, bool mix) {
-    size_t n = (size_t)mdi * mdk * mdi + (size_t)mdk * mdk * mdi + (size_t)mk3u * xc * mdi + (size_t)mdk * xc * mdi +
-               (size_t)mdk * mdk * xc + 2ull * D * mdk * xc + (size_t)xc * mdk * mk3u + (size_t)D * mdk * mdi +
-               2ull * mdi * mdk;
-    if (mix) n += (((size_t)mdk * mdk * mdi + 3) / 4) * 2 + ((size_t)mdi * mdk + 1) / 2 + 1;
-    return n;
+size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, int mni3, bool mix) {
+    const size_t chunk = shell_chunk_doubles(mdk, mk3u, xc, D, mni3);
+    const size_t vf = mix ? ((size_t)mdk * mdk * mni3 + 1) / 2 : 0;
+    return (size_t)mdi * mdk * mni3 + (size_t)mdk * mdk * mni3 + (size_t)D * mdk * mni3 + 2ull * mdi * mdk +
+           ((size_t)mdi * mdk + 1) / 2 + (chunk > vf ? chunk : vf);
 }
 
 // MIX = false: every phase in FP64 (the FP64 path). MIX = true (the mixed path): the booster
 // contractions over k2 (B2, with S4 S5), over k3 (B3, summed over l23) and over k4 (B4) take FP32
 // inputs and accumulate in FP32 within one (l24, l34) 5-tuple; the {6j} contractions (S3, and the
 // x-sum with S1 S2), every sum across 5-tuples and groups, and the k5 contraction stay FP64.
-template <bool MIX>
-__global__ void __launch_bounds__(SF_SHELL_THREADS, 1) k_shell(const VtxDev* __restrict__ V, int mdi, int mdk, int mk3u, int XC,
-                                                    int Dmax, const WorkItem* __restrict__ items, int n_items,
-                                                    int* counter, double* __restrict__ part, ShellFilter filt) {
+// NT threads per CTA: 512 (one CTA per SM) or 256 (two CTAs per SM, whose phases interleave).
+// A work item covers the i3 sub-range [i3b, i3b + ni3) of its output tile.
+template <bool MIX, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict__ V, int mdi, int mdk, int mk3u, int XC,
+                                                        int Dmax, int mni3, const WorkItem* __restrict__ items,
+                                                        int n_items, int* counter, double* __restrict__ part,
+                                                        ShellFilter filt) {
     extern __shared__ double smem[];
     __shared__ int s_item;
     __shared__ int s_k2lo[SF_MAX_DL + 1], s_nk2[SF_MAX_DL + 1], s_k3lo[SF_MAX_DL + 1], s_nk3[SF_MAX_DL + 1];
     __shared__ double s_sig[SF_MAX_DL + 1];
     __shared__ SlotDesc s_sd4[SF_MAX_DL + 1];
-    const ShellSmem sm = carve(smem, mdi, mdk, mk3u, XC, Dmax);
-    const int tid = threadIdx.x, nth = blockDim.x;
+    const ShellSmem sm = carve(smem, mdi, mdk, mk3u, XC, Dmax, mni3);
+    const int tid = threadIdx.x, nth = NT;
     for (;;) {
         __syncthreads();
         if (tid == 0) s_item = atomicAdd(counter, 1);
@@ -139,7 +153,7 @@ __global__ void __launch_bounds__(SF_SHELL_THREADS, 1) k_shell(const VtxDev* __r
         const int j12 = v.tj[F12], j13 = v.tj[F13], j14 = v.tj[F14], j15 = v.tj[F15];
         const int i1 = v.ilo[0] + 2 * w.i1;
         const int ci2 = w.i2;
-        const int di3 = v.di[2], di4 = v.di[3], di5 = v.di[4];
+        const int di3 = w.ni3, i3b = w.i3b, di3f = v.di[2], di4 = v.di[3], di5 = v.di[4];
         const int dk1 = v.dkmax[1];
         const int jsum = j12 + j13 + j14 + j15 + v.ilo[0];
         // output tile T[i4][i5][i3] in registers: blocks (i4, 2 i5, 4 i3), block b = tid + r * nth
@@ -234,7 +248,7 @@ __global__ void __launch_bounds__(SF_SHELL_THREADS, 1) k_shell(const VtxDev* __r
                 for (int q = tid; q < D * mdk * di3; q += nth) {
                     const int i3 = q % di3, r = q / di3, c3 = r % mdk, d = r / mdk;
                     const int t3 = (d34 * D + d35) * D + d;
-                    const double b3 = (c3 < dk1) ? __ldg(v.B[1] + ((int64_t)t3 * di3 + i3) * dk1 + c3) : 0.0;
+                    const double b3 = (c3 < dk1) ? __ldg(v.B[1] + ((int64_t)t3 * di3f + i3b + i3) * dk1 + c3) : 0.0;
                     if constexpr (MIX) reinterpret_cast<float*>(sm.B3s)[q] = (float)b3;
                     else sm.B3s[q] = b3;
                 }
@@ -414,14 +428,23 @@ __global__ void __launch_bounds__(SF_SHELL_THREADS, 1) k_shell(const VtxDev* __r
     }
 }
 
-int sf_shell_prepare(bool mix, int mdi, int mdk, int mk3u, int xc, int Dmax, int n_items, int num_sms, int* grid,
-                     size_t* smem) {
-    const size_t bytes = sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax, mix) * sizeof(double);
+template <bool MIX, int NT>
+static const void* shell_fn() { return (const void*)k_shell<MIX, NT>; }
+
+static const void* shell_kernel(bool mix, int nt) {
+    if (nt == 256) return mix ? shell_fn<true, 256>() : shell_fn<false, 256>();
+    return mix ? shell_fn<true, 512>() : shell_fn<false, 512>();
+}
+
+int sf_shell_prepare(bool mix, int nt, int mdi, int mdk, int mk3u, int xc, int Dmax, int mni3, int n_items, int num_sms,
+                     int* grid, size_t* smem) {
+    if (nt != 256 && nt != 512) return sf_set_error(SF_ERR_ARG, "shell kernel runs 256 or 512 threads per CTA");
+    const size_t bytes = sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax, mni3, mix) * sizeof(double);
     if (bytes > 200 * 1024) return sf_set_error(SF_ERR_LIMIT, "shell kernel needs %zu bytes of shared memory", bytes);
-    const void* fn = mix ? (const void*)k_shell<true> : (const void*)k_shell<false>;
+    const void* fn = shell_kernel(mix, nt);
     SF_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     int per_sm = 0;
-    SF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, SF_SHELL_THREADS, bytes));
+    SF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, bytes));
     if (per_sm < 1) per_sm = 1;
     int g = num_sms * per_sm;
     if (g > n_items) g = n_items;
@@ -430,39 +453,32 @@ int sf_shell_prepare(bool mix, int mdi, int mdk, int mk3u, int xc, int Dmax, int
     return SF_OK;
 }
 
-int sf_shell_launch_prepared(bool mix, int grid, size_t smem, const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc,
-                             int Dmax, const WorkItem* d_items, int n_items, int* d_counter, double* d_part,
-                             ShellFilter filt, cudaStream_t s) {
+int sf_shell_launch_prepared(bool mix, int nt, int grid, size_t smem, const VtxDev* d_v, int mdi, int mdk, int mk3u,
+                             int xc, int Dmax, int mni3, const WorkItem* d_items, int n_items, int* d_counter,
+                             double* d_part, ShellFilter filt, cudaStream_t s) {
     SF_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(int), s));
-    if (mix)
-        k_shell<true><<<grid, SF_SHELL_THREADS, smem, s>>>(d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter,
-                                                           d_part, filt);
-    else
-        k_shell<false><<<grid, SF_SHELL_THREADS, smem, s>>>(d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter,
-                                                            d_part, filt);
+#define SF_SHELL_GO(M, N)                                                                                     \
+    k_shell<M, N><<<grid, N, smem, s>>>(d_v, mdi, mdk, mk3u, xc, Dmax, mni3, d_items, n_items, d_counter, d_part, filt)
+    if (nt == 256) {
+        if (mix) SF_SHELL_GO(true, 256);
+        else SF_SHELL_GO(false, 256);
+    } else {
+        if (mix) SF_SHELL_GO(true, 512);
+        else SF_SHELL_GO(false, 512);
+    }
+#undef SF_SHELL_GO
     sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;
 }
 
-static int shell_launch(bool mix, const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax,
-                        const WorkItem* d_items, int n_items, int* d_counter, double* d_part, ShellFilter filt,
-                        int num_sms, cudaStream_t s) {
-    int grid = 0;
-    size_t smem = 0;
-    SF_TRY(sf_shell_prepare(mix, mdi, mdk, mk3u, xc, Dmax, n_items, num_sms, &grid, &smem));
-    return sf_shell_launch_prepared(mix, grid, smem, d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter, d_part,
-                                    filt, s);
-}
-
 int sf_shell_fp64_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax, const WorkItem* d_items,
                          int n_items, int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s) {
-    return shell_launch(false, d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter, d_part, filt, num_sms, s);
-}
-
-int sf_shell_mixed_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, int Dmax, const WorkItem* d_items,
-                          int n_items, int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s) {
-    return shell_launch(true, d_v, mdi, mdk, mk3u, xc, Dmax, d_items, n_items, d_counter, d_part, filt, num_sms, s);
+    int grid = 0;
+    size_t smem = 0;
+    SF_TRY(sf_shell_prepare(false, 512, mdi, mdk, mk3u, xc, Dmax, mdi, n_items, num_sms, &grid, &smem));
+    return sf_shell_launch_prepared(false, 512, grid, smem, d_v, mdi, mdk, mk3u, xc, Dmax, mdi, d_items, n_items,
+                                    d_counter, d_part, filt, s);
 }
 
 // A[i1][i2][i3][i4][i5] = (-1)^(n_i1) prod_e sqrt(2 i_e + 1) * sum_{chunks} part[tile, chunk][i3][i4][i5]
@@ -493,19 +509,19 @@ int sf_reduce_launch(const VtxDev* d_v, int vtx, int ntiles, const WorkItem* d_i
     return SF_OK;
 }
 
-// the same reduction for many vertices in one launch: one CTA per output tile (ReduceJob)
+// the same reduction for many vertices in one launch: one CTA per (output tile, i3 range)
 __global__ void k_reduce_jobs(const VtxDev* __restrict__ V, const ReduceJob* __restrict__ jobs,
                               const WorkItem* __restrict__ items, const double* __restrict__ part) {
     const ReduceJob jb = jobs[blockIdx.x];
     const VtxDev& v = V[jb.vtx];
     const int ci1 = jb.tile / v.di[1], ci2 = jb.tile % v.di[1];
-    const int n3 = v.di[2] * v.di[3] * v.di[4];
+    const int n3 = jb.ni3 * v.di[3] * v.di[4];
     const double s12 = sqrt((double)(v.ilo[0] + 2 * ci1 + 1)) * sqrt((double)(v.ilo[1] + 2 * ci2 + 1)) *
                        ((ci1 & 1) ? -1.0 : 1.0);
     for (int q = threadIdx.x; q < n3; q += blockDim.x) {
         double acc = 0.0;
-        for (int c = 0; c < jb.nchunk; c++) acc += part[items[jb.item0 + c].part_off + q];
-        const int c5 = q % v.di[4], c4 = (q / v.di[4]) % v.di[3], c3 = q / (v.di[4] * v.di[3]);
+        for (int c = 0; c < jb.nchunk; c++) acc += part[items[jb.item0 + c * jb.stride].part_off + q];
+        const int c5 = q % v.di[4], c4 = (q / v.di[4]) % v.di[3], c3 = jb.i3b + q / (v.di[4] * v.di[3]);
         const double s = s12 * sqrt((double)(v.ilo[2] + 2 * c3 + 1)) * sqrt((double)(v.ilo[3] + 2 * c4 + 1)) *
                          sqrt((double)(v.ilo[4] + 2 * c5 + 1));
         jb.A[q] = s * acc;

@@ -77,10 +77,10 @@ def test_autotune(batch):
     bt, t, _ = batch
     plan = sf.Plan(t, sf.SF_FP64, 0, SHELL_END)
     base = [o.clone() for o in plan.run()]
-    xc, ips = plan.autotune(sample_shells=64)
+    xc, ips, nt, split = plan.autotune(sample_shells=64)
     info = plan.info()
-    assert 1 <= xc <= 16 and ips in (4, 8, 16, 32)
-    assert (info["x_chunk"], info["items_per_sm"]) == (xc, ips)
+    assert 1 <= xc <= 16 and ips in (4, 8, 16) and nt in (256, 512) and split in (1, 2)
+    assert (info["x_chunk"], info["items_per_sm"], info["threads"], info["i3_split"]) == (xc, ips, nt, split)
     assert info["grid"] >= 1 and info["n_items"] >= len(bt)
     outs = plan.graph_launch()
     plan.sync()
@@ -89,15 +89,24 @@ def test_autotune(batch):
         assert float((a - b).norm()) <= 1e-13 * max(n, 1e-300)
 
 
-@pytest.mark.parametrize("tiling", [(1, 1), (4, 32), (16, 256)])
+@pytest.mark.parametrize("tiling", [(1, 1), (4, 32), (16, 256), (6, 8, 512, 1), (3, 8, 256, 1), (5, 4, 256, 2),
+                                    (16, 16, 256, 2)])
 def test_explicit_tilings(batch, tiling):
     bt, t, _ = batch
     base = sf.sf_vertex_amplitude(t, shell_end=SHELL_END)
     plan = sf.Plan(t, sf.SF_FP64, 0, SHELL_END, tiling=tiling)
+    info = plan.info()
+    if len(tiling) == 4:
+        assert (info["threads"], info["i3_split"]) == tiling[2:]
     outs = plan.run()
     plan.sync()
     for a, b in zip(outs, base):
         assert float((a - b).norm()) <= 1e-13 * max(float(b.norm()), 1e-300)
+    mixed = sf.Plan(t, sf.SF_MIXED, 0, SHELL_END, tiling=tiling)
+    outm = mixed.run()
+    mixed.sync()
+    for a, b in zip(outm, base):
+        assert float((a - b).norm()) <= 1e-6 * max(float(b.norm()), 1e-300)
 
 
 def test_batched_plan_against_oracle(batch):
@@ -118,6 +127,10 @@ def test_plan_errors(batch):
     with pytest.raises(sf.SfError) as ei:
         sf.Plan(t, sf.SF_FP64, 0, SHELL_END, tiling=(17, 0))
     assert ei.value.code == sf.SF_ERR_ARG
+    for bad in ((0, 0, 384, 0), (0, 0, 512, 2), (0, 0, 0, 3), (0, -1)):
+        with pytest.raises(sf.SfError) as ei:
+            sf.Plan(t, sf.SF_FP64, 0, SHELL_END, tiling=bad)
+        assert ei.value.code == sf.SF_ERR_ARG
     with pytest.raises(sf.SfError) as ei:
         sf.Plan(t, sf.SF_FP64, -1, SHELL_END)
     assert ei.value.code == sf.SF_ERR_ARG
