@@ -30,6 +30,13 @@ SWEEP = [(lam, 10) for lam in range(1, 17)]
 GAMMA = 1.2
 # FP64 FMA pipe of the GB300: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.070 GHz (max SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# FP32 pipe: 152 SMs x 128 lanes x 2.070 GHz, in lane operations (FFMA, FADD, FMUL) per second
+FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_ff": 2}
+# FP32 lane operations per multiply-add of the compensated-pair phases (SF_MIXED_FF): D is a Dot2
+# step with a pair times a float (FMUL, 2 FFMA, TwoSum = 6, 2 FADD), F a pair times a pair (one
+# more FFMA); the FP32 booster phases take one FFMA per multiply-add
+FF_OPS = {"D": 11, "F": 12}
 # DRAM bytes (read + write) of the benchmark's shell-sum launch from one ncu capture per precision
 # (profiles/k_shell_mixed_sweep_traffic.md), valid while the kernel source hashes to "sha1".
 NCU_TRAFFIC = {"sha1": "f105b5962be0", "bytes_per_launch": {"mixed": 135627228928 + 161291776, "fp64": None}}
@@ -120,7 +127,20 @@ def executed_fmas(tj, dl, g0, g1):
     return {k: v * dim[1] for k, v in total.items()}
 
 
-FP32_PHASES_MIXED = ("B", "C", "G")   # booster contractions the mixed path runs in FP32
+FP32_PHASES_MIXED = ("B", "C", "G")   # booster contractions the mixed paths run in FP32
+
+
+def pipe_ops(phases, precision):
+    """(FP64 flops, FP32 lane ops) the shell kernel executes for a phase count dict."""
+    f64, f32 = 0, 0
+    for name, n in phases.items():
+        if precision != "fp64" and name in FP32_PHASES_MIXED:
+            f32 += n
+        elif precision == "mixed_ff" and name in FF_OPS:
+            f32 += FF_OPS[name] * n
+        else:
+            f64 += 2 * n
+    return f64, f32
 
 
 # ------------------------------------------------------------------------------------------
@@ -244,7 +264,7 @@ def batched_measure(shells, steps=3):
     n = sum(min(shells, (b["dl"] + 1) ** 6) for b in batch)
     stream = torch.cuda.current_stream()
     res, outs = {}, {}
-    for name, prec in (("fp64", sf.SF_FP64), ("mixed", sf.SF_MIXED)):
+    for name, prec in PRECISIONS.items():
         plan = sf.Plan(t, prec, 0, shells)
         tiling = plan.autotune(min(shells, 2048))
         plan.graph_launch()
@@ -260,13 +280,16 @@ def batched_measure(shells, steps=3):
                      "tiling": {"x_chunk": tiling[0], "items_per_sm": tiling[1]}}
         outs[name] = [o.clone() for o in plan.outputs]
         del plan
-    num = sum(float((a - b).norm()) ** 2 for a, b in zip(outs["mixed"], outs["fp64"])) ** 0.5
     den = sum(float(b.norm()) ** 2 for b in outs["fp64"]) ** 0.5
+    errs = {}
+    for name in ("mixed", "mixed_ff"):
+        num = sum(float((a - b).norm()) ** 2 for a, b in zip(outs[name], outs["fp64"])) ** 0.5
+        errs[name] = num / den if den > 0 else None
     return {"workload": "256 irregular vertices (spins 1/2..6, dl 0..12, gamma 0.1/1.2/5.0, seed 0), shells "
                         "[0, %d) of every vertex, %d shells in all; one CUDA-graph replay of a planned launch "
                         "per step, %d steps" % (shells, n, steps),
-            "fp64": res["fp64"], "mixed": res["mixed"],
-            "mixed_vs_fp64_rel_err": num / den if den > 0 else None}
+            "fp64": res["fp64"], "mixed": res["mixed"], "mixed_ff": res["mixed_ff"],
+            "rel_err_vs_fp64": errs}
 
 
 def main():
@@ -275,8 +298,8 @@ def main():
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
-                    help="path timed for `value`; the other path is timed for one step beside it")
+    ap.add_argument("--precision", default="mixed_ff", choices=list(PRECISIONS),
+                    help="path timed for `value`; the other paths are timed for one step beside it")
     ap.add_argument("--slices", type=int, default=16, help="steps per full pass over the sweep")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -335,7 +358,7 @@ def main():
     torch.cuda.set_device(local)
     import paper_2107_13952_gb300 as sf
     sf.load()
-    prec = sf.SF_FP64 if args.precision == "fp64" else sf.SF_MIXED
+    prec = PRECISIONS[args.precision]
     verts = [sf.vertex((lam,) * 10, GAMMA, dl) for lam, dl in SWEEP]
     dims = [sf.intertwiner_ranges((lam,) * 10, GAMMA, dl)[1] for lam, dl in SWEEP]
     S = args.slices
@@ -395,23 +418,28 @@ def main():
     clocks = clk.stop()
     ms_e2e, _, shells_e2e, _, _ = timed(True, args.warmup + args.steps)
 
-    # the other precision on one slice, timed the same way, and the relative error between them
-    other = sf.SF_FP64 if prec == sf.SF_MIXED else sf.SF_MIXED
+    # every path on one slice, timed the same way (one warm step each), and the relative error of
+    # the mixed paths against the FP64 path on that slice
     kk = (args.warmup + 2 * args.steps) * world + rank
-    step(kk, False, other)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    kms_o, n_o = step(kk, False, other)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_other = e0.elapsed_time(e1)
-    ref = [o.clone() for o in outs]
-    step(kk, False, prec)
-    torch.cuda.synchronize()
-    num = sum(float((o - r).norm()) ** 2 for o, r in zip(outs, ref)) ** 0.5
-    den = sum(float(r.norm()) ** 2 for r in ref) ** 0.5
-    rel_err = num / den if den > 0 else None
+    others, res_slice = {}, {}
+    for name, p in PRECISIONS.items():
+        step(kk, False, p)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        kms_o, n_o = step(kk, False, p)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_o = e0.elapsed_time(e1)
+        res_slice[name] = [o.clone() for o in outs]
+        if name != args.precision:
+            others[name] = {"value": n_o * world / (ms_o / 1e3), "unit": "shells/s", "ms_per_step": ms_o,
+                            "kernel_ms_per_step": kms_o}
+    den = sum(float(r.norm()) ** 2 for r in res_slice["fp64"]) ** 0.5
+    rel_err = {}
+    for name in ("mixed", "mixed_ff"):
+        num = sum(float((o - r).norm()) ** 2 for o, r in zip(res_slice[name], res_slice["fp64"])) ** 0.5
+        rel_err[name] = num / den if den > 0 else None
 
     # max over ranks
     if world > 1:
@@ -428,18 +456,29 @@ def main():
         return
 
     # roofline of the dominant kernel (the shell sum): executed FP64 flops / event-timed duration
-    flops, flops32 = 0, 0
+    flops, ops32 = 0, 0
     for k in slices:
         _, _, g0, g1 = slice_bounds(k)
         for lam, dl in SWEEP:
-            ph = executed_fmas((lam,) * 10, dl, g0, g1)
-            for name, n in ph.items():
-                if args.precision == "mixed" and name in FP32_PHASES_MIXED:
-                    flops32 += 2 * n
-                else:
-                    flops += 2 * n
+            f64, f32 = pipe_ops(executed_fmas((lam,) * 10, dl, g0, g1), args.precision)
+            flops += f64
+            ops32 += f32
     kern_s = sum(kms_all) / 1e3
-    achieved = flops / kern_s / 1e12 if kern_s > 0 else None
+    fp64_tflops = flops / kern_s / 1e12 if kern_s > 0 else None
+    fp32_tops = ops32 / kern_s / 1e12 if kern_s > 0 else None
+    if args.precision == "mixed_ff":
+        # the FP32 pipe carries the kernel: lane operations (FFMA, FADD, FMUL) per second
+        roof = {"bound": "alu", "achieved": fp32_tops, "peak": FP32_PEAK_TOPS, "unit": "Tops/s (FP32 lane ops)",
+                "frac": (fp32_tops / FP32_PEAK_TOPS) if fp32_tops else None,
+                "ops_counted": "FP32 lane operations of the loops (compensated-pair steps at 11-12 operations per "
+                               "multiply-add, FP32 booster contractions at one FFMA), trip counts x operations",
+                "fp64_tflops": fp64_tflops, "fp64_frac": (fp64_tflops / FP64_PEAK_TFLOPS) if fp64_tflops else None}
+    else:
+        roof = {"bound": "alu", "achieved": fp64_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": (fp64_tflops / FP64_PEAK_TFLOPS) if fp64_tflops else None,
+                "flops_counted": "FP64-pipe FMAs the kernel executes x 2 (loop trip counts); the FP32 phases of the "
+                                 "mixed path are reported separately",
+                "fp32_tops": fp32_tops}
     traffic = None
     if NCU_TRAFFIC["sha1"] == kernel_sha1():
         traffic = NCU_TRAFFIC["bytes_per_launch"].get(args.precision)
@@ -457,32 +496,25 @@ def main():
 
     d2h = sum(h.numel() * 8 for h in host)
     h2d = len(verts) * 56
-    other_name = "fp64" if args.precision == "mixed" else "mixed"
     line = {
         "metric": "EPRL vertex shells/sec (mixed vs FP64 GPU path) at stated relative error",
         "value": value, "unit": "shells/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f64+f32", "data": "synthetic",
+        "dtype": {"fp64": "f64", "mixed": "f64+f32", "mixed_ff": "f64+f32+f32x2"}[args.precision], "data": "synthetic",
         "config": {"workload": "homogeneous sweep: 16 vertices, all spins j=lambda/2 for lambda=1..16, gamma=1.2, "
                                "dl=10 (11^6 shells each), rule r_max=40 / 40 panels x 50 nodes; one step = 6j "
                                "tables + d-tables + boosters of all 16 vertices + shell sum over a 1/%d slice "
                                "of every vertex's group-major shell range" % S,
                    "slices_per_pass": S, "precision": args.precision, "cache": "working set < L2 per kernel; "
                    "no flush (compute-bound FP64 path)"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": traffic,
-                     "kernel": "k_shell<%d>" % (1 if args.precision == "mixed" else 0),
-                     "flops_counted": "FP64-pipe FMAs the kernel executes x 2 (loop trip counts); the FP32 "
-                                      "phases of the mixed path are reported separately",
-                     "fp32_tflops": (flops32 / kern_s / 1e12) if kern_s > 0 else None,
-                     "kernel_ms_per_step": 1e3 * kern_s / args.steps},
+        "roofline": dict(roof, traffic=traffic, kernel="k_shell<%d>" % PRECISIONS[args.precision],
+                         kernel_ms_per_step=1e3 * kern_s / args.steps),
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "shells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clocks,
         "path": args.precision,
-        other_name: {"value": n_o * world / (ms_other / 1e3), "unit": "shells/s", "ms_per_step": ms_other,
-                     "kernel_ms_per_step": kms_o},
+        "other_paths": others,
         "batched": batched,
         "mixed_vs_fp64": {"rel_err": rel_err, "stated_bound": 1e-6,
                           "metric": "||A_mixed - A_fp64|| / ||A_fp64|| over the 16 vertices of one slice"},

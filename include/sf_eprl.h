@@ -75,9 +75,16 @@ typedef struct {
 
 typedef enum {
     SF_FP64  = 0,   /* every step in FP64                                                         */
-    SF_MIXED = 1    /* booster contractions over k2, k3, k4 with FP32 inputs and FP32 accumulation
+    SF_MIXED = 1,   /* booster contractions over k2, k3, k4 with FP32 inputs and FP32 accumulation
                        within one (l24, l34) set of shells; the {6j} contractions, the k5 contraction
                        and every sum across shells in FP64                                        */
+    SF_MIXED_FF = 2 /* booster contractions as SF_MIXED; the {6j} contractions (the S3 contraction
+                       over k3 and the x-sum with S1 S2) in compensated FP32 pairs: operands are
+                       (hi, lo) float pairs holding about 48 significant bits, products are formed
+                       exactly (Dekker) and summed with an error-compensated dot product (Ogita,
+                       Rump and Oishi, "Accurate sum and dot product", 2005, Dot2), so these sums
+                       keep nearly FP64 accuracy on the FP32 pipe; the k5 contraction and every
+                       sum across (l24, l34) sets and groups in FP64                              */
 } sf_precision;
 
 typedef struct sf_tables sf_tables;
@@ -119,7 +126,7 @@ int sf_boosters_upload(sf_tables* t, int32_t vertex, int32_t edge, const double*
 int sf_boosters_download(const sf_tables* t, int32_t vertex, int32_t edge, double* B, cudaStream_t stream);
 
 /* Vertex amplitude tensors by the shell sum (framed algorithm steps 5-7).
- *   precision  SF_FP64 or SF_MIXED.
+ *   precision  SF_FP64, SF_MIXED or SF_MIXED_FF.
  *   shell_begin, shell_end: linear shell range [begin, end) of every vertex (clamped to its shell
  *     count; pass 0 and INT64_MAX for all shells). Partial sums over disjoint ranges add up, so a
  *     long sum can be split or resumed.

@@ -45,6 +45,8 @@ struct VertexHost {
     int64_t nshell = 0;
     Table6j S[5];
     float* d_S4f = nullptr;
+    float* d_S5f = nullptr;
+    float2* d_Sff[3] = {nullptr, nullptr, nullptr};
     int64_t ntrip = 0;
     int32_t dkmax[4];
     std::vector<int32_t> klo[4];
@@ -259,6 +261,8 @@ static int upload_vtxdev(sf_tables* t) {
         d.nshell = h.nshell;
         for (int k = 0; k < 5; k++) { d.S[k] = h.S[k].d_vals; d.slot[k] = h.S[k].d_slots; }
         d.S4f = h.d_S4f;
+        d.S5f = h.d_S5f;
+        for (int k = 0; k < 3; k++) d.Sff[k] = h.d_Sff[k];
         for (int e = 0; e < 4; e++) { d.B[e] = h.d_B[e]; d.klo[e] = h.d_klo[e]; d.dkmax[e] = h.dkmax[e]; }
         d.ntrip = h.ntrip;
         for (int f = 0; f < 10; f++) { d.dtab[f] = h.d_dtab[f]; d.nl[f] = h.nl[f]; }
@@ -318,6 +322,8 @@ extern "C" int sf_6j_table(const sf_vertex* v, int32_t n, sf_tables** out, cudaS
             plan_boosters(h);
             for (int k = 0; k < 5 && rc == SF_OK; k++) {
                 if (k == 3) rc = dev_alloc(t, (void**)&h.d_S4f, h.S[3].n * sizeof(float));
+                if (k == 4) rc = dev_alloc(t, (void**)&h.d_S5f, h.S[4].n * sizeof(float));
+                if (k < 3) rc = dev_alloc(t, (void**)&h.d_Sff[k], h.S[k].n * sizeof(float2));
                 if (rc != SF_OK) break;
                 rc = dev_alloc(t, (void**)&h.S[k].d_slots, h.S[k].slots.size() * sizeof(SlotDesc));
                 if (rc == SF_OK) rc = dev_alloc(t, (void**)&h.S[k].d_vals, h.S[k].n * sizeof(double));
@@ -347,6 +353,8 @@ extern "C" int sf_6j_table(const sf_vertex* v, int32_t n, sf_tables** out, cudaS
                 rc = sf_sixj_table_build(k + 1, t->d_vtx + i, h.S[k].d_slots, (int)h.S[k].slots.size(), h.S[k].n,
                                          h.S[k].d_vals, t->d_fact, t->d_status, t->num_sms, stream);
             if (rc == SF_OK) rc = sf_to_float(h.S[3].d_vals, h.d_S4f, h.S[3].n, t->num_sms, stream);
+            if (rc == SF_OK) rc = sf_to_float(h.S[4].d_vals, h.d_S5f, h.S[4].n, t->num_sms, stream);
+            for (int k = 0; k < 3 && rc == SF_OK; k++) rc = sf_to_ff(h.S[k].d_vals, h.d_Sff[k], h.S[k].n, t->num_sms, stream);
         }
         if (rc != SF_OK) break;
         rc = check_status(t, stream, "sf_6j_table");
@@ -499,10 +507,10 @@ static bool shell_tile_fits(const sf_tables* t, int nt, int split) {
 }
 
 // largest x chunk <= cap whose shared memory fits the CTA size's limit; 0 if none
-static int shell_max_xc(const ShellDims& d, bool mix, int nt, int split, int cap) {
+static int shell_max_xc(const ShellDims& d, int mode, int nt, int split, int cap) {
     const int mni3 = (d.mdi3 + split - 1) / split;
     for (int xc = std::max(1, std::min(cap, 16)); xc >= 1; xc--)
-        if (sf_shell_smem_doubles(d.mdi, d.mdk, d.mk3u, xc, d.Dmax, mni3, mix) * sizeof(double) <= shell_smem_limit(nt))
+        if (sf_shell_smem_doubles(d.mdi, d.mdk, d.mk3u, xc, d.Dmax, mni3, mode) * sizeof(double) <= shell_smem_limit(nt))
             return xc;
     return 0;
 }
@@ -511,7 +519,7 @@ static int shell_max_xc(const ShellDims& d, bool mix, int nt, int split, int cap
 // on whole tiles when the tile fits with an x chunk of at least 4, else one CTA of 512 threads.
 // Half tiles (measured slower at spin 8, where only they give two CTAs per SM: the duplicated
 // staging costs more than the overlap gains) are used only when requested.
-static int shell_config(const sf_tables* t, bool mix, const sf_tiling& req, ShellConfig* out) {
+static int shell_config(const sf_tables* t, int mode, const sf_tiling& req, ShellConfig* out) {
     if (req.x_chunk < 0 || req.x_chunk > 16) return sf_set_error(SF_ERR_ARG, "x_chunk must be 0 (default) or 1..16");
     if (req.items_per_sm < 0 || req.items_per_sm > 256) return sf_set_error(SF_ERR_ARG, "items_per_sm must be 0..256");
     if (req.threads != 0 && req.threads != 256 && req.threads != 512)
@@ -527,7 +535,7 @@ static int shell_config(const sf_tables* t, bool mix, const sf_tiling& req, Shel
         if (req.i3_split != 0 && req.i3_split != split) continue;
         if (req.i3_split == 0 && split == 2) continue;   // half tiles only on request (duplicated staging)
         if (!shell_tile_fits(t, nt, split)) continue;
-        const int xc = shell_max_xc(d, mix, nt, split, cap);
+        const int xc = shell_max_xc(d, mode, nt, split, cap);
         if (xc == 0) continue;
         if (!explicit_cfg && nt == 256 && xc < std::min(4, cap)) continue;
         out->nt = nt;
@@ -639,7 +647,8 @@ static int schedule_shells(const sf_tables* t, bool whole_range, int64_t shell_b
 extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t shell_begin, int64_t shell_end,
                                    const int64_t* shell_list, int64_t n_list, double* const* A_out, cudaStream_t stream) {
     if (!t || !A_out) return sf_set_error(SF_ERR_ARG, "null argument");
-    if (precision != SF_FP64 && precision != SF_MIXED) return sf_set_error(SF_ERR_ARG, "unknown precision");
+    if (precision != SF_FP64 && precision != SF_MIXED && precision != SF_MIXED_FF)
+        return sf_set_error(SF_ERR_ARG, "unknown precision");
     if (shell_list && t->vs.size() != 1) return sf_set_error(SF_ERR_ARG, "a shell list needs single-vertex tables");
     if (shell_list && n_list < 0) return sf_set_error(SF_ERR_ARG, "negative list length");
     if (!shell_list && shell_begin < 0) return sf_set_error(SF_ERR_ARG, "negative shell_begin");
@@ -647,7 +656,7 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
         if (!t->vs[i].boosters_ready) return sf_set_error(SF_ERR_ARG, "boosters of vertex %zu were never computed or uploaded", i);
         if (!A_out[i]) return sf_set_error(SF_ERR_ARG, "null output for vertex %zu", i);
     }
-    const bool mix = precision == SF_MIXED;
+    const int mix = (int)precision;
     ShellConfig cfg;
     SF_TRY(shell_config(t, mix, sf_tiling{}, &cfg));
     ShellSchedule sc;
@@ -708,7 +717,7 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
 // ----------------------------------------------------------------------------------------------
 struct sf_plan {
     sf_tables* t = nullptr;
-    bool mix = false;
+    int mix = 0;   // shell-kernel mode (the sf_precision value)
     int64_t begin = 0, end = 0;
     std::vector<double*> A;
     sf_tiling tiling{};
@@ -802,7 +811,8 @@ extern "C" int sf_plan_create(sf_tables* t, sf_precision precision, int64_t shel
     if (!out) return sf_set_error(SF_ERR_ARG, "null output pointer");
     *out = nullptr;
     if (!t || !A_out) return sf_set_error(SF_ERR_ARG, "null argument");
-    if (precision != SF_FP64 && precision != SF_MIXED) return sf_set_error(SF_ERR_ARG, "unknown precision");
+    if (precision != SF_FP64 && precision != SF_MIXED && precision != SF_MIXED_FF)
+        return sf_set_error(SF_ERR_ARG, "unknown precision");
     if (shell_begin < 0) return sf_set_error(SF_ERR_ARG, "negative shell_begin");
     for (size_t i = 0; i < t->vs.size(); i++) {
         if (!t->vs[i].boosters_ready) return sf_set_error(SF_ERR_ARG, "boosters of vertex %zu were never computed or uploaded", i);
@@ -810,7 +820,7 @@ extern "C" int sf_plan_create(sf_tables* t, sf_precision precision, int64_t shel
     }
     sf_plan* p = new sf_plan();
     p->t = t;
-    p->mix = precision == SF_MIXED;
+    p->mix = (int)precision;
     p->begin = shell_begin;
     p->end = shell_end;
     p->A.assign(A_out, A_out + t->vs.size());

@@ -221,7 +221,9 @@ struct VtxDev {
     int32_t ilo[5], di[5];     // intertwiner ranges
     int64_t nshell;            // D^6
     const double* S[5];        // {6j} tables S1..S5
-    const float* S4f;          // S4 rounded to FP32 once (mixed path)
+    const float* S4f;          // S4 rounded to FP32 once (mixed paths)
+    const float* S5f;          // S5 rounded to FP32 once (SF_MIXED_FF)
+    const float2* Sff[3];      // S1, S2, S3 as (hi, lo) float pairs, hi + lo = S to about 2^-48 (SF_MIXED_FF)
     const SlotDesc* slot[5];
     const double* B[4];        // boosters of edges 2..5: [t][i][k - klo(t)], padded to dkmax
     const int32_t* klo[4];
@@ -258,6 +260,8 @@ int sf_fact_table_build(dd* F, cudaStream_t s);
 int sf_sixj_table_build(int table_id, const VtxDev* d_v, const SlotDesc* d_slots, int nslots, int64_t n,
                         double* d_out, const dd* F, int* d_status, int num_sms, cudaStream_t s);
 int sf_to_float(const double* d_in, float* d_out, int64_t n, int num_sms, cudaStream_t s);
+// (hi, lo) float pairs: hi = fl32(d), lo = fl32(d - hi)
+int sf_to_ff(const double* d_in, float2* d_out, int64_t n, int num_sms, cudaStream_t s);
 int sf_rule_build(const sf_quad_rule* q, double* d_gl, double* d_x, double* d_w, double* d_r, double* d_W,
                   cudaStream_t s);
 int sf_dtable_build(int tk, double gamma, int nl, int nnodes, const double* d_r, const double* d_gl, double2* d_out,
@@ -265,14 +269,16 @@ int sf_dtable_build(int tk, double gamma, int nl, int nnodes, const double* d_r,
 size_t sf_booster_smem(int tj1, int tj2, int tj3, int tj4, int nk);
 int sf_booster_build(const VtxDev* d_v, int edge, int ntrip, size_t smem, const double* d_W, int nnodes,
                      const dd* F, double* d_Aj, double* d_Cj, double* d_B, int* d_status, cudaStream_t s);
+// Shell-kernel modes: the sf_precision values (0 FP64, 1 mixed, 2 mixed with compensated FP32
+// pairs for the {6j} contractions).
 // shared memory (in doubles) of the shell kernel; mni3 = largest i3 extent of a work item
-size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, int mni3, bool mix);
+size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, int mni3, int mode);
 // sets the kernel's shared-memory attribute and returns its grid (resident CTAs, at most n_items);
 // host-only, so a capturable launch sequence calls it beforehand. nt: 256 or 512 threads per CTA.
-int sf_shell_prepare(bool mix, int nt, int mdi, int mdk, int mk3u, int xc, int Dmax, int mni3, int n_items, int num_sms,
+int sf_shell_prepare(int mode, int nt, int mdi, int mdk, int mk3u, int xc, int Dmax, int mni3, int n_items, int num_sms,
                      int* grid, size_t* smem);
 // zeroes the work counter and launches the persistent shell kernel (stream work only)
-int sf_shell_launch_prepared(bool mix, int nt, int grid, size_t smem, const VtxDev* d_v, int mdi, int mdk, int mk3u,
+int sf_shell_launch_prepared(int mode, int nt, int grid, size_t smem, const VtxDev* d_v, int mdi, int mdk, int mk3u,
                              int xc, int Dmax, int mni3, const WorkItem* d_items, int n_items, int* d_counter,
                              double* d_part, ShellFilter filt, cudaStream_t s);
 // FP64 shell kernel with 512 threads over whole-tile items (i3b = 0, ni3 = di3), one call

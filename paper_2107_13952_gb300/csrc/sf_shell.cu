@@ -77,6 +77,147 @@ __device__ __forceinline__ void flat_gemm(int nbatch, int M, int N, int K, const
     }
 }
 
+// ----------------------------------------------------------------------------------------------
+// Compensated FP32 pairs (SF_MIXED_FF). A value is held as (hi, lo) with |lo| <= ulp(hi)/2.
+// Error-free transformations (Knuth's TwoSum, Dekker's FastTwoSum, the FMA form of Dekker's
+// TwoProduct) as published; the intrinsics keep the compiler from contracting them into FMAs.
+// Dot products follow Ogita, Rump and Oishi's Dot2 (SIAM J. Sci. Comput. 26, 2005): the exact
+// products' high parts are summed with TwoSum, every rounding error goes to a second FP32 sum, and
+// the pair is normalised at the end, so the result is as accurate as a dot product in twice the
+// working precision (about 2^-48 relative to the sum of |terms|).
+// ----------------------------------------------------------------------------------------------
+__device__ __forceinline__ void ff_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void ff_fast_two_sum(float a, float b, float& s, float& e) {   // |a| >= |b| or a == 0
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+// one Dot2 step: (sh, sl) += (ah + al) * b, with b a single float
+__device__ __forceinline__ void ff_dot_step(float ah, float al, float b, float& sh, float& sl) {
+    const float p = __fmul_rn(ah, b);
+    float e = __fmaf_rn(ah, b, -p);
+    e = __fmaf_rn(al, b, e);
+    float s, t;
+    ff_two_sum(sh, p, s, t);
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(t, e));
+}
+// one Dot2 step with a pair on both sides (the lo * lo term, below 2^-48 relative, is dropped)
+__device__ __forceinline__ void ff_dot_step2(float ah, float al, float bh, float bl, float& sh, float& sl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    float s, t;
+    ff_two_sum(sh, p, s, t);
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(t, e));
+}
+// normalised product of two pairs
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    float h, l;
+    ff_fast_two_sum(p, e, h, l);
+    return make_float2(h, l);
+}
+// normalised product of a pair and a float
+__device__ __forceinline__ float2 ff_mul_f(float2 a, float b) {
+    const float p = __fmul_rn(a.x, b);
+    float e = __fmaf_rn(a.x, b, -p);
+    e = __fmaf_rn(a.y, b, e);
+    float h, l;
+    ff_fast_two_sum(p, e, h, l);
+    return make_float2(h, l);
+}
+// normalised pair from an unnormalised Dot2 accumulator (TwoSum: |sl| may exceed |sh| after cancellation)
+__device__ __forceinline__ float2 ff_norm(float sh, float sl) {
+    float h, l;
+    ff_two_sum(sh, sl, h, l);
+    return make_float2(h, l);
+}
+// pair + pair (both normalised), normalised
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    float s, t;
+    ff_two_sum(a.x, b.x, s, t);
+    t = __fadd_rn(t, __fadd_rn(a.y, b.y));
+    float h, l;
+    ff_fast_two_sum(s, t, h, l);
+    return make_float2(h, l);
+}
+
+// C[bt][m][n] (+)= sum_k A[bt][m][k] B[bt][k][n] with pair operands A, pair or float operands B
+// and Dot2 accumulation (k in increasing order). Each thread computes RM rows m of one column n;
+// consecutive threads take consecutive n, so B loads are contiguous and A loads are broadcasts.
+template <int RM, bool BPAIR, bool ACC>
+__device__ __forceinline__ void ff_gemm(int nbatch, int M, int N, int K, const float2* A, int a_bs, int am, int ak,
+                                        const void* Bv, int b_bs, int bk, int bn, float2* C, int c_bs, int cm, int cn,
+                                        int tid, int nth) {
+    const int MB = (M + RM - 1) / RM, L = nbatch * MB * N;
+    for (int o = tid; o < L; o += nth) {
+        const int n = o % N, r = o / N, mb = r % MB, bt = r / MB;
+        const float2* ap[RM];
+#pragma unroll
+        for (int i = 0; i < RM; i++) {
+            const int m = imin_(mb * RM + i, M - 1);
+            ap[i] = A + bt * a_bs + m * am;
+        }
+        float sh[RM], sl[RM];
+#pragma unroll
+        for (int i = 0; i < RM; i++) { sh[i] = 0.0f; sl[i] = 0.0f; }
+        const int boff = bt * b_bs + n * bn;
+        for (int k = 0; k < K; k++) {
+            if constexpr (BPAIR) {
+                const float2 b = reinterpret_cast<const float2*>(Bv)[boff + k * bk];
+#pragma unroll
+                for (int i = 0; i < RM; i++) {
+                    const float2 a = ap[i][k * ak];
+                    ff_dot_step2(a.x, a.y, b.x, b.y, sh[i], sl[i]);
+                }
+            } else {
+                const float b = reinterpret_cast<const float*>(Bv)[boff + k * bk];
+#pragma unroll
+                for (int i = 0; i < RM; i++) {
+                    const float2 a = ap[i][k * ak];
+                    ff_dot_step(a.x, a.y, b, sh[i], sl[i]);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < RM; i++) {
+            const int m = mb * RM + i;
+            if (m < M) {
+                float2* cp = C + bt * c_bs + m * cm + n * cn;
+                const float2 v = ff_norm(sh[i], sl[i]);
+                if (ACC) *cp = ff_add(*cp, v);
+                else *cp = v;
+            }
+        }
+    }
+}
+
+// {6j} lookups with box and parity checks for the FP32 copies (zero outside)
+__device__ __forceinline__ int s6_index(const SlotDesc& sd, int a, int b, int x) {
+    const int da = a - sd.alo, db = b - sd.blo, dx = x - sd.xlo;
+    if (((da | db | dx) & 1) != 0) return -1;
+    const int ia = da >> 1, ib = db >> 1, ix = dx >> 1;
+    if ((unsigned)ia >= (unsigned)sd.na || (unsigned)ib >= (unsigned)sd.nb || (unsigned)ix >= (unsigned)sd.nx) return -1;
+    return (ia * sd.nb + ib) * sd.nx + ix;
+}
+__device__ __forceinline__ float2 s6ff(const float2* __restrict__ S, const SlotDesc& sd, int a, int b, int x) {
+    const int i = s6_index(sd, a, b, x);
+    return i < 0 ? make_float2(0.0f, 0.0f) : __ldg(S + sd.off + i);
+}
+__device__ __forceinline__ float s6f(const float* __restrict__ S, const SlotDesc& sd, int a, int b, int x) {
+    const int i = s6_index(sd, a, b, x);
+    return i < 0 ? 0.0f : __ldg(S + sd.off + i);
+}
+
 #define SF_TRT 2   // output-tile register blocks per thread (2 x 4 doubles each)
 
 struct ShellSmem {
@@ -116,28 +257,36 @@ __device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int 
     return s;
 }
 
-size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, int mni3, bool mix) {
+size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, int mni3, int mode) {
+    const bool mix = mode >= 1;
     const size_t chunk = shell_chunk_doubles(mdk, mk3u, xc, D, mni3);
     const size_t vf = mix ? ((size_t)mdk * mdk * mni3 + 1) / 2 : 0;
     return (size_t)mdi * mdk * mni3 + (size_t)mdk * mdk * mni3 + (size_t)D * mdk * mni3 + 2ull * mdi * mdk +
            ((size_t)mdi * mdk + 1) / 2 + (chunk > vf ? chunk : vf);
 }
 
-// MIX = false: every phase in FP64 (the FP64 path). MIX = true (the mixed path): the booster
+// MODE 0: every phase in FP64 (the FP64 path). MODE 1 (the mixed path): the booster
 // contractions over k2 (B2, with S4 S5), over k3 (B3, summed over l23) and over k4 (B4) take FP32
 // inputs and accumulate in FP32 within one (l24, l34) 5-tuple; the {6j} contractions (S3, and the
 // x-sum with S1 S2), every sum across 5-tuples and groups, and the k5 contraction stay FP64.
+// MODE 2: as MODE 1, but the {6j} contractions (phases D and F, and the products Q) run on
+// compensated FP32 pairs with Dot2 accumulation, from (hi, lo) copies of S1, S2, S3; V is kept as
+// a pair across the x chunks of a 5-tuple. GB300's FP64 pipe issues 2 FMAs per clock per SM
+// against 128 FP32 FMAs, so a pair step of about 11 FP32 instructions is several times cheaper.
 // NT threads per CTA: 512 (one CTA per SM) or 256 (two CTAs per SM, whose phases interleave).
 // A work item covers the i3 sub-range [i3b, i3b + ni3) of its output tile.
-template <bool MIX, int NT>
+template <int MODE, int NT>
 __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict__ V, int mdi, int mdk, int mk3u, int XC,
                                                         int Dmax, int mni3, const WorkItem* __restrict__ items,
                                                         int n_items, int* counter, double* __restrict__ part,
                                                         ShellFilter filt) {
+    constexpr bool MIX = MODE >= 1;
+    constexpr bool FF = MODE == 2;
     extern __shared__ double smem[];
     __shared__ int s_item;
     __shared__ int s_k2lo[SF_MAX_DL + 1], s_nk2[SF_MAX_DL + 1], s_k3lo[SF_MAX_DL + 1], s_nk3[SF_MAX_DL + 1];
     __shared__ double s_sig[SF_MAX_DL + 1];
+    __shared__ float s_sigf[SF_MAX_DL + 1];
     __shared__ SlotDesc s_sd4[SF_MAX_DL + 1];
     const ShellSmem sm = carve(smem, mdi, mdk, mk3u, XC, Dmax, mni3);
     const int tid = threadIdx.x, nth = NT;
@@ -232,6 +381,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                     s_k2lo[d] = k2lo; s_nk2[d] = nk2; s_k3lo[d] = k3lo; s_nk3[d] = nk3;
                     const int E2 = jsum + k2lo + k3lo + k4lo + k5lo + l23 + l24 + l25 + l34 + l35 + l45;
                     s_sig[d] = ((E2 >> 1) & 1) ? -1.0 : 1.0;
+                    s_sigf[d] = ((E2 >> 1) & 1) ? -1.0f : 1.0f;
                     s_sd4[d] = load_slot(v.slot[3] + d * D + d24);
                 }
                 const int nk3u = (k3uhi - k3ulo) / 2 + 1;
@@ -265,20 +415,31 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                         const int k2 = s_k2lo[d] + 2 * c2, x = xc0 + 2 * xc;
                         const int t2 = (d * D + d24) * D + d25;
                         const double b2 = __ldg(v.B[0] + ((int64_t)t2 * v.di[1] + ci2) * v.dkmax[0] + c2);
-                        const double f = (double)(k2 + 1) * ((c2 & 1) ? -s_sig[d] : s_sig[d]);
-                        const double sb = f * b2 * s6(v.S[4], sd5, k2, i1, x);
-                        if constexpr (MIX) reinterpret_cast<float*>(sm.SB)[(d * mdk + c2) * XC + xc] = (float)sb;
-                        else sm.SB[(d * mdk + c2) * XC + xc] = sb;
+                        if constexpr (FF) {
+                            const float f = (float)(k2 + 1) * ((c2 & 1) ? -s_sigf[d] : s_sigf[d]);
+                            reinterpret_cast<float*>(sm.SB)[(d * mdk + c2) * XC + xc] =
+                                (f * (float)b2) * s6f(v.S5f, sd5, k2, i1, x);
+                        } else {
+                            const double f = (double)(k2 + 1) * ((c2 & 1) ? -s_sig[d] : s_sig[d]);
+                            const double sb = f * b2 * s6(v.S[4], sd5, k2, i1, x);
+                            if constexpr (MIX) reinterpret_cast<float*>(sm.SB)[(d * mdk + c2) * XC + xc] = (float)sb;
+                            else sm.SB[(d * mdk + c2) * XC + xc] = sb;
+                        }
                     }
                     for (int q = tid; q < nxc * nk4 * nk3u; q += nth) {
                         const int ku = q % nk3u, r = q / nk3u, c4 = r % nk4, xc = r / nk4;
-                        sm.S3s[q] = s6(v.S[2], sd3, k4lo + 2 * c4, k3ulo + 2 * ku, xc0 + 2 * xc);
+                        if constexpr (FF)
+                            reinterpret_cast<float2*>(sm.S3s)[q] = s6ff(v.Sff[2], sd3, k4lo + 2 * c4, k3ulo + 2 * ku, xc0 + 2 * xc);
+                        else sm.S3s[q] = s6(v.S[2], sd3, k4lo + 2 * c4, k3ulo + 2 * ku, xc0 + 2 * xc);
                     }
                     // E: Q[k5][k4][x] = (2x+1) S1[i1,k5,x] S2[k5,k4,x]
                     for (int q = tid; q < nk5 * nk4 * nxc; q += nth) {
                         const int xc = q % nxc, r = q / nxc, c4 = r % nk4, c5 = r / nk4;
                         const int k5 = k5lo + 2 * c5, k4 = k4lo + 2 * c4, x = xc0 + 2 * xc;
-                        sm.Q[q] = (double)(x + 1) * s6(v.S[0], sd1, i1, k5, x) * s6(v.S[1], sd2, k5, k4, x);
+                        if constexpr (FF)
+                            reinterpret_cast<float2*>(sm.Q)[q] =
+                                ff_mul_f(ff_mul(s6ff(v.Sff[0], sd1, i1, k5, x), s6ff(v.Sff[1], sd2, k5, k4, x)), (float)(x + 1));
+                        else sm.Q[q] = (double)(x + 1) * s6(v.S[0], sd1, i1, k5, x) * s6(v.S[1], sd2, k5, k4, x);
                     }
                     __syncthreads();
                     // B: R[d][k3][x] = (2k3+1)(-1)^(k3-k3lo) sum_k2 S4_d[k3,k2,x] SB[d][k2][x]
@@ -358,26 +519,51 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                                     if (i30 + 3 < di3) a3 = fma(rr, bp[3], a3);
                                 }
                             }
-                            double* up = sm.U + (ku * nxc + xc) * di3 + i30;
-                            up[0] = a0;
-                            if (i30 + 1 < di3) up[1] = a1;
-                            if (i30 + 2 < di3) up[2] = a2;
-                            if (i30 + 3 < di3) up[3] = a3;
+                            if constexpr (FF) {
+                                float* up = reinterpret_cast<float*>(sm.U) + (ku * nxc + xc) * di3 + i30;
+                                up[0] = (float)a0;
+                                if (i30 + 1 < di3) up[1] = (float)a1;
+                                if (i30 + 2 < di3) up[2] = (float)a2;
+                                if (i30 + 3 < di3) up[3] = (float)a3;
+                            } else {
+                                double* up = sm.U + (ku * nxc + xc) * di3 + i30;
+                                up[0] = a0;
+                                if (i30 + 1 < di3) up[1] = a1;
+                                if (i30 + 2 < di3) up[2] = a2;
+                                if (i30 + 3 < di3) up[3] = a3;
+                            }
                         }
                     }
                     __syncthreads();
                     // D: P[k4][x][i3] = sum_k3u S3s[x][k4][k3u] U[k3u][x][i3]        (batch over x)
-                    flat_gemm<double, false>(nxc, nk4, di3, nk3u, sm.S3s, nk4 * nk3u, nk3u, 1, sm.U, di3, nxc * di3, 1,
-                                          sm.P, di3, nxc * di3, 1, tid, nth);
+                    if constexpr (FF)
+                        ff_gemm<2, false, false>(nxc, nk4, di3, nk3u, reinterpret_cast<const float2*>(sm.S3s), nk4 * nk3u,
+                                                 nk3u, 1, sm.U, di3, nxc * di3, 1, reinterpret_cast<float2*>(sm.P), di3,
+                                                 nxc * di3, 1, tid, nth);
+                    else
+                        flat_gemm<double, false>(nxc, nk4, di3, nk3u, sm.S3s, nk4 * nk3u, nk3u, 1, sm.U, di3, nxc * di3, 1,
+                                                 sm.P, di3, nxc * di3, 1, tid, nth);
                     __syncthreads();
                     // F: V[k4][k5][i3] += sum_x Q[k5][k4][x] P[k4][x][i3]             (batch over k4)
-                    flat_gemm<double, true>(nk4, nk5, di3, nxc, sm.Q, nxc, nk4 * nxc, 1, sm.P, nxc * di3, di3, 1,
-                                         sm.V, nk5 * di3, di3, 1, tid, nth);
+                    if constexpr (FF)
+                        ff_gemm<2, true, true>(nk4, nk5, di3, nxc, reinterpret_cast<const float2*>(sm.Q), nxc, nk4 * nxc, 1,
+                                               sm.P, nxc * di3, di3, 1, reinterpret_cast<float2*>(sm.V), nk5 * di3, di3, 1,
+                                               tid, nth);
+                    else
+                        flat_gemm<double, true>(nk4, nk5, di3, nxc, sm.Q, nxc, nk4 * nxc, 1, sm.P, nxc * di3, di3, 1,
+                                                sm.V, nk5 * di3, di3, 1, tid, nth);
                 }
                 __syncthreads();
                 // G: Y[i4][k5][i3] += sum_k4 B4'[i4][k4] V[k4][k5][i3]             (batch over k5)
                 if constexpr (MIX) {
-                    for (int q = tid; q < nk4 * nk5 * di3; q += nth) sm.Vf[q] = (float)sm.V[q];
+                    for (int q = tid; q < nk4 * nk5 * di3; q += nth) {
+                        if constexpr (FF) {
+                            const float2 vv = reinterpret_cast<const float2*>(sm.V)[q];
+                            sm.Vf[q] = vv.x + vv.y;
+                        } else {
+                            sm.Vf[q] = (float)sm.V[q];
+                        }
+                    }
                     for (int q = tid; q < di4 * nk4; q += nth) sm.B4f[q] = (float)sm.B4[q];
                     __syncthreads();
                     flat_gemm<float, true>(nk5, di4, di3, nk4, sm.B4f, 0, nk4, 1, sm.Vf, di3, nk5 * di3, 1,
@@ -428,20 +614,21 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
     }
 }
 
-template <bool MIX, int NT>
-static const void* shell_fn() { return (const void*)k_shell<MIX, NT>; }
+template <int MODE, int NT>
+static const void* shell_fn() { return (const void*)k_shell<MODE, NT>; }
 
-static const void* shell_kernel(bool mix, int nt) {
-    if (nt == 256) return mix ? shell_fn<true, 256>() : shell_fn<false, 256>();
-    return mix ? shell_fn<true, 512>() : shell_fn<false, 512>();
+static const void* shell_kernel(int mode, int nt) {
+    if (nt == 256) return mode == 2 ? shell_fn<2, 256>() : mode == 1 ? shell_fn<1, 256>() : shell_fn<0, 256>();
+    return mode == 2 ? shell_fn<2, 512>() : mode == 1 ? shell_fn<1, 512>() : shell_fn<0, 512>();
 }
 
-int sf_shell_prepare(bool mix, int nt, int mdi, int mdk, int mk3u, int xc, int Dmax, int mni3, int n_items, int num_sms,
+int sf_shell_prepare(int mode, int nt, int mdi, int mdk, int mk3u, int xc, int Dmax, int mni3, int n_items, int num_sms,
                      int* grid, size_t* smem) {
     if (nt != 256 && nt != 512) return sf_set_error(SF_ERR_ARG, "shell kernel runs 256 or 512 threads per CTA");
-    const size_t bytes = sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax, mni3, mix) * sizeof(double);
+    if (mode < 0 || mode > 2) return sf_set_error(SF_ERR_ARG, "unknown shell-kernel mode %d", mode);
+    const size_t bytes = sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax, mni3, mode) * sizeof(double);
     if (bytes > 200 * 1024) return sf_set_error(SF_ERR_LIMIT, "shell kernel needs %zu bytes of shared memory", bytes);
-    const void* fn = shell_kernel(mix, nt);
+    const void* fn = shell_kernel(mode, nt);
     SF_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     int per_sm = 0;
     SF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, bytes));
@@ -453,18 +640,21 @@ int sf_shell_prepare(bool mix, int nt, int mdi, int mdk, int mk3u, int xc, int D
     return SF_OK;
 }
 
-int sf_shell_launch_prepared(bool mix, int nt, int grid, size_t smem, const VtxDev* d_v, int mdi, int mdk, int mk3u,
+int sf_shell_launch_prepared(int mode, int nt, int grid, size_t smem, const VtxDev* d_v, int mdi, int mdk, int mk3u,
                              int xc, int Dmax, int mni3, const WorkItem* d_items, int n_items, int* d_counter,
                              double* d_part, ShellFilter filt, cudaStream_t s) {
     SF_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(int), s));
 #define SF_SHELL_GO(M, N)                                                                                     \
     k_shell<M, N><<<grid, N, smem, s>>>(d_v, mdi, mdk, mk3u, xc, Dmax, mni3, d_items, n_items, d_counter, d_part, filt)
+    if (mode < 0 || mode > 2) return sf_set_error(SF_ERR_ARG, "unknown shell-kernel mode %d", mode);
     if (nt == 256) {
-        if (mix) SF_SHELL_GO(true, 256);
-        else SF_SHELL_GO(false, 256);
+        if (mode == 2) SF_SHELL_GO(2, 256);
+        else if (mode == 1) SF_SHELL_GO(1, 256);
+        else SF_SHELL_GO(0, 256);
     } else {
-        if (mix) SF_SHELL_GO(true, 512);
-        else SF_SHELL_GO(false, 512);
+        if (mode == 2) SF_SHELL_GO(2, 512);
+        else if (mode == 1) SF_SHELL_GO(1, 512);
+        else SF_SHELL_GO(0, 512);
     }
 #undef SF_SHELL_GO
     sf_note_launch(1);
@@ -476,8 +666,8 @@ int sf_shell_fp64_launch(const VtxDev* d_v, int mdi, int mdk, int mk3u, int xc, 
                          int n_items, int* d_counter, double* d_part, ShellFilter filt, int num_sms, cudaStream_t s) {
     int grid = 0;
     size_t smem = 0;
-    SF_TRY(sf_shell_prepare(false, 512, mdi, mdk, mk3u, xc, Dmax, mdi, n_items, num_sms, &grid, &smem));
-    return sf_shell_launch_prepared(false, 512, grid, smem, d_v, mdi, mdk, mk3u, xc, Dmax, mdi, d_items, n_items,
+    SF_TRY(sf_shell_prepare(0, 512, mdi, mdk, mk3u, xc, Dmax, mdi, n_items, num_sms, &grid, &smem));
+    return sf_shell_launch_prepared(0, 512, grid, smem, d_v, mdi, mdk, mk3u, xc, Dmax, mdi, d_items, n_items,
                                     d_counter, d_part, filt, s);
 }
 

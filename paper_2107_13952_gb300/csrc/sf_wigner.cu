@@ -87,6 +87,25 @@ __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ ou
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = (float)in[i];
 }
 
+__global__ void k_to_ff(const double* __restrict__ in, float2* __restrict__ out, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double d = in[i];
+        const float hi = (float)d;
+        out[i] = make_float2(hi, (float)(d - (double)hi));
+    }
+}
+
+int sf_to_ff(const double* d_in, float2* d_out, int64_t n, int num_sms, cudaStream_t s) {
+    if (n <= 0) return SF_OK;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > (int64_t)num_sms * 16) blocks = (int64_t)num_sms * 16;
+    k_to_ff<<<(unsigned)blocks, 256, 0, s>>>(d_in, d_out, n);
+    sf_note_launch(1);
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
 int sf_to_float(const double* d_in, float* d_out, int64_t n, int num_sms, cudaStream_t s) {
     if (n <= 0) return SF_OK;
     int64_t blocks = (n + 255) / 256;

@@ -34,7 +34,7 @@ def batch(lib):
     return bt, t, bss
 
 
-@pytest.mark.parametrize("prec", [sf.SF_FP64, sf.SF_MIXED])
+@pytest.mark.parametrize("prec", [sf.SF_FP64, sf.SF_MIXED, sf.SF_MIXED_FF])
 def test_plan_run_equals_plain_call(batch, prec):
     bt, t, _ = batch
     plan = sf.Plan(t, prec, 0, SHELL_END)
@@ -102,11 +102,12 @@ def test_explicit_tilings(batch, tiling):
     plan.sync()
     for a, b in zip(outs, base):
         assert float((a - b).norm()) <= 1e-13 * max(float(b.norm()), 1e-300)
-    mixed = sf.Plan(t, sf.SF_MIXED, 0, SHELL_END, tiling=tiling)
-    outm = mixed.run()
-    mixed.sync()
-    for a, b in zip(outm, base):
-        assert float((a - b).norm()) <= 1e-6 * max(float(b.norm()), 1e-300)
+    for prec in (sf.SF_MIXED, sf.SF_MIXED_FF):
+        mixed = sf.Plan(t, prec, 0, SHELL_END, tiling=tiling)
+        outm = mixed.run()
+        mixed.sync()
+        for a, b in zip(outm, base):
+            assert float((a - b).norm()) <= 1e-6 * max(float(b.norm()), 1e-300)
 
 
 def test_batched_plan_against_oracle(batch):

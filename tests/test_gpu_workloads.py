@@ -55,13 +55,15 @@ def test_full_size_shell_subsets(lib, name):
     shells = g["shells"]
     a64 = sf.sf_vertex_amplitude(t, shell_list=shells)[0].cpu().numpy()
     amx = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED, shell_list=shells)[0].cpu().numpy()
+    aff = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED_FF, shell_list=shells)[0].cpu().numpy()
     if "idx" in g:      # large tensor: a seeded sample of entries plus the norm of the whole
-        for a, bound in ((a64, FP64_BOUND), (amx, MIXED_BOUND)):
+        for a, bound in ((a64, FP64_BOUND), (amx, MIXED_BOUND), (aff, MIXED_BOUND)):
             assert abs(np.linalg.norm(a) - float(g["A_norm"])) <= bound * float(g["A_norm"])
             assert _rel(a.reshape(-1)[g["idx"]], g["A"]) <= bound
     else:
         assert _rel(a64, g["A"]) <= FP64_BOUND
         assert _rel(amx, g["A"]) <= MIXED_BOUND
+        assert _rel(aff, g["A"]) <= MIXED_BOUND
 
 
 def test_dtable_entries_full_rule(lib):
@@ -127,6 +129,7 @@ def test_random_batch_256_against_oracle(lib, batch256):
     batch, verts, t, bss = batch256
     out64 = sf.sf_vertex_amplitude(t, shell_end=BATCH_SHELL_END)
     outmx = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED, shell_end=BATCH_SHELL_END)
+    outff = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED_FF, shell_end=BATCH_SHELL_END)
     small = [i for i, b in enumerate(batch) if b["dl"] <= 2]
     assert small
     rng = np.random.default_rng(7)
@@ -135,6 +138,7 @@ def test_random_batch_256_against_oracle(lib, batch256):
         ref = ov.vertex_amplitude(b["two_j"], b["dl"], bss[int(i)])
         assert _rel(out64[int(i)].cpu().numpy(), ref) <= FP64_BOUND
         assert _rel(outmx[int(i)].cpu().numpy(), ref) <= MIXED_BOUND
+        assert _rel(outff[int(i)].cpu().numpy(), ref) <= MIXED_BOUND
 
 
 def test_random_batch_256_against_single_launches(lib, batch256):
