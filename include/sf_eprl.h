@@ -83,8 +83,9 @@ typedef enum {
                        (hi, lo) float pairs holding about 48 significant bits, products are formed
                        exactly (Dekker) and summed with an error-compensated dot product (Ogita,
                        Rump and Oishi, "Accurate sum and dot product", 2005, Dot2), so these sums
-                       keep nearly FP64 accuracy on the FP32 pipe; the k5 contraction and every
-                       sum across (l24, l34) sets and groups in FP64                              */
+                       keep nearly FP64 accuracy on the FP32 pipe; the sums across the (l24, l34)
+                       sets of one (l25, l35, l45) group also in pairs; the k5 contraction and the
+                       sums across groups in FP64                                                 */
 } sf_precision;
 
 typedef struct sf_tables sf_tables;

@@ -52,6 +52,7 @@ struct VertexHost {
     std::vector<int32_t> klo[4];
     int32_t* d_klo[4] = {nullptr, nullptr, nullptr, nullptr};
     double* d_B[4] = {nullptr, nullptr, nullptr, nullptr};
+    float* d_Bf[4] = {nullptr, nullptr, nullptr, nullptr};
     bool boosters_ready = false;
     double2* d_dtab[10] = {nullptr};
     int32_t nl[10];
@@ -263,7 +264,12 @@ static int upload_vtxdev(sf_tables* t) {
         d.S4f = h.d_S4f;
         d.S5f = h.d_S5f;
         for (int k = 0; k < 3; k++) d.Sff[k] = h.d_Sff[k];
-        for (int e = 0; e < 4; e++) { d.B[e] = h.d_B[e]; d.klo[e] = h.d_klo[e]; d.dkmax[e] = h.dkmax[e]; }
+        for (int e = 0; e < 4; e++) {
+            d.B[e] = h.d_B[e];
+            d.Bf[e] = h.d_Bf[e];
+            d.klo[e] = h.d_klo[e];
+            d.dkmax[e] = h.dkmax[e];
+        }
         d.ntrip = h.ntrip;
         for (int f = 0; f < 10; f++) { d.dtab[f] = h.d_dtab[f]; d.nl[f] = h.nl[f]; }
     }
@@ -334,9 +340,11 @@ extern "C" int sf_6j_table(const sf_vertex* v, int32_t n, sf_tables** out, cudaS
             for (int e = 0; e < 4 && rc == SF_OK; e++) {
                 rc = dev_alloc(t, (void**)&h.d_klo[e], h.ntrip * sizeof(int32_t));
                 if (rc == SF_OK) rc = dev_alloc(t, (void**)&h.d_B[e], (size_t)h.ntrip * h.di[e + 1] * h.dkmax[e] * sizeof(double));
+                if (rc == SF_OK) rc = dev_alloc(t, (void**)&h.d_Bf[e], (size_t)h.ntrip * h.di[e + 1] * h.dkmax[e] * sizeof(float));
                 if (rc == SF_OK && cudaMemcpy(h.d_klo[e], h.klo[e].data(), h.ntrip * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
                     rc = sf_set_error(SF_ERR_CUDA, "klo upload failed");
-                if (rc == SF_OK && cudaMemsetAsync(h.d_B[e], 0, (size_t)h.ntrip * h.di[e + 1] * h.dkmax[e] * sizeof(double), stream) != cudaSuccess)
+                if (rc == SF_OK && (cudaMemsetAsync(h.d_B[e], 0, (size_t)h.ntrip * h.di[e + 1] * h.dkmax[e] * sizeof(double), stream) != cudaSuccess ||
+                                    cudaMemsetAsync(h.d_Bf[e], 0, (size_t)h.ntrip * h.di[e + 1] * h.dkmax[e] * sizeof(float), stream) != cudaSuccess))
                     rc = sf_set_error(SF_ERR_CUDA, "booster clear failed");
             }
         }
@@ -414,6 +422,7 @@ extern "C" int sf_boosters(sf_tables* t, const sf_quad_rule* q, cudaStream_t str
             size_t smem = sf_booster_smem(j[faces[e][0]], j[faces[e][1]], j[faces[e][2]], j[faces[e][3]], h.dkmax[e]);
             SF_TRY(sf_booster_build(t->d_vtx + i, e + 2, (int)h.ntrip, smem, t->d_W, nnodes, t->d_fact, t->d_Aj, t->d_Cj,
                                     h.d_B[e], t->d_status, stream));
+            SF_TRY(sf_to_float(h.d_B[e], h.d_Bf[e], (int64_t)h.ntrip * h.di[e + 1] * h.dkmax[e], t->num_sms, stream));
         }
         h.boosters_ready = true;
     }
@@ -442,6 +451,8 @@ extern "C" int sf_boosters_upload(sf_tables* t, int32_t vertex, int32_t edge, co
     VertexHost& h = t->vs[vertex];
     size_t bytes = (size_t)h.ntrip * h.di[edge - 1] * h.dkmax[edge - 2] * sizeof(double);
     SF_CUDA_TRY(cudaMemcpyAsync(h.d_B[edge - 2], B, bytes, cudaMemcpyDefault, stream));
+    SF_TRY(sf_to_float(h.d_B[edge - 2], h.d_Bf[edge - 2], (int64_t)h.ntrip * h.di[edge - 1] * h.dkmax[edge - 2], t->num_sms,
+                       stream));
     SF_CUDA_TRY(cudaStreamSynchronize(stream));
     h.boosters_ready = true;   // edges never uploaded keep their last (initially zero) contents
     return SF_OK;

@@ -280,9 +280,13 @@ __global__ void k_boundary_3j(const VtxDev* __restrict__ vp, int edge, const dd*
 //   B[i][k] = sum_m 4jm(j;m)^(i) 4jm(l;m)^(k) Re I(m),
 // and with the tuples ordered so that m -> -m reverses the flat index, only the upper half is
 // summed (weight 2, the self-conjugate tuple m = 0 weight 1). The node sum is factored through
-// pair products P12 = W d1 d2 and P34 = d3 d4 staged per chunk of nodes.
-#define SF_BT 12   // canonical tuples per thread (upper half of at most 17^3 tuples / 256 threads)
-__global__ void __launch_bounds__(256) k_booster(const VtxDev* __restrict__ vp, int edge, const double* __restrict__ Wm,
+// pair products P12 = W d1 d2 and P34 = d3 d4 staged per chunk of nodes. The same reflection
+// gives P12(-m1, -m2) = s12 conj(P12(m1, m2)) with s12 = (-1)^((k1 - l1) + (k2 - l2)) (likewise
+// P34), so only the upper half of each pair table is staged; a tuple whose pair lies in the
+// lower half reads its mirror, and Re(conj(a) b) = a.x b.x + a.y b.y flips one sign.
+#define SF_BT 6         // canonical tuples per thread (upper half of at most 17^3 tuples / 512 threads)
+#define SF_BOOST_NT 512
+__global__ void __launch_bounds__(SF_BOOST_NT) k_booster(const VtxDev* __restrict__ vp, int edge, const double* __restrict__ Wm,
                                                  int nnodes, const dd* __restrict__ F, const double* __restrict__ gAj,
                                                  const double* __restrict__ gCj, double* __restrict__ Bout, int* status) {
     extern __shared__ __align__(16) double sm[];
@@ -309,11 +313,16 @@ __global__ void __launch_bounds__(256) k_booster(const VtxDev* __restrict__ vp, 
     const int n1 = tj[0] + 1, n2 = tj[1] + 1, n3 = tj[2] + 1, n4 = tj[3] + 1;
     const int M = n1 * n2 * n3;
     const int Mh = M / 2;   // canonical tuples: [Mh, M); Mh itself is m = 0 when M is odd
-    // shared: Ir[M] | union { P12[n1 n2][SF_NC], P34[n3 n4][SF_NC] (complex) ; Al[nk][n1 n2], Cl[nk][n3 n4] }
+    // pair tables: flat pair index f = ia * nb + ib; -m maps f to N - 1 - f; staged f >= N / 2
+    const int N12 = n1 * n2, N34 = n3 * n4, h12 = N12 / 2, h34 = N34 / 2;
+    const int C12 = N12 - h12, C34 = N34 - h34;
+    const double sg12 = ((((tl[0] - tj[0]) + (tl[1] - tj[1])) / 2) & 1) ? -1.0 : 1.0;
+    const double sg34 = ((((tl[2] - tj[2]) + (tl[3] - tj[3])) / 2) & 1) ? -1.0 : 1.0;
+    // shared: Ir[M] | union { P12[C12][SF_NC], P34[C34][SF_NC] (complex) ; Al[nk][n1 n2], Cl[nk][n3 n4] }
     double* sIr = sm;
     const int Mpad = (M + 1) & ~1;   // keep the complex staging area 16-byte aligned
     double2* P12 = reinterpret_cast<double2*>(sm + Mpad);
-    double2* P34 = P12 + n1 * n2 * SF_NC;
+    double2* P34 = P12 + C12 * SF_NC;
     double* sAl = sm + Mpad;
     double* sCl = sAl + nk * n1 * n2;
     const double2* d0 = v.dtab[fc[0]] + (int64_t)il[0] * n1 * nnodes;
@@ -326,8 +335,8 @@ __global__ void __launch_bounds__(256) k_booster(const VtxDev* __restrict__ vp, 
     for (int n0 = 0; n0 < nnodes; n0 += SF_NC) {
         const int nc = imin_(SF_NC, nnodes - n0);
         __syncthreads();
-        for (int q = threadIdx.x; q < n1 * n2 * SF_NC; q += blockDim.x) {
-            const int nn = q % SF_NC, pr = q / SF_NC, a2 = pr % n2, a1 = pr / n2;
+        for (int q = threadIdx.x; q < C12 * SF_NC; q += blockDim.x) {
+            const int nn = q % SF_NC, pr = h12 + q / SF_NC, a2 = pr % n2, a1 = pr / n2;
             double2 z = make_double2(0.0, 0.0);
             if (nn < nc) {
                 const double2 x = d0[(int64_t)a1 * nnodes + n0 + nn], y = d1[(int64_t)a2 * nnodes + n0 + nn];
@@ -336,8 +345,8 @@ __global__ void __launch_bounds__(256) k_booster(const VtxDev* __restrict__ vp, 
             }
             P12[q] = z;
         }
-        for (int q = threadIdx.x; q < n3 * n4 * SF_NC; q += blockDim.x) {
-            const int nn = q % SF_NC, pr = q / SF_NC, a4 = pr % n4, a3 = pr / n4;
+        for (int q = threadIdx.x; q < C34 * SF_NC; q += blockDim.x) {
+            const int nn = q % SF_NC, pr = h34 + q / SF_NC, a4 = pr % n4, a3 = pr / n4;
             double2 z = make_double2(0.0, 0.0);
             if (nn < nc) {
                 const double2 x = d2[(int64_t)a3 * nnodes + n0 + nn], y = d3[(int64_t)a4 * nnodes + n0 + nn];
@@ -354,15 +363,20 @@ __global__ void __launch_bounds__(256) k_booster(const VtxDev* __restrict__ vp, 
                 const int tm4 = -((-tj[0] + 2 * i1) + (-tj[1] + 2 * i2) + (-tj[2] + 2 * i3));
                 if (iabs_(tm4) <= tj[3]) {
                     const int i4 = (tm4 + tj[3]) / 2;
-                    const double2* p = P12 + (i1 * n2 + i2) * SF_NC;
-                    const double2* r = P34 + (i3 * n4 + i4) * SF_NC;
-                    double s0 = acc[q], s1 = 0.0;
+                    const int f12 = i1 * n2 + i2, f34 = i3 * n4 + i4;
+                    const bool c12 = f12 < h12, c34 = f34 < h34;   // mirrored (conjugated) pairs
+                    const double2* p = P12 + ((c12 ? N12 - 1 - f12 : f12) - h12) * SF_NC;
+                    const double2* r = P34 + ((c34 ? N34 - 1 - f34 : f34) - h34) * SF_NC;
+                    double s0 = 0.0, s1 = 0.0;
                     for (int nn = 0; nn < nc; nn++) {
                         const double2 a = p[nn], b = r[nn];
                         s0 = fma(a.x, b.x, s0);
                         s1 = fma(a.y, b.y, s1);
                     }
-                    acc[q] = s0 - s1;
+                    // Re of the product: s0 - s1, or s0 + s1 with exactly one factor conjugated
+                    const double re = (c12 != c34) ? s0 + s1 : s0 - s1;
+                    const double sg = (c12 ? sg12 : 1.0) * (c34 ? sg34 : 1.0);
+                    acc[q] = fma(sg, re, acc[q]);
                 }
             }
         }
@@ -418,7 +432,8 @@ __global__ void __launch_bounds__(256) k_booster(const VtxDev* __restrict__ vp, 
 size_t sf_booster_smem(int tj1, int tj2, int tj3, int tj4, int nk) {
     int n1 = tj1 + 1, n2 = tj2 + 1, n3 = tj3 + 1, n4 = tj4 + 1;
     size_t M = ((size_t)n1 * n2 * n3 + 1) & ~(size_t)1;
-    size_t stage = (size_t)(n1 * n2 + n3 * n4) * SF_NC * sizeof(double2);
+    const int c12 = n1 * n2 - (n1 * n2) / 2, c34 = n3 * n4 - (n3 * n4) / 2;
+    size_t stage = (size_t)(c12 + c34) * SF_NC * sizeof(double2);
     size_t tabs = sizeof(double) * ((size_t)nk * n1 * n2 + (size_t)nk * n3 * n4);
     return M * sizeof(double) + (stage > tabs ? stage : tabs);
 }
@@ -430,7 +445,7 @@ int sf_booster_build(const VtxDev* d_v, int edge, int ntrip, size_t smem, const 
     sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     SF_CUDA_TRY(cudaFuncSetAttribute(k_booster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_booster<<<ntrip, 256, smem, s>>>(d_v, edge, d_W, nnodes, F, d_Aj, d_Cj, d_B, d_status);
+    k_booster<<<ntrip, SF_BOOST_NT, smem, s>>>(d_v, edge, d_W, nnodes, F, d_Aj, d_Cj, d_B, d_status);
     sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;

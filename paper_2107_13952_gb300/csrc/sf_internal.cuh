@@ -226,6 +226,7 @@ struct VtxDev {
     const float2* Sff[3];      // S1, S2, S3 as (hi, lo) float pairs, hi + lo = S to about 2^-48 (SF_MIXED_FF)
     const SlotDesc* slot[5];
     const double* B[4];        // boosters of edges 2..5: [t][i][k - klo(t)], padded to dkmax
+    const float* Bf[4];        // the same boosters rounded to FP32 (SF_MIXED_FF)
     const int32_t* klo[4];
     int32_t dkmax[4];
     int64_t ntrip;             // D^3

@@ -20,6 +20,7 @@
 // by the reduction. Each CTA owns whole work items (tile, range of groups), so the partial sums
 // and their fixed-order reduction are deterministic.
 #include "sf_internal.cuh"
+#include <type_traits>
 
 // {6j} table read with box and parity checks (zero outside: the symbol vanishes there)
 __device__ __forceinline__ double s6(const double* __restrict__ S, const SlotDesc& sd, int a, int b, int x) {
@@ -151,51 +152,94 @@ __device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
     return make_float2(h, l);
 }
 
-// C[bt][m][n] (+)= sum_k A[bt][m][k] B[bt][k][n] with pair operands A, pair or float operands B
-// and Dot2 accumulation (k in increasing order). Each thread computes RM rows m of one column n;
-// consecutive threads take consecutive n, so B loads are contiguous and A loads are broadcasts.
-template <int RM, bool BPAIR, bool ACC>
-__device__ __forceinline__ void ff_gemm(int nbatch, int M, int N, int K, const float2* A, int a_bs, int am, int ak,
-                                        const void* Bv, int b_bs, int bk, int bn, float2* C, int c_bs, int cm, int cn,
-                                        int tid, int nth) {
-    const int MB = (M + RM - 1) / RM, L = nbatch * MB * N;
-    for (int o = tid; o < L; o += nth) {
-        const int n = o % N, r = o / N, mb = r % MB, bt = r / MB;
-        const float2* ap[RM];
+// floor(o / d) for 0 <= o < 2^31, 1 <= d: multiply by m = floor((2^32 - 1) / d), which
+// underestimates by at most one, then correct once
+struct FDiv { unsigned m; int d; };
+__device__ __forceinline__ FDiv fdiv_make(int d) { return FDiv{0xFFFFFFFFu / (unsigned)d, d}; }
+__device__ __forceinline__ int fdiv_q(int o, FDiv f) {
+    int q = (int)__umulhi((unsigned)o, f.m);
+    if (o - q * f.d >= f.d) q++;
+    return q;
+}
+
+// Staging loop over q in [0, L) with U elements per thread in flight: all U loads of a round are
+// issued before any result is stored, so a thread waits for one L2 round trip per round instead
+// of one per element. ld(q) gathers an element, st(q, value) stores it.
+template <int U, typename LoadF, typename StoreF>
+__device__ __forceinline__ void gather_loop(int L, int tid, int nth, LoadF ld, StoreF st) {
+    for (int q0 = tid; q0 < L; q0 += U * nth) {
+        decltype(ld(0)) val[U];
 #pragma unroll
-        for (int i = 0; i < RM; i++) {
-            const int m = imin_(mb * RM + i, M - 1);
-            ap[i] = A + bt * a_bs + m * am;
+        for (int u = 0; u < U; u++) {
+            const int q = q0 + u * nth;
+            if (q < L) val[u] = ld(q);
         }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int q = q0 + u * nth;
+            if (q < L) st(q, val[u]);
+        }
+    }
+}
+
+// Small batched GEMMs of the mixed paths, C[bt][m][n] (+)= sum_k A[bt][m][k] B[bt][k][n] with A
+// contiguous in k and B, C contiguous in n. Each thread computes RM rows of one column n;
+// consecutive threads take consecutive n, so B loads are contiguous and A loads are broadcasts;
+// every output sums over k in increasing order. KIND selects the arithmetic:
+//   GEMM_FF_D: A (hi, lo) pairs, B floats, Dot2 accumulation, C = the normalised pair;
+//   GEMM_FF_F: A and B pairs, Dot2 accumulation, C += the pair (pair addition);
+//   GEMM_F32:  A and B floats, FP32 FMA accumulation, C (double) += the float result.
+//   GEMM_F32_FF: as GEMM_F32, with C a pair (C += the float result, pair addition).
+enum { GEMM_FF_D = 0, GEMM_FF_F = 1, GEMM_F32 = 2, GEMM_F32_FF = 3 };
+template <int KIND, int RM>
+__device__ __forceinline__ void rows_gemm(int nbatch, int M, int N, int K, const void* Av, int a_bs, int am,
+                                          const void* Bv, int b_bs, int bk, void* Cv, int c_bs, int cm, int tid,
+                                          int nth) {
+    constexpr bool F32 = KIND == GEMM_F32 || KIND == GEMM_F32_FF;
+    using TA = typename std::conditional<F32, float, float2>::type;
+    using TB = typename std::conditional<KIND == GEMM_FF_F, float2, float>::type;
+    const TA* A = reinterpret_cast<const TA*>(Av);
+    const TB* B = reinterpret_cast<const TB*>(Bv);
+    const int MB = (M + RM - 1) / RM, L = nbatch * MB * N;
+    const FDiv dN = fdiv_make(N), dMB = fdiv_make(MB);
+    for (int o = tid; o < L; o += nth) {
+        const int r = fdiv_q(o, dN), n = o - r * N;
+        const int bt = fdiv_q(r, dMB), mb = r - bt * MB;
+        const TA* ap[RM];
+#pragma unroll
+        for (int i = 0; i < RM; i++) ap[i] = A + bt * a_bs + imin_(mb * RM + i, M - 1) * am;
+        const TB* bp = B + bt * b_bs + n;
         float sh[RM], sl[RM];
 #pragma unroll
         for (int i = 0; i < RM; i++) { sh[i] = 0.0f; sl[i] = 0.0f; }
-        const int boff = bt * b_bs + n * bn;
+#pragma unroll 4
         for (int k = 0; k < K; k++) {
-            if constexpr (BPAIR) {
-                const float2 b = reinterpret_cast<const float2*>(Bv)[boff + k * bk];
+            const TB b = *bp;
+            bp += bk;
 #pragma unroll
-                for (int i = 0; i < RM; i++) {
-                    const float2 a = ap[i][k * ak];
-                    ff_dot_step2(a.x, a.y, b.x, b.y, sh[i], sl[i]);
-                }
-            } else {
-                const float b = reinterpret_cast<const float*>(Bv)[boff + k * bk];
-#pragma unroll
-                for (int i = 0; i < RM; i++) {
-                    const float2 a = ap[i][k * ak];
-                    ff_dot_step(a.x, a.y, b, sh[i], sl[i]);
-                }
+            for (int i = 0; i < RM; i++) {
+                const TA a = ap[i][k];
+                if constexpr (F32) sh[i] = fmaf(a, b, sh[i]);
+                else if constexpr (KIND == GEMM_FF_D) ff_dot_step(a.x, a.y, b, sh[i], sl[i]);
+                else ff_dot_step2(a.x, a.y, b.x, b.y, sh[i], sl[i]);
             }
         }
 #pragma unroll
         for (int i = 0; i < RM; i++) {
             const int m = mb * RM + i;
             if (m < M) {
-                float2* cp = C + bt * c_bs + m * cm + n * cn;
-                const float2 v = ff_norm(sh[i], sl[i]);
-                if (ACC) *cp = ff_add(*cp, v);
-                else *cp = v;
+                const int co = bt * c_bs + m * cm + n;
+                if constexpr (KIND == GEMM_F32) {
+                    reinterpret_cast<double*>(Cv)[co] += (double)sh[i];
+                } else if constexpr (KIND == GEMM_F32_FF) {
+                    float2* cp = reinterpret_cast<float2*>(Cv) + co;
+                    *cp = ff_add(*cp, make_float2(sh[i], 0.0f));
+                } else {
+                    float2* cp = reinterpret_cast<float2*>(Cv) + co;
+                    const float2 v = ff_norm(sh[i], sl[i]);
+                    if constexpr (KIND == GEMM_FF_F) *cp = ff_add(*cp, v);
+                    else *cp = v;
+                }
             }
         }
     }
@@ -271,7 +315,8 @@ size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, int mni3
 // x-sum with S1 S2), every sum across 5-tuples and groups, and the k5 contraction stay FP64.
 // MODE 2: as MODE 1, but the {6j} contractions (phases D and F, and the products Q) run on
 // compensated FP32 pairs with Dot2 accumulation, from (hi, lo) copies of S1, S2, S3; V is kept as
-// a pair across the x chunks of a 5-tuple. GB300's FP64 pipe issues 2 FMAs per clock per SM
+// a pair across the x chunks of a 5-tuple and Y across the 5-tuples of a group (converted to FP64
+// for the k5 contraction); the booster operands come from FP32 copies of the boosters. GB300's FP64 pipe issues 2 FMAs per clock per SM
 // against 128 FP32 FMAs, so a pair step of about 11 FP32 instructions is several times cheaper.
 // NT threads per CTA: 512 (one CTA per SM) or 256 (two CTAs per SM, whose phases interleave).
 // A work item covers the i3 sub-range [i3b, i3b + ni3) of its output tile.
@@ -282,12 +327,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                                                         ShellFilter filt) {
     constexpr bool MIX = MODE >= 1;
     constexpr bool FF = MODE == 2;
+    constexpr int GU = FF ? 4 : 2;   // staging elements in flight per thread (FP64 values: register budget)
     extern __shared__ double smem[];
     __shared__ int s_item;
     __shared__ int s_k2lo[SF_MAX_DL + 1], s_nk2[SF_MAX_DL + 1], s_k3lo[SF_MAX_DL + 1], s_nk3[SF_MAX_DL + 1];
     __shared__ double s_sig[SF_MAX_DL + 1];
     __shared__ float s_sigf[SF_MAX_DL + 1];
     __shared__ SlotDesc s_sd4[SF_MAX_DL + 1];
+    __shared__ SlotDesc s_sdx[4];   // slots of S1, S5, S2 (per group) and S3 (per 5-tuple), read in place
     const ShellSmem sm = carve(smem, mdi, mdk, mk3u, XC, Dmax, mni3);
     const int tid = threadIdx.x, nth = NT;
     for (;;) {
@@ -331,9 +378,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                 }
             }
             for (int q = tid; q < di4 * nk5 * di3; q += nth) sm.Y[q] = 0.0;
-            const SlotDesc sd1 = load_slot(v.slot[0] + d25);
-            const SlotDesc sd5 = load_slot(v.slot[4] + d25);
-            const SlotDesc sd2 = load_slot(v.slot[1] + d35 * D + d45);
+            if (tid == 0) {
+                s_sdx[0] = load_slot(v.slot[0] + d25);
+                s_sdx[1] = load_slot(v.slot[4] + d25);
+                s_sdx[2] = load_slot(v.slot[1] + d35 * D + d45);
+            }
+            const SlotDesc& sd1 = s_sdx[0];
+            const SlotDesc& sd5 = s_sdx[1];
+            const SlotDesc& sd2 = s_sdx[2];
             const int k5hi = k5lo + 2 * (nk5 - 1);
             const int x_lo_a = iabs_(i1 - l25), x_hi_a = i1 + l25;
             const int x_lo_b = (j14 < k5lo) ? (k5lo - j14) : (j14 > k5hi ? j14 - k5hi : ((j14 + k5lo) & 1));
@@ -385,8 +437,16 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                     s_sd4[d] = load_slot(v.slot[3] + d * D + d24);
                 }
                 const int nk3u = (k3uhi - k3ulo) / 2 + 1;
+                const FDiv f_nk3u = fdiv_make(nk3u), f_di3 = fdiv_make(di3), f_mdk5 = fdiv_make(mdk);
                 const int t4 = (d45 * D + d24) * D + d34;
-                {
+                if constexpr (FF) {
+                    const float* B4 = v.Bf[2] + (int64_t)t4 * di4 * v.dkmax[2];
+                    for (int q = tid; q < di4 * nk4; q += nth) {
+                        const int i4 = q / nk4, c4 = q % nk4;
+                        const float f = (float)(k4lo + 2 * c4 + 1) * ((c4 & 1) ? -1.0f : 1.0f);
+                        sm.B4f[q] = f * B4[i4 * v.dkmax[2] + c4];
+                    }
+                } else {
                     const double* B4 = v.B[2] + (int64_t)t4 * di4 * v.dkmax[2];
                     for (int q = tid; q < di4 * nk4; q += nth) {
                         const int i4 = q / nk4, c4 = q % nk4;
@@ -394,57 +454,127 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                         sm.B4[q] = f * B4[i4 * v.dkmax[2] + c4];
                     }
                 }
-                // raw B3 rows of every l23, transposed to [d][c3][i3]
-                for (int q = tid; q < D * mdk * di3; q += nth) {
-                    const int i3 = q % di3, r = q / di3, c3 = r % mdk, d = r / mdk;
-                    const int t3 = (d34 * D + d35) * D + d;
-                    const double b3 = (c3 < dk1) ? __ldg(v.B[1] + ((int64_t)t3 * di3f + i3b + i3) * dk1 + c3) : 0.0;
-                    if constexpr (MIX) reinterpret_cast<float*>(sm.B3s)[q] = (float)b3;
-                    else sm.B3s[q] = b3;
+                // raw B3 rows of every l23, transposed to [d][c3][i3] (read along c3: coalesced)
+                {
+                    const int t30 = (d34 * D + d35) * D;
+                    auto b3_at = [&](int q, int& d, int& i3, int& c3) {
+                        const int r = fdiv_q(q, f_mdk5);
+                        c3 = q - r * mdk;
+                        d = fdiv_q(r, f_di3);
+                        i3 = r - d * di3;
+                    };
+                    if constexpr (FF) {
+                        gather_loop<4>(D * mdk * di3, tid, nth, [&](int q) {
+                            int d, i3, c3;
+                            b3_at(q, d, i3, c3);
+                            return (c3 < dk1) ? __ldg(v.Bf[1] + ((int64_t)(t30 + d) * di3f + i3b + i3) * dk1 + c3) : 0.0f;
+                        }, [&](int q, float val) {
+                            int d, i3, c3;
+                            b3_at(q, d, i3, c3);
+                            reinterpret_cast<float*>(sm.B3s)[(d * mdk + c3) * di3 + i3] = val;
+                        });
+                    } else {
+                        gather_loop<4>(D * mdk * di3, tid, nth, [&](int q) {
+                            int d, i3, c3;
+                            b3_at(q, d, i3, c3);
+                            return (c3 < dk1) ? __ldg(v.B[1] + ((int64_t)(t30 + d) * di3f + i3b + i3) * dk1 + c3) : 0.0;
+                        }, [&](int q, double val) {
+                            int d, i3, c3;
+                            b3_at(q, d, i3, c3);
+                            if constexpr (MIX) reinterpret_cast<float*>(sm.B3s)[(d * mdk + c3) * di3 + i3] = (float)val;
+                            else sm.B3s[(d * mdk + c3) * di3 + i3] = val;
+                        });
+                    }
                 }
                 for (int q = tid; q < nk4 * nk5 * di3; q += nth) sm.V[q] = 0.0;
-                const SlotDesc sd3 = load_slot(v.slot[2] + (d24 * D + d34) * D + d35);
+                if (tid == 0) s_sdx[3] = load_slot(v.slot[2] + (d24 * D + d34) * D + d35);
+                const SlotDesc& sd3 = s_sdx[3];
                 for (int xc0 = xlo; xc0 <= xhi; xc0 += 2 * XC) {
                     const int nxc = imin_(XC, (xhi - xc0) / 2 + 1);
                     __syncthreads();
                     // A: SB[d][k2][x] = sigma_d (2k2+1)(-1)^(k2-k2lo) B2[t2][i2][k2] S5[k2,i1,x];
                     //    S3s[x][k4][k3u] staged from the S3 slot (zero outside its box)
-                    for (int q = tid; q < D * mdk * nxc; q += nth) {
-                        const int xc = q % nxc, r = q / nxc, c2 = r % mdk, d = r / mdk;
-                        if (c2 >= s_nk2[d]) continue;
-                        const int k2 = s_k2lo[d] + 2 * c2, x = xc0 + 2 * xc;
-                        const int t2 = (d * D + d24) * D + d25;
-                        const double b2 = __ldg(v.B[0] + ((int64_t)t2 * v.di[1] + ci2) * v.dkmax[0] + c2);
-                        if constexpr (FF) {
-                            const float f = (float)(k2 + 1) * ((c2 & 1) ? -s_sigf[d] : s_sigf[d]);
-                            reinterpret_cast<float*>(sm.SB)[(d * mdk + c2) * XC + xc] =
-                                (f * (float)b2) * s6f(v.S5f, sd5, k2, i1, x);
-                        } else {
-                            const double f = (double)(k2 + 1) * ((c2 & 1) ? -s_sig[d] : s_sig[d]);
-                            const double sb = f * b2 * s6(v.S[4], sd5, k2, i1, x);
-                            if constexpr (MIX) reinterpret_cast<float*>(sm.SB)[(d * mdk + c2) * XC + xc] = (float)sb;
-                            else sm.SB[(d * mdk + c2) * XC + xc] = sb;
-                        }
+                    const FDiv f_nxc = fdiv_make(nxc), f_mdk = fdiv_make(mdk), f_nk4 = fdiv_make(nk4);
+                    {
+                        // SB: gather (B2 entry, S5 entry) pairs, then scale and store
+                        auto sb_at = [&](int q, int& d, int& c2, int& xc) {
+                            const int r = fdiv_q(q, f_nxc);
+                            xc = q - r * nxc;
+                            d = fdiv_q(r, f_mdk);
+                            c2 = r - d * mdk;
+                        };
+                        using T2 = typename std::conditional<FF, float2, double2>::type;
+                        gather_loop<GU>(D * mdk * nxc, tid, nth, [&](int q) {
+                            int d, c2, xc;
+                            sb_at(q, d, c2, xc);
+                            T2 val;
+                            val.x = 0; val.y = 0;
+                            if (c2 < s_nk2[d]) {
+                                const int k2 = s_k2lo[d] + 2 * c2, x = xc0 + 2 * xc;
+                                const int64_t bi = ((int64_t)((d * D + d24) * D + d25) * v.di[1] + ci2) * v.dkmax[0] + c2;
+                                if constexpr (FF) {
+                                    val.x = __ldg(v.Bf[0] + bi);
+                                    val.y = s6f(v.S5f, sd5, k2, i1, x);
+                                } else {
+                                    val.x = __ldg(v.B[0] + bi);
+                                    val.y = s6(v.S[4], sd5, k2, i1, x);
+                                }
+                            }
+                            return val;
+                        }, [&](int q, T2 val) {
+                            int d, c2, xc;
+                            sb_at(q, d, c2, xc);
+                            if (c2 >= s_nk2[d]) return;
+                            const int k2 = s_k2lo[d] + 2 * c2;
+                            if constexpr (FF) {
+                                const float f = (float)(k2 + 1) * ((c2 & 1) ? -s_sigf[d] : s_sigf[d]);
+                                reinterpret_cast<float*>(sm.SB)[(d * mdk + c2) * XC + xc] = (f * val.x) * val.y;
+                            } else {
+                                const double f = (double)(k2 + 1) * ((c2 & 1) ? -s_sig[d] : s_sig[d]);
+                                const double sb = f * val.x * val.y;
+                                if constexpr (MIX) reinterpret_cast<float*>(sm.SB)[(d * mdk + c2) * XC + xc] = (float)sb;
+                                else sm.SB[(d * mdk + c2) * XC + xc] = sb;
+                            }
+                        });
                     }
-                    for (int q = tid; q < nxc * nk4 * nk3u; q += nth) {
-                        const int ku = q % nk3u, r = q / nk3u, c4 = r % nk4, xc = r / nk4;
-                        if constexpr (FF)
-                            reinterpret_cast<float2*>(sm.S3s)[q] = s6ff(v.Sff[2], sd3, k4lo + 2 * c4, k3ulo + 2 * ku, xc0 + 2 * xc);
-                        else sm.S3s[q] = s6(v.S[2], sd3, k4lo + 2 * c4, k3ulo + 2 * ku, xc0 + 2 * xc);
+                    // S3s[x][k4][k3u] from the S3 slot
+                    if constexpr (FF) {
+                        gather_loop<4>(nxc * nk4 * nk3u, tid, nth, [&](int q) {
+                            const int r = fdiv_q(q, f_nk3u), ku = q - r * nk3u, xc = fdiv_q(r, f_nk4), c4 = r - xc * nk4;
+                            return s6ff(v.Sff[2], sd3, k4lo + 2 * c4, k3ulo + 2 * ku, xc0 + 2 * xc);
+                        }, [&](int q, float2 val) { reinterpret_cast<float2*>(sm.S3s)[q] = val; });
+                    } else {
+                        gather_loop<GU>(nxc * nk4 * nk3u, tid, nth, [&](int q) {
+                            const int r = fdiv_q(q, f_nk3u), ku = q - r * nk3u, xc = fdiv_q(r, f_nk4), c4 = r - xc * nk4;
+                            return s6(v.S[2], sd3, k4lo + 2 * c4, k3ulo + 2 * ku, xc0 + 2 * xc);
+                        }, [&](int q, double val) { sm.S3s[q] = val; });
                     }
                     // E: Q[k5][k4][x] = (2x+1) S1[i1,k5,x] S2[k5,k4,x]
-                    for (int q = tid; q < nk5 * nk4 * nxc; q += nth) {
-                        const int xc = q % nxc, r = q / nxc, c4 = r % nk4, c5 = r / nk4;
-                        const int k5 = k5lo + 2 * c5, k4 = k4lo + 2 * c4, x = xc0 + 2 * xc;
-                        if constexpr (FF)
+                    if constexpr (FF) {
+                        gather_loop<4>(nk5 * nk4 * nxc, tid, nth, [&](int q) {
+                            const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, c5 = fdiv_q(r, f_nk4), c4 = r - c5 * nk4;
+                            const int k5 = k5lo + 2 * c5, k4 = k4lo + 2 * c4, x = xc0 + 2 * xc;
+                            const float2 a = s6ff(v.Sff[0], sd1, i1, k5, x), b = s6ff(v.Sff[1], sd2, k5, k4, x);
+                            return make_float4(a.x, a.y, b.x, b.y);
+                        }, [&](int q, float4 val) {
+                            const int x = xc0 + 2 * (q - fdiv_q(q, f_nxc) * nxc);
                             reinterpret_cast<float2*>(sm.Q)[q] =
-                                ff_mul_f(ff_mul(s6ff(v.Sff[0], sd1, i1, k5, x), s6ff(v.Sff[1], sd2, k5, k4, x)), (float)(x + 1));
-                        else sm.Q[q] = (double)(x + 1) * s6(v.S[0], sd1, i1, k5, x) * s6(v.S[1], sd2, k5, k4, x);
+                                ff_mul_f(ff_mul(make_float2(val.x, val.y), make_float2(val.z, val.w)), (float)(x + 1));
+                        });
+                    } else {
+                        gather_loop<GU>(nk5 * nk4 * nxc, tid, nth, [&](int q) {
+                            const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, c5 = fdiv_q(r, f_nk4), c4 = r - c5 * nk4;
+                            const int k5 = k5lo + 2 * c5, k4 = k4lo + 2 * c4, x = xc0 + 2 * xc;
+                            return make_double2(s6(v.S[0], sd1, i1, k5, x), s6(v.S[1], sd2, k5, k4, x));
+                        }, [&](int q, double2 val) {
+                            const int x = xc0 + 2 * (q - fdiv_q(q, f_nxc) * nxc);
+                            sm.Q[q] = (double)(x + 1) * val.x * val.y;
+                        });
                     }
                     __syncthreads();
                     // B: R[d][k3][x] = (2k3+1)(-1)^(k3-k3lo) sum_k2 S4_d[k3,k2,x] SB[d][k2][x]
                     for (int q = tid; q < D * mdk * nxc; q += nth) {
-                        const int xc = q % nxc, r = q / nxc, c3 = r % mdk, d = r / mdk;
+                        const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, d = fdiv_q(r, f_mdk), c3 = r - d * mdk;
                         const int nk3 = s_nk3[d];
                         if (c3 >= nk3) continue;
                         const int k3 = s_k3lo[d] + 2 * c3, x = xc0 + 2 * xc;
@@ -459,16 +589,21 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                             const float* sbp = reinterpret_cast<const float*>(sm.SB) + (d * mdk) * XC + xc;
                             // the FP32 copy of S4 holds the same roundings as converting each entry here
                             const float* s4f = v.S4f + sd4.off + ((int64_t)ia * sd4.nb + ib0) * sd4.nx + ix;
-                            float acc0 = 0.0f, acc1 = 0.0f;
+                            float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f, acc3 = 0.0f;
                             if (inbox) {
+                                const int nx = sd4.nx;
                                 int c2 = 0;
-                                for (; c2 + 1 < nk2; c2 += 2) {
-                                    acc0 = fmaf(__ldg(s4f + (int64_t)c2 * sd4.nx), sbp[c2 * XC], acc0);
-                                    acc1 = fmaf(__ldg(s4f + (int64_t)(c2 + 1) * sd4.nx), sbp[(c2 + 1) * XC], acc1);
+                                for (; c2 + 3 < nk2; c2 += 4) {   // four loads in flight
+                                    const float s0 = __ldg(s4f + c2 * nx), s1 = __ldg(s4f + (c2 + 1) * nx);
+                                    const float s2 = __ldg(s4f + (c2 + 2) * nx), s3 = __ldg(s4f + (c2 + 3) * nx);
+                                    acc0 = fmaf(s0, sbp[c2 * XC], acc0);
+                                    acc1 = fmaf(s1, sbp[(c2 + 1) * XC], acc1);
+                                    acc2 = fmaf(s2, sbp[(c2 + 2) * XC], acc2);
+                                    acc3 = fmaf(s3, sbp[(c2 + 3) * XC], acc3);
                                 }
-                                if (c2 < nk2) acc0 = fmaf(__ldg(s4f + (int64_t)c2 * sd4.nx), sbp[c2 * XC], acc0);
+                                for (; c2 < nk2; c2++) acc0 = fmaf(__ldg(s4f + c2 * nx), sbp[c2 * XC], acc0);
                             }
-                            reinterpret_cast<float*>(sm.R)[(d * mdk + c3) * XC + xc] = (acc0 + acc1) * (float)sgn3;
+                            reinterpret_cast<float*>(sm.R)[(d * mdk + c3) * XC + xc] = ((acc0 + acc1) + (acc2 + acc3)) * (float)sgn3;
                         } else {
                             const double* sbp = sm.SB + (d * mdk) * XC + xc;
                             double acc0 = 0.0, acc1 = 0.0;
@@ -487,8 +622,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                     // C: U[k3u][x][i3] = sum_d R[d][k3][x] B3_d[i3][k3]   (4 consecutive i3 per thread)
                     {
                         const int nb3 = (di3 + 3) / 4;
+                        const FDiv f_nb3 = fdiv_make(nb3);
                         for (int q = tid; q < nk3u * nxc * nb3; q += nth) {
-                            const int b = q % nb3, r = q / nb3, xc = r % nxc, ku = r / nxc;
+                            const int r = fdiv_q(q, f_nb3), b = q - r * nb3, ku = fdiv_q(r, f_nxc), xc = r - ku * nxc;
                             const int i30 = 4 * b;
                             const int k3 = k3ulo + 2 * ku;
                             double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
@@ -506,6 +642,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                                     if (i30 + 2 < di3) f2 = fmaf(rr, bp[2], f2);
                                     if (i30 + 3 < di3) f3 = fmaf(rr, bp[3], f3);
                                 }
+                                if constexpr (FF) {
+                                    float* up = reinterpret_cast<float*>(sm.U) + (ku * nxc + xc) * di3 + i30;
+                                    up[0] = f0;
+                                    if (i30 + 1 < di3) up[1] = f1;
+                                    if (i30 + 2 < di3) up[2] = f2;
+                                    if (i30 + 3 < di3) up[3] = f3;
+                                    continue;
+                                }
                                 a0 = f0; a1 = f1; a2 = f2; a3 = f3;
                             } else {
                                 for (int d = 0; d < D; d++) {
@@ -519,36 +663,26 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                                     if (i30 + 3 < di3) a3 = fma(rr, bp[3], a3);
                                 }
                             }
-                            if constexpr (FF) {
-                                float* up = reinterpret_cast<float*>(sm.U) + (ku * nxc + xc) * di3 + i30;
-                                up[0] = (float)a0;
-                                if (i30 + 1 < di3) up[1] = (float)a1;
-                                if (i30 + 2 < di3) up[2] = (float)a2;
-                                if (i30 + 3 < di3) up[3] = (float)a3;
-                            } else {
-                                double* up = sm.U + (ku * nxc + xc) * di3 + i30;
-                                up[0] = a0;
-                                if (i30 + 1 < di3) up[1] = a1;
-                                if (i30 + 2 < di3) up[2] = a2;
-                                if (i30 + 3 < di3) up[3] = a3;
-                            }
+                            double* up = sm.U + (ku * nxc + xc) * di3 + i30;
+                            up[0] = a0;
+                            if (i30 + 1 < di3) up[1] = a1;
+                            if (i30 + 2 < di3) up[2] = a2;
+                            if (i30 + 3 < di3) up[3] = a3;
                         }
                     }
                     __syncthreads();
                     // D: P[k4][x][i3] = sum_k3u S3s[x][k4][k3u] U[k3u][x][i3]        (batch over x)
                     if constexpr (FF)
-                        ff_gemm<2, false, false>(nxc, nk4, di3, nk3u, reinterpret_cast<const float2*>(sm.S3s), nk4 * nk3u,
-                                                 nk3u, 1, sm.U, di3, nxc * di3, 1, reinterpret_cast<float2*>(sm.P), di3,
-                                                 nxc * di3, 1, tid, nth);
+                        rows_gemm<GEMM_FF_D, 2>(nxc, nk4, di3, nk3u, sm.S3s, nk4 * nk3u, nk3u, sm.U, di3, nxc * di3,
+                                                sm.P, di3, nxc * di3, tid, nth);
                     else
                         flat_gemm<double, false>(nxc, nk4, di3, nk3u, sm.S3s, nk4 * nk3u, nk3u, 1, sm.U, di3, nxc * di3, 1,
                                                  sm.P, di3, nxc * di3, 1, tid, nth);
                     __syncthreads();
                     // F: V[k4][k5][i3] += sum_x Q[k5][k4][x] P[k4][x][i3]             (batch over k4)
                     if constexpr (FF)
-                        ff_gemm<2, true, true>(nk4, nk5, di3, nxc, reinterpret_cast<const float2*>(sm.Q), nxc, nk4 * nxc, 1,
-                                               sm.P, nxc * di3, di3, 1, reinterpret_cast<float2*>(sm.V), nk5 * di3, di3, 1,
-                                               tid, nth);
+                        rows_gemm<GEMM_FF_F, 2>(nk4, nk5, di3, nxc, sm.Q, nxc, nk4 * nxc, sm.P, nxc * di3, di3, sm.V,
+                                                nk5 * di3, di3, tid, nth);
                     else
                         flat_gemm<double, true>(nk4, nk5, di3, nxc, sm.Q, nxc, nk4 * nxc, 1, sm.P, nxc * di3, di3, 1,
                                                 sm.V, nk5 * di3, di3, 1, tid, nth);
@@ -564,10 +698,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                             sm.Vf[q] = (float)sm.V[q];
                         }
                     }
-                    for (int q = tid; q < di4 * nk4; q += nth) sm.B4f[q] = (float)sm.B4[q];
+                    if constexpr (!FF) for (int q = tid; q < di4 * nk4; q += nth) sm.B4f[q] = (float)sm.B4[q];
                     __syncthreads();
-                    flat_gemm<float, true>(nk5, di4, di3, nk4, sm.B4f, 0, nk4, 1, sm.Vf, di3, nk5 * di3, 1,
-                                       sm.Y, di3, nk5 * di3, 1, tid, nth);
+                    rows_gemm<FF ? GEMM_F32_FF : GEMM_F32, 2>(nk5, di4, di3, nk4, sm.B4f, 0, nk4, sm.Vf, di3, nk5 * di3,
+                                                              sm.Y, di3, nk5 * di3, tid, nth);
                 } else {
                     flat_gemm<double, true>(nk5, di4, di3, nk4, sm.B4, 0, nk4, 1, sm.V, di3, nk5 * di3, 1,
                                          sm.Y, di3, nk5 * di3, 1, tid, nth);
@@ -575,6 +709,13 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
             }
             if (!gany) continue;
             __syncthreads();
+            if constexpr (FF) {   // the group's pair sums Y to FP64, in place (each thread its own entries)
+                for (int q = tid; q < di4 * nk5 * di3; q += nth) {
+                    const float2 y = reinterpret_cast<const float2*>(sm.Y)[q];
+                    sm.Y[q] = (double)y.x + (double)y.y;
+                }
+                __syncthreads();
+            }
             // H: T[i4][i5][i3] += sum_k5 B5'[i5][k5] Y[i4][k5][i3]   (register-resident output tile)
 #pragma unroll
             for (int rr = 0; rr < SF_TRT; rr++) {
