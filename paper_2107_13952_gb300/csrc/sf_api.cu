@@ -506,7 +506,7 @@ static ShellDims shell_dims(const sf_tables* t) {
     return d;
 }
 
-static size_t shell_smem_limit(int nt) { return nt == 256 ? 110 * 1024 : 200 * 1024; }
+static size_t shell_smem_limit(int nt) { return nt == 256 ? 109 * 1024 : 200 * 1024; }   // 256: two CTAs (with static shared memory) per SM
 
 // the register-resident output tile (blocks of 2 i5 x 4 i3 per i4) fits SF_TRT blocks per thread
 static bool shell_tile_fits(const sf_tables* t, int nt, int split) {

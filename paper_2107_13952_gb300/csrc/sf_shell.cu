@@ -331,10 +331,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
     extern __shared__ double smem[];
     __shared__ int s_item;
     __shared__ int s_k2lo[SF_MAX_DL + 1], s_nk2[SF_MAX_DL + 1], s_k3lo[SF_MAX_DL + 1], s_nk3[SF_MAX_DL + 1];
+    __shared__ int2 s_c3n[SF_MAX_DL + 1];   // per l23: (offset of the k3 union start in its k3 range, range size)
     __shared__ double s_sig[SF_MAX_DL + 1];
     __shared__ float s_sigf[SF_MAX_DL + 1];
     __shared__ SlotDesc s_sd4[SF_MAX_DL + 1];
     __shared__ SlotDesc s_sdx[4];   // slots of S1, S5, S2 (per group) and S3 (per 5-tuple), read in place
+    __shared__ VtxDev s_v;          // the current work item's vertex record
+    __shared__ int s_vtx;
+    if (threadIdx.x == 0) s_vtx = -1;
     const ShellSmem sm = carve(smem, mdi, mdk, mk3u, XC, Dmax, mni3);
     const int tid = threadIdx.x, nth = NT;
     for (;;) {
@@ -344,7 +348,16 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
         const int it = s_item;
         if (it >= n_items) break;
         const WorkItem w = items[it];
-        const VtxDev& v = V[w.vtx];
+        // the vertex record in shared memory: its fields are read throughout the item, and from
+        // global memory they would be evicted from L1 by the streamed {6j} slabs
+        if (w.vtx != s_vtx) {
+            const int* src = reinterpret_cast<const int*>(V + w.vtx);
+            int* dst = reinterpret_cast<int*>(&s_v);
+            for (int q = tid; q < (int)(sizeof(VtxDev) / sizeof(int)); q += nth) dst[q] = src[q];
+            __syncthreads();
+            if (tid == 0) s_vtx = w.vtx;
+        }
+        const VtxDev& v = s_v;
         const int D = v.D;
         const int j12 = v.tj[F12], j13 = v.tj[F13], j14 = v.tj[F14], j15 = v.tj[F15];
         const int i1 = v.ilo[0] + 2 * w.i1;
@@ -404,31 +417,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                 const int xhi = imin_(x_hi_a, imin_(x_hi_b, x_hi_c));
                 if (((xlo - x_lo_a) & 1) != 0) xlo++;   // parity of i1 + l25
                 if (xlo > xhi) continue;
-                // per-l23 shell data (uniform across the block) and the union of the k3 ranges
-                int k3ulo = 1 << 30, k3uhi = -1;
-                bool any = false;
-                for (int d = 0; d < D; d++) {
-                    const int l23 = v.tj[F23] + 2 * d;
-                    int k2lo, nk2, k3lo, nk3;
-                    sf_pair_range(l23, l24, l25, j12, &k2lo, &nk2);
-                    sf_pair_range(l34, l35, j13, l23, &k3lo, &nk3);
-                    const int64_t s = (((int64_t)g * D + d24) * D + d34) * D + d;   // group-major order
-                    if (nk2 == 0 || nk3 == 0 || !shell_selected(filt, s)) { nk2 = 0; nk3 = 0; }
-                    if (nk3 > 0) {
-                        any = true;
-                        k3ulo = imin_(k3ulo, k3lo);
-                        k3uhi = imax_(k3uhi, k3lo + 2 * (nk3 - 1));
-                    }
-                }
-                if (!any) continue;
-                gany = true;
-                __syncthreads();   // previous 5-tuple done with the shared buffers below
+                __syncthreads();   // the previous 5-tuple is done with the per-l23 arrays and the buffers
+                // per-l23 shell data, one thread per l23
                 for (int d = tid; d < D; d += nth) {
                     const int l23 = v.tj[F23] + 2 * d;
                     int k2lo, nk2, k3lo, nk3;
                     sf_pair_range(l23, l24, l25, j12, &k2lo, &nk2);
                     sf_pair_range(l34, l35, j13, l23, &k3lo, &nk3);
-                    const int64_t s = (((int64_t)g * D + d24) * D + d34) * D + d;
+                    const int64_t s = (((int64_t)g * D + d24) * D + d34) * D + d;   // group-major order
                     if (nk2 == 0 || nk3 == 0 || !shell_selected(filt, s)) { nk2 = 0; nk3 = 0; }
                     s_k2lo[d] = k2lo; s_nk2[d] = nk2; s_k3lo[d] = k3lo; s_nk3[d] = nk3;
                     const int E2 = jsum + k2lo + k3lo + k4lo + k5lo + l23 + l24 + l25 + l34 + l35 + l45;
@@ -436,6 +432,19 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                     s_sigf[d] = ((E2 >> 1) & 1) ? -1.0f : 1.0f;
                     s_sd4[d] = load_slot(v.slot[3] + d * D + d24);
                 }
+                __syncthreads();
+                // the union of the k3 ranges (every thread, from the shared arrays)
+                int k3ulo = 1 << 30, k3uhi = -1;
+                for (int d = 0; d < D; d++) {
+                    const int nk3 = s_nk3[d], k3lo = s_k3lo[d];
+                    if (nk3 > 0) {
+                        k3ulo = imin_(k3ulo, k3lo);
+                        k3uhi = imax_(k3uhi, k3lo + 2 * (nk3 - 1));
+                    }
+                }
+                if (k3uhi < 0) continue;   // no selected shell in this 5-tuple
+                gany = true;
+                for (int d = tid; d < D; d += nth) s_c3n[d] = make_int2((k3ulo - s_k3lo[d]) / 2, s_nk3[d]);
                 const int nk3u = (k3uhi - k3ulo) / 2 + 1;
                 const FDiv f_nk3u = fdiv_make(nk3u), f_di3 = fdiv_make(di3), f_mdk5 = fdiv_make(mdk);
                 const int t4 = (d45 * D + d24) * D + d34;
@@ -626,15 +635,16 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                         for (int q = tid; q < nk3u * nxc * nb3; q += nth) {
                             const int r = fdiv_q(q, f_nb3), b = q - r * nb3, ku = fdiv_q(r, f_nxc), xc = r - ku * nxc;
                             const int i30 = 4 * b;
-                            const int k3 = k3ulo + 2 * ku;
                             double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
                             if constexpr (MIX) {
                                 const float* Rf = reinterpret_cast<const float*>(sm.R);
                                 const float* Bf = reinterpret_cast<const float*>(sm.B3s);
                                 float f0 = 0.0f, f1 = 0.0f, f2 = 0.0f, f3 = 0.0f;
+#pragma unroll 2
                                 for (int d = 0; d < D; d++) {
-                                    const int c3 = (k3 - s_k3lo[d]) >> 1;
-                                    if (k3 < s_k3lo[d] || c3 >= s_nk3[d]) continue;
+                                    const int2 cn = s_c3n[d];
+                                    const int c3 = ku + cn.x;
+                                    if ((unsigned)c3 >= (unsigned)cn.y) continue;
                                     const float rr = Rf[(d * mdk + c3) * XC + xc];
                                     const float* bp = Bf + (d * mdk + c3) * di3 + i30;
                                     f0 = fmaf(rr, bp[0], f0);
@@ -652,9 +662,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                                 }
                                 a0 = f0; a1 = f1; a2 = f2; a3 = f3;
                             } else {
+#pragma unroll 2
                                 for (int d = 0; d < D; d++) {
-                                    const int c3 = (k3 - s_k3lo[d]) >> 1;
-                                    if (k3 < s_k3lo[d] || c3 >= s_nk3[d]) continue;
+                                    const int2 cn = s_c3n[d];
+                                    const int c3 = ku + cn.x;
+                                    if ((unsigned)c3 >= (unsigned)cn.y) continue;
                                     const double rr = sm.R[(d * mdk + c3) * XC + xc];
                                     const double* bp = sm.B3s + (d * mdk + c3) * di3 + i30;
                                     a0 = fma(rr, bp[0], a0);
