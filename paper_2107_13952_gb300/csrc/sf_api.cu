@@ -414,13 +414,17 @@ extern "C" int sf_boosters(sf_tables* t, const sf_quad_rule* q, cudaStream_t str
     SF_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, sizeof(int), stream));
     for (size_t i = 0; i < t->vs.size(); i++) {
         VertexHost& h = t->vs[i];
-        for (int f = 0; f < 10; f++)
-            SF_TRY(sf_dtable_build(h.v.two_j[f], h.v.gamma, h.nl[f], nnodes, t->d_r, t->d_gl, h.d_dtab[f], stream));
+        {
+            int nlf[10];
+            for (int f = 0; f < 10; f++) nlf[f] = h.nl[f];
+            SF_TRY(sf_dtable_build(h.v.two_j, h.v.gamma, nlf, nnodes, t->d_r, t->d_gl, h.d_dtab, stream));
+        }
         for (int e = 0; e < 4; e++) {
             static const int faces[4][4] = {{F23, F24, F25, F12}, {F34, F35, F13, F23}, {F45, F14, F24, F34}, {F15, F25, F35, F45}};
             const int32_t* j = h.v.two_j;
             size_t smem = sf_booster_smem(j[faces[e][0]], j[faces[e][1]], j[faces[e][2]], j[faces[e][3]], h.dkmax[e]);
-            SF_TRY(sf_booster_build(t->d_vtx + i, e + 2, (int)h.ntrip, smem, t->d_W, nnodes, t->d_fact, t->d_Aj, t->d_Cj,
+            const int nc = sf_booster_chunk(j[faces[e][0]], j[faces[e][1]], j[faces[e][2]], j[faces[e][3]]);
+            SF_TRY(sf_booster_build(t->d_vtx + i, e + 2, (int)h.ntrip, smem, nc, t->d_W, nnodes, t->d_fact, t->d_Aj, t->d_Cj,
                                     h.d_B[e], t->d_status, stream));
             SF_TRY(sf_to_float(h.d_B[e], h.d_Bf[e], (int64_t)h.ntrip * h.di[e + 1] * h.dkmax[e], t->num_sms, stream));
         }

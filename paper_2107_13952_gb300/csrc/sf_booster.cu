@@ -9,6 +9,7 @@
 //   4. per (edge, virtual-spin triple): I(m) = sum_n W_n prod_a d_a(m_a, r_n) and
 //      B[i][k] = Re sum_m 4jm(j;m)^(i) 4jm(l;m)^(k) I(m).
 #include "sf_racah.cuh"
+#include <algorithm>
 
 #define SF_PI 3.14159265358979323846
 
@@ -117,10 +118,16 @@ __device__ inline double ipow_(double b, int e) {
     return r;
 }
 
-// grid: x = node blocks, y = m index; one face per launch; l values [il0, il0 + nlc)
-__global__ void __launch_bounds__(128) k_dtable(int tk, double rho, int nl, int nnodes, const double* __restrict__ R,
-                                                const double* __restrict__ gl, double2* __restrict__ out) {
+// grid: x = node blocks, y = m index, z = face; all ten faces of a vertex in one launch
+#define SF_DT_NT 64
+__global__ void __launch_bounds__(SF_DT_NT) k_dtable(const __grid_constant__ DtabFaces fc, int nnodes,
+                                                     const double* __restrict__ R, const double* __restrict__ gl) {
+    const int face = blockIdx.z;
+    const int tk = fc.tk[face], nl = fc.nl[face];
+    const double rho = fc.rho[face];
+    double2* __restrict__ out = fc.out[face];
     const int im = blockIdx.y;
+    if (im > tk) return;   // this face has fewer m values than the largest one (uniform per CTA)
     const int tm = -tk + 2 * im;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     // recurrence coefficients d^{l+1} = (al cos(b) - gl) d^l - de d^{l-1}, l = k + p
@@ -230,12 +237,20 @@ __global__ void __launch_bounds__(128) k_dtable(int tk, double rho, int nl, int 
     }
 }
 
-int sf_dtable_build(int tk, double gamma, int nl, int nnodes, const double* d_r, const double* d_gl, double2* d_out,
-                    cudaStream_t s) {
-    if (nl > SF_MAX_DL + 1) return sf_set_error(SF_ERR_LIMIT, "dl too large for the d-table kernel");
-    double rho = gamma * (0.5 * tk + 1.0);
-    dim3 grid((nnodes + 127) / 128, tk + 1);
-    k_dtable<<<grid, 128, 0, s>>>(tk, rho, nl, nnodes, d_r, d_gl, d_out);
+int sf_dtable_build(const int tk[10], double gamma, const int nl[10], int nnodes, const double* d_r, const double* d_gl,
+                    double2* const d_out[10], cudaStream_t s) {
+    DtabFaces fc{};
+    int mmax = 1;
+    for (int f = 0; f < 10; f++) {
+        if (nl[f] > SF_MAX_DL + 1) return sf_set_error(SF_ERR_LIMIT, "dl too large for the d-table kernel");
+        fc.tk[f] = tk[f];
+        fc.nl[f] = nl[f];
+        fc.rho[f] = gamma * (0.5 * tk[f] + 1.0);
+        fc.out[f] = d_out[f];
+        mmax = std::max(mmax, tk[f] + 1);
+    }
+    dim3 grid((nnodes + SF_DT_NT - 1) / SF_DT_NT, mmax, 10);
+    k_dtable<<<grid, SF_DT_NT, 0, s>>>(fc, nnodes, d_r, d_gl);
     sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;
@@ -249,7 +264,16 @@ int sf_dtable_build(int tk, double gamma, int nl, int nnodes, const double* d_r,
 __constant__ int c_edge_face[4][4] = {{F23, F24, F25, F12}, {F34, F35, F13, F23}, {F45, F14, F24, F34}, {F15, F25, F35, F45}};
 __constant__ int c_edge_slot[4][4] = {{0, 1, 2, -1}, {0, 1, -1, 2}, {0, -1, 1, 2}, {-1, 0, 1, 2}};
 
-#define SF_NC 16   // nodes per staged chunk
+// nodes per staged chunk: as many as keep the staged pair tables within SF_NC_BYTES (so that two
+// CTAs fit per SM), a power of two between 16 and 1024; small spins stage many nodes per barrier
+#define SF_NC_BYTES (80 * 1024)
+int sf_booster_chunk(int tj1, int tj2, int tj3, int tj4) {
+    const int n12 = (tj1 + 1) * (tj2 + 1), n34 = (tj3 + 1) * (tj4 + 1);
+    const size_t per_node = (size_t)((n12 - n12 / 2) + (n34 - n34 / 2)) * sizeof(double2);
+    int nc = 16;
+    while (nc < 1024 && per_node * (size_t)(2 * nc) <= SF_NC_BYTES) nc *= 2;
+    return nc;
+}
 
 // boundary-side 3j tables of one edge (shared by every triple):
 //   Aj[i][m1][m2] = (j1 j2 i; m1 m2 mu), Cj[i][m3][m4] = (i j3 j4; -mu m3 m4), mu = -(m1+m2)
@@ -287,7 +311,7 @@ __global__ void k_boundary_3j(const VtxDev* __restrict__ vp, int edge, const dd*
 #define SF_BT 6         // canonical tuples per thread (upper half of at most 17^3 tuples / 512 threads)
 #define SF_BOOST_NT 512
 __global__ void __launch_bounds__(SF_BOOST_NT) k_booster(const VtxDev* __restrict__ vp, int edge, const double* __restrict__ Wm,
-                                                 int nnodes, const dd* __restrict__ F, const double* __restrict__ gAj,
+                                                 int nnodes, int NC, const dd* __restrict__ F, const double* __restrict__ gAj,
                                                  const double* __restrict__ gCj, double* __restrict__ Bout, int* status) {
     extern __shared__ __align__(16) double sm[];
     const VtxDev& v = *vp;
@@ -318,11 +342,11 @@ __global__ void __launch_bounds__(SF_BOOST_NT) k_booster(const VtxDev* __restric
     const int C12 = N12 - h12, C34 = N34 - h34;
     const double sg12 = ((((tl[0] - tj[0]) + (tl[1] - tj[1])) / 2) & 1) ? -1.0 : 1.0;
     const double sg34 = ((((tl[2] - tj[2]) + (tl[3] - tj[3])) / 2) & 1) ? -1.0 : 1.0;
-    // shared: Ir[M] | union { P12[C12][SF_NC], P34[C34][SF_NC] (complex) ; Al[nk][n1 n2], Cl[nk][n3 n4] }
+    // shared: Ir[M] | union { P12[C12][NC], P34[C34][NC] (complex) ; Al[nk][n1 n2], Cl[nk][n3 n4] }
     double* sIr = sm;
     const int Mpad = (M + 1) & ~1;   // keep the complex staging area 16-byte aligned
     double2* P12 = reinterpret_cast<double2*>(sm + Mpad);
-    double2* P34 = P12 + C12 * SF_NC;
+    double2* P34 = P12 + C12 * NC;
     double* sAl = sm + Mpad;
     double* sCl = sAl + nk * n1 * n2;
     const double2* d0 = v.dtab[fc[0]] + (int64_t)il[0] * n1 * nnodes;
@@ -332,11 +356,11 @@ __global__ void __launch_bounds__(SF_BOOST_NT) k_booster(const VtxDev* __restric
     double acc[SF_BT];
 #pragma unroll
     for (int q = 0; q < SF_BT; q++) acc[q] = 0.0;
-    for (int n0 = 0; n0 < nnodes; n0 += SF_NC) {
-        const int nc = imin_(SF_NC, nnodes - n0);
+    for (int n0 = 0; n0 < nnodes; n0 += NC) {
+        const int nc = imin_(NC, nnodes - n0);
         __syncthreads();
-        for (int q = threadIdx.x; q < C12 * SF_NC; q += blockDim.x) {
-            const int nn = q % SF_NC, pr = h12 + q / SF_NC, a2 = pr % n2, a1 = pr / n2;
+        for (int q = threadIdx.x; q < C12 * NC; q += blockDim.x) {
+            const int nn = q % NC, pr = h12 + q / NC, a2 = pr % n2, a1 = pr / n2;
             double2 z = make_double2(0.0, 0.0);
             if (nn < nc) {
                 const double2 x = d0[(int64_t)a1 * nnodes + n0 + nn], y = d1[(int64_t)a2 * nnodes + n0 + nn];
@@ -345,8 +369,8 @@ __global__ void __launch_bounds__(SF_BOOST_NT) k_booster(const VtxDev* __restric
             }
             P12[q] = z;
         }
-        for (int q = threadIdx.x; q < C34 * SF_NC; q += blockDim.x) {
-            const int nn = q % SF_NC, pr = h34 + q / SF_NC, a4 = pr % n4, a3 = pr / n4;
+        for (int q = threadIdx.x; q < C34 * NC; q += blockDim.x) {
+            const int nn = q % NC, pr = h34 + q / NC, a4 = pr % n4, a3 = pr / n4;
             double2 z = make_double2(0.0, 0.0);
             if (nn < nc) {
                 const double2 x = d2[(int64_t)a3 * nnodes + n0 + nn], y = d3[(int64_t)a4 * nnodes + n0 + nn];
@@ -365,8 +389,8 @@ __global__ void __launch_bounds__(SF_BOOST_NT) k_booster(const VtxDev* __restric
                     const int i4 = (tm4 + tj[3]) / 2;
                     const int f12 = i1 * n2 + i2, f34 = i3 * n4 + i4;
                     const bool c12 = f12 < h12, c34 = f34 < h34;   // mirrored (conjugated) pairs
-                    const double2* p = P12 + ((c12 ? N12 - 1 - f12 : f12) - h12) * SF_NC;
-                    const double2* r = P34 + ((c34 ? N34 - 1 - f34 : f34) - h34) * SF_NC;
+                    const double2* p = P12 + ((c12 ? N12 - 1 - f12 : f12) - h12) * NC;
+                    const double2* r = P34 + ((c34 ? N34 - 1 - f34 : f34) - h34) * NC;
                     double s0 = 0.0, s1 = 0.0;
                     for (int nn = 0; nn < nc; nn++) {
                         const double2 a = p[nn], b = r[nn];
@@ -433,19 +457,19 @@ size_t sf_booster_smem(int tj1, int tj2, int tj3, int tj4, int nk) {
     int n1 = tj1 + 1, n2 = tj2 + 1, n3 = tj3 + 1, n4 = tj4 + 1;
     size_t M = ((size_t)n1 * n2 * n3 + 1) & ~(size_t)1;
     const int c12 = n1 * n2 - (n1 * n2) / 2, c34 = n3 * n4 - (n3 * n4) / 2;
-    size_t stage = (size_t)(c12 + c34) * SF_NC * sizeof(double2);
+    size_t stage = (size_t)(c12 + c34) * sf_booster_chunk(tj1, tj2, tj3, tj4) * sizeof(double2);
     size_t tabs = sizeof(double) * ((size_t)nk * n1 * n2 + (size_t)nk * n3 * n4);
     return M * sizeof(double) + (stage > tabs ? stage : tabs);
 }
 
-int sf_booster_build(const VtxDev* d_v, int edge, int ntrip, size_t smem, const double* d_W, int nnodes,
+int sf_booster_build(const VtxDev* d_v, int edge, int ntrip, size_t smem, int nc, const double* d_W, int nnodes,
                      const dd* F, double* d_Aj, double* d_Cj, double* d_B, int* d_status, cudaStream_t s) {
     if (smem > 227 * 1024) return sf_set_error(SF_ERR_LIMIT, "booster kernel needs %zu bytes of shared memory", smem);
     k_boundary_3j<<<64, 256, 0, s>>>(d_v, edge, F, d_Aj, d_Cj, d_status);
     sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     SF_CUDA_TRY(cudaFuncSetAttribute(k_booster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_booster<<<ntrip, SF_BOOST_NT, smem, s>>>(d_v, edge, d_W, nnodes, F, d_Aj, d_Cj, d_B, d_status);
+    k_booster<<<ntrip, SF_BOOST_NT, smem, s>>>(d_v, edge, d_W, nnodes, nc, F, d_Aj, d_Cj, d_B, d_status);
     sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;

@@ -127,20 +127,20 @@ __host__ __device__ inline double dd_to_d(dd a) { return a.hi + a.lo; }
 
 // ----------------------------------------------------------------------------------------------
 // exact unsigned big integers for the Racah sums (limbs of 32 bits, little-endian, fixed
-// capacity, loops fully unrolled so that the limbs live in registers)
-// ----------------------------------------------------------------------------------------------
-struct BigU { uint32_t w[SF_BI_LIMBS]; };
+// capacity NL, loops fully unrolled so that the limbs live in registers)
+template <int NL> struct BigUT { uint32_t w[NL]; };
+using BigU = BigUT<SF_BI_LIMBS>;
 
-__device__ inline void bi_zero(BigU& a) {
+template <int NL> __device__ inline void bi_zero(BigUT<NL>& a) {
 #pragma unroll
-    for (int i = 0; i < SF_BI_LIMBS; i++) a.w[i] = 0u;
+    for (int i = 0; i < NL; i++) a.w[i] = 0u;
 }
-__device__ inline void bi_set(BigU& a, uint32_t v) { bi_zero(a); a.w[0] = v; }
+template <int NL> __device__ inline void bi_set(BigUT<NL>& a, uint32_t v) { bi_zero(a); a.w[0] = v; }
 // a *= m; returns the carry out of the top limb (non-zero means overflow)
-__device__ inline uint32_t bi_mul(BigU& a, uint32_t m) {
+template <int NL> __device__ inline uint32_t bi_mul(BigUT<NL>& a, uint32_t m) {
     uint64_t c = 0;
 #pragma unroll
-    for (int i = 0; i < SF_BI_LIMBS; i++) {
+    for (int i = 0; i < NL; i++) {
         uint64_t t = (uint64_t)a.w[i] * m + c;
         a.w[i] = (uint32_t)t;
         c = t >> 32;
@@ -149,11 +149,11 @@ __device__ inline uint32_t bi_mul(BigU& a, uint32_t m) {
 }
 // a /= d for a divisor d >= 1 that divides a exactly (quotient by reciprocal multiplication:
 // q = mulhi(cur, floor((2^64-1)/d)) is q_true or q_true - 1 because cur < 2^64)
-__device__ inline void bi_divexact(BigU& a, uint32_t d) {
+template <int NL> __device__ inline void bi_divexact(BigUT<NL>& a, uint32_t d) {
     const uint64_t M = 0xFFFFFFFFFFFFFFFFull / d;
     uint64_t rem = 0;
 #pragma unroll
-    for (int i = SF_BI_LIMBS - 1; i >= 0; i--) {
+    for (int i = NL - 1; i >= 0; i--) {
         uint64_t cur = (rem << 32) | a.w[i];
         uint64_t q = __umul64hi(cur, M);
         uint64_t r = cur - q * d;
@@ -162,10 +162,10 @@ __device__ inline void bi_divexact(BigU& a, uint32_t d) {
         rem = r;
     }
 }
-__device__ inline uint32_t bi_add(BigU& a, const BigU& b) {
+template <int NL> __device__ inline uint32_t bi_add(BigUT<NL>& a, const BigUT<NL>& b) {
     uint64_t c = 0;
 #pragma unroll
-    for (int i = 0; i < SF_BI_LIMBS; i++) {
+    for (int i = 0; i < NL; i++) {
         uint64_t t = (uint64_t)a.w[i] + b.w[i] + c;
         a.w[i] = (uint32_t)t;
         c = t >> 32;
@@ -173,29 +173,29 @@ __device__ inline uint32_t bi_add(BigU& a, const BigU& b) {
     return (uint32_t)c;
 }
 // compare: -1, 0, 1
-__device__ inline int bi_cmp(const BigU& a, const BigU& b) {
+template <int NL> __device__ inline int bi_cmp(const BigUT<NL>& a, const BigUT<NL>& b) {
     int r = 0;
 #pragma unroll
-    for (int i = 0; i < SF_BI_LIMBS; i++) {
+    for (int i = 0; i < NL; i++) {
         if (a.w[i] != b.w[i]) r = (a.w[i] > b.w[i]) ? 1 : -1;   // the highest differing limb wins
     }
     return r;
 }
 // a -= b, requires a >= b
-__device__ inline void bi_sub(BigU& a, const BigU& b) {
+template <int NL> __device__ inline void bi_sub(BigUT<NL>& a, const BigUT<NL>& b) {
     int64_t br = 0;
 #pragma unroll
-    for (int i = 0; i < SF_BI_LIMBS; i++) {
+    for (int i = 0; i < NL; i++) {
         int64_t t = (int64_t)a.w[i] - (int64_t)b.w[i] - br;
         br = (t < 0) ? 1 : 0;
         a.w[i] = (uint32_t)(t + (br << 32));
     }
 }
 // value as double-double (top 128 bits, exact up to the dd rounding of the sum)
-__device__ inline dd bi_to_dd(const BigU& a) {
+template <int NL> __device__ inline dd bi_to_dd(const BigUT<NL>& a) {
     int top = -1;
 #pragma unroll
-    for (int i = 0; i < SF_BI_LIMBS; i++) if (a.w[i]) top = i;
+    for (int i = 0; i < NL; i++) if (a.w[i]) top = i;
     if (top < 0) return dd{0.0, 0.0};
     dd acc{0.0, 0.0};
     for (int i = top; i >= 0 && i > top - 4; i--) {
@@ -265,10 +265,18 @@ int sf_to_float(const double* d_in, float* d_out, int64_t n, int num_sms, cudaSt
 int sf_to_ff(const double* d_in, float2* d_out, int64_t n, int num_sms, cudaStream_t s);
 int sf_rule_build(const sf_quad_rule* q, double* d_gl, double* d_x, double* d_w, double* d_r, double* d_W,
                   cudaStream_t s);
-int sf_dtable_build(int tk, double gamma, int nl, int nnodes, const double* d_r, const double* d_gl, double2* d_out,
-                    cudaStream_t s);
+// d-tables of the ten faces of one vertex (one launch): doubled boundary spins tk, l counts nl
+struct DtabFaces {
+    int tk[10], nl[10];
+    double rho[10];
+    double2* out[10];
+};
+int sf_dtable_build(const int tk[10], double gamma, const int nl[10], int nnodes, const double* d_r, const double* d_gl,
+                    double2* const d_out[10], cudaStream_t s);
+// node chunk of the booster kernel for the edge's four boundary spins, and its shared memory
+int sf_booster_chunk(int tj1, int tj2, int tj3, int tj4);
 size_t sf_booster_smem(int tj1, int tj2, int tj3, int tj4, int nk);
-int sf_booster_build(const VtxDev* d_v, int edge, int ntrip, size_t smem, const double* d_W, int nnodes,
+int sf_booster_build(const VtxDev* d_v, int edge, int ntrip, size_t smem, int nc, const double* d_W, int nnodes,
                      const dd* F, double* d_Aj, double* d_Cj, double* d_B, int* d_status, cudaStream_t s);
 // Shell-kernel modes: the sf_precision values (0 FP64, 1 mixed, 2 mixed with compensated FP32
 // pairs for the {6j} contractions).

@@ -18,26 +18,23 @@ __device__ inline dd sf_delta(const dd* F, int x, int y, int z) {
 }
 
 // flush an accumulated numerator/denominator pair into t (exact: t*num/den is an integer)
-__device__ inline void sf_muldiv(BigU& t, uint32_t num, uint32_t den, uint32_t& ovf) {
+template <int NL> __device__ inline void sf_muldiv(BigUT<NL>& t, uint32_t num, uint32_t den, uint32_t& ovf) {
     ovf |= bi_mul(t, num);
     if (den > 1u) bi_divexact(t, den);
 }
 
-// {a b c; d e f}, doubled spins. Racah's single sum (Edmonds eq. 6.3.7).
-__device__ inline double sf_sixj(int ta, int tb, int tc, int td, int te, int tf, const dd* F, int* status) {
-    if (!(sf_tri(ta, tb, tc) && sf_tri(ta, te, tf) && sf_tri(td, tb, tf) && sf_tri(td, te, tc))) return 0.0;
-    const int a1 = (ta + tb + tc) / 2, a2 = (ta + te + tf) / 2, a3 = (td + tb + tf) / 2, a4 = (td + te + tc) / 2;
-    const int b1 = (ta + tb + td + te) / 2, b2 = (ta + tc + td + tf) / 2, b3 = (tb + tc + te + tf) / 2;
-    const int zmin = imax_(imax_(a1, a2), imax_(a3, a4));
-    const int zmax = imin_(imin_(b1, b2), b3);
-    if (zmin > zmax) return 0.0;
+// The exact alternating Racah sum of {a b c; d e f} for z in [zmin, zmax], times the four
+// triangle coefficients, rounded once; NL limbs hold every term (see sf_sixj).
+template <int NL>
+__device__ inline double sf_sixj_sum(int ta, int tb, int tc, int td, int te, int tf, int zmin, int zmax, const int a[4],
+                                     const int b[3], const dd* F, int* status) {
     uint32_t ovf = 0;
     // first term (zmin+1)! / prod of seven factorials whose arguments sum to zmin:
     // (zmin+1) times a multinomial, built one exact factor at a time
-    BigU t;
+    BigUT<NL> t;
     bi_set(t, 1u);
     {
-        const int n7[7] = {zmin - a1, zmin - a2, zmin - a3, zmin - a4, b1 - zmin, b2 - zmin, b3 - zmin};
+        const int n7[7] = {zmin - a[0], zmin - a[1], zmin - a[2], zmin - a[3], b[0] - zmin, b[1] - zmin, b[2] - zmin};
         uint32_t num = 1u, den = 1u;
         int m = 0;
         for (int i = 0; i < 7; i++) {
@@ -55,15 +52,15 @@ __device__ inline double sf_sixj(int ta, int tb, int tc, int td, int te, int tf,
         sf_muldiv(t, num, den, ovf);
         ovf |= bi_mul(t, (uint32_t)(zmin + 1));
     }
-    BigU pos, neg;
+    BigUT<NL> pos, neg;
     bi_zero(pos);
     bi_zero(neg);
     for (int z = zmin; z <= zmax; z++) {
         if (z & 1) ovf |= bi_add(neg, t); else ovf |= bi_add(pos, t);
         if (z == zmax) break;
         // term ratio t_{z+1}/t_z = (z+2)(b1-z)(b2-z)(b3-z) / ((z+1-a1)(z+1-a2)(z+1-a3)(z+1-a4))
-        uint32_t num = (uint32_t)(z + 2) * (uint32_t)(b1 - z) * (uint32_t)(b2 - z) * (uint32_t)(b3 - z);
-        uint32_t den = (uint32_t)(z + 1 - a1) * (uint32_t)(z + 1 - a2) * (uint32_t)(z + 1 - a3) * (uint32_t)(z + 1 - a4);
+        uint32_t num = (uint32_t)(z + 2) * (uint32_t)(b[0] - z) * (uint32_t)(b[1] - z) * (uint32_t)(b[2] - z);
+        uint32_t den = (uint32_t)(z + 1 - a[0]) * (uint32_t)(z + 1 - a[1]) * (uint32_t)(z + 1 - a[2]) * (uint32_t)(z + 1 - a[3]);
         sf_muldiv(t, num, den, ovf);
     }
     if (ovf && status) atomicCAS(status, SF_DEV_OK, SF_DEV_BIGINT_OVERFLOW);
@@ -77,6 +74,23 @@ __device__ inline double sf_sixj(int ta, int tb, int tc, int td, int te, int tf,
     S = dd_mul(S, sf_delta(F, td, tb, tf));
     S = dd_mul(S, sf_delta(F, td, te, tc));
     return dd_to_d(S);
+}
+
+// {a b c; d e f}, doubled spins. Racah's single sum (Edmonds eq. 6.3.7). The term of index z is
+// (z+1) times a multinomial coefficient of z into seven parts, so it is below (z+1) 7^z; with
+// 32 bits of headroom for the exact multiply-then-divide steps, 8, 16 or 24 limbs are chosen
+// from that bound at zmax (8 limbs up to zmax = 76, 16 up to 167).
+__device__ inline double sf_sixj(int ta, int tb, int tc, int td, int te, int tf, const dd* F, int* status) {
+    if (!(sf_tri(ta, tb, tc) && sf_tri(ta, te, tf) && sf_tri(td, tb, tf) && sf_tri(td, te, tc))) return 0.0;
+    const int a[4] = {(ta + tb + tc) / 2, (ta + te + tf) / 2, (td + tb + tf) / 2, (td + te + tc) / 2};
+    const int b[3] = {(ta + tb + td + te) / 2, (ta + tc + td + tf) / 2, (tb + tc + te + tf) / 2};
+    const int zmin = imax_(imax_(a[0], a[1]), imax_(a[2], a[3]));
+    const int zmax = imin_(imin_(b[0], b[1]), b[2]);
+    if (zmin > zmax) return 0.0;
+    const float bits = log2f((float)(zmax + 2)) + 2.8074f * (float)zmax + 34.0f;   // log2 7 = 2.8074
+    if (bits <= 256.0f) return sf_sixj_sum<8>(ta, tb, tc, td, te, tf, zmin, zmax, a, b, F, status);
+    if (bits <= 512.0f) return sf_sixj_sum<16>(ta, tb, tc, td, te, tf, zmin, zmax, a, b, F, status);
+    return sf_sixj_sum<SF_BI_LIMBS>(ta, tb, tc, td, te, tf, zmin, zmax, a, b, F, status);
 }
 
 // C(n, k) multiplied into t exactly (k steps of *(n-k+i)/i, batched)

@@ -546,17 +546,36 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                             }
                         });
                     }
-                    // S3s[x][k4][k3u] from the S3 slot
-                    if constexpr (FF) {
-                        gather_loop<4>(nxc * nk4 * nk3u, tid, nth, [&](int q) {
-                            const int r = fdiv_q(q, f_nk3u), ku = q - r * nk3u, xc = fdiv_q(r, f_nk4), c4 = r - xc * nk4;
-                            return s6ff(v.Sff[2], sd3, k4lo + 2 * c4, k3ulo + 2 * ku, xc0 + 2 * xc);
-                        }, [&](int q, float2 val) { reinterpret_cast<float2*>(sm.S3s)[q] = val; });
-                    } else {
-                        gather_loop<GU>(nxc * nk4 * nk3u, tid, nth, [&](int q) {
-                            const int r = fdiv_q(q, f_nk3u), ku = q - r * nk3u, xc = fdiv_q(r, f_nk4), c4 = r - xc * nk4;
-                            return s6(v.S[2], sd3, k4lo + 2 * c4, k3ulo + 2 * ku, xc0 + 2 * xc);
-                        }, [&](int q, double val) { sm.S3s[q] = val; });
+                    // S3s[x][k4][k3u] from the S3 slot, read along x (contiguous in the table) and
+                    // stored transposed
+                    {
+                        auto s3_at = [&](int q, int& xc, int& c4, int& ku) {
+                            const int r = fdiv_q(q, f_nxc);
+                            xc = q - r * nxc;
+                            c4 = fdiv_q(r, f_nk3u);
+                            ku = r - c4 * nk3u;
+                        };
+                        if constexpr (FF) {
+                            gather_loop<4>(nxc * nk4 * nk3u, tid, nth, [&](int q) {
+                                int xc, c4, ku;
+                                s3_at(q, xc, c4, ku);
+                                return s6ff(v.Sff[2], sd3, k4lo + 2 * c4, k3ulo + 2 * ku, xc0 + 2 * xc);
+                            }, [&](int q, float2 val) {
+                                int xc, c4, ku;
+                                s3_at(q, xc, c4, ku);
+                                reinterpret_cast<float2*>(sm.S3s)[(xc * nk4 + c4) * nk3u + ku] = val;
+                            });
+                        } else {
+                            gather_loop<GU>(nxc * nk4 * nk3u, tid, nth, [&](int q) {
+                                int xc, c4, ku;
+                                s3_at(q, xc, c4, ku);
+                                return s6(v.S[2], sd3, k4lo + 2 * c4, k3ulo + 2 * ku, xc0 + 2 * xc);
+                            }, [&](int q, double val) {
+                                int xc, c4, ku;
+                                s3_at(q, xc, c4, ku);
+                                sm.S3s[(xc * nk4 + c4) * nk3u + ku] = val;
+                            });
+                        }
                     }
                     // E: Q[k5][k4][x] = (2x+1) S1[i1,k5,x] S2[k5,k4,x]
                     if constexpr (FF) {
