@@ -26,6 +26,13 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 RULE = (40.0, 40, 50)
+METRIC = "EPRL vertex shells/sec (mixed vs FP64 GPU path) at stated relative error"
+
+
+def workload_name(slices):
+    return ("homogeneous sweep: 16 vertices, all spins j=lambda/2 for lambda=1..16, gamma=1.2, dl=10 (11^6 shells "
+            "each), rule r_max=40 / 40 panels x 50 nodes; one step = 6j tables + d-tables + boosters of all 16 "
+            "vertices + shell sum over a 1/%d slice of every vertex's group-major shell range" % slices)
 SWEEP = [(lam, 10) for lam in range(1, 17)]
 GAMMA = 1.2
 # FP64 FMA pipe of the GB300: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.070 GHz (max SM clock)
@@ -37,9 +44,10 @@ PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_ff": 2}
 # step with a pair times a float (FMUL, 2 FFMA, TwoSum = 6, 2 FADD), F a pair times a pair (one
 # more FFMA); the FP32 booster phases take one FFMA per multiply-add
 FF_OPS = {"D": 11, "F": 12}
-# DRAM bytes (read + write) of the benchmark's shell-sum launch from one ncu capture per precision
-# (profiles/k_shell_mixed_sweep_traffic.md), valid while the kernel source hashes to "sha1".
-NCU_TRAFFIC = {"sha1": "f105b5962be0", "bytes_per_launch": {"mixed": 135627228928 + 161291776, "fp64": None}}
+# DRAM bytes (read + write) of the benchmark's shell-sum launch from one ncu capture (the first timed
+# launch, slice 3 of the sweep; profiles/k_shell_mixed_ff_sweep_traffic.md), valid while the kernel
+# source hashes to "sha1"
+NCU_TRAFFIC = {"sha1": "77e3c11e9e92", "bytes_per_launch": {"mixed_ff": 32906166784 + 118807808, "mixed": None, "fp64": None}}
 
 
 def kernel_sha1():
@@ -292,6 +300,55 @@ def batched_measure(shells, steps=3):
             "rel_err_vs_fp64": errs}
 
 
+def other_workloads(large_fraction=32):
+    """The two remaining workloads, timed once each after a warm-up (CUDA events):
+    * spin 4, gamma 1.2, dl 20 (21^6 = 85,766,121 shells): the first 1/large_fraction of its
+      group-major shell range in the pair path and the FP64 path, and the relative error between them;
+    * spin 3, gamma 1.2, dl 8 (9^6 shells): the boundary-contracted amplitude and its gradients with
+      respect to the five seeded boundary vectors and the four booster tensors (adjoint kernels)."""
+    import torch
+    import paper_2107_13952_gb300 as sf
+    from paper_2107_13952_gb300 import inputs
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    res = {}
+    w = inputs.large_shell()
+    t = sf.sf_6j_table([sf.vertex(w["two_j"], w["gamma"], w["dl"])])
+    sf.sf_boosters(t, RULE)
+    D = w["dl"] + 1
+    end = (D ** 3 // large_fraction) * D ** 3
+    lg = {"workload": "all spins 4, gamma 1.2, dl 20: shells [0, %d) of 85,766,121 (group-major)" % end}
+    outs = {}
+    for name, p in (("mixed_ff", sf.SF_MIXED_FF), ("fp64", sf.SF_FP64)):
+        ms, o = timed(lambda: sf.sf_vertex_amplitude(t, p, 0, end)[0].clone())
+        lg[name] = {"value": end / (ms / 1e3), "unit": "shells/s", "ms": ms}
+        outs[name] = o
+    lg["mixed_ff_vs_fp64_rel_err"] = float((outs["mixed_ff"] - outs["fp64"]).norm() / outs["fp64"].norm())
+    res["large_shell"] = lg
+    del t
+    w = inputs.boundary_contraction_vertex()
+    t = sf.sf_6j_table([sf.vertex(w["two_j"], w["gamma"], w["dl"])])
+    sf.sf_boosters(t, RULE)
+    dims = sf.intertwiner_ranges(w["two_j"], w["gamma"], w["dl"])[1]
+    psis = [torch.tensor(v, dtype=torch.complex128, device="cuda") for v in inputs.boundary_vectors(dims)]
+    n = (w["dl"] + 1) ** 6
+    ms, _ = timed(lambda: sf.sf_vertex_adjoint(t, psis, want_grads=True))
+    res["adjoint"] = {"workload": "all spins 3, gamma 1.2, dl 8 (531,441 shells): contracted amplitude and "
+                                  "gradients w.r.t. five boundary vectors and four booster tensors, FP64",
+                      "value": n / (ms / 1e3), "unit": "shells/s", "ms": ms}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -306,6 +363,7 @@ def main():
     ap.add_argument("--batched-shells", type=int, default=16384,
                     help="shells per vertex of the 256-vertex batched measurement (0: skip)")
     ap.add_argument("--case", default=None, help="lambda:groups:precision -- one shell-sum launch (profiling)")
+    ap.add_argument("--no-other-workloads", action="store_true", help="skip the spin-4 dl-20 and adjoint timings")
     args = ap.parse_args()
 
     if args.case:
@@ -336,13 +394,13 @@ def main():
                 n_all += n
                 t_all += el
         value = n_all / t_all
-        line = {"impl": "reference", "metric": "EPRL vertex shells/sec", "value": value, "unit": "shells/s",
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "shells/s",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * t_all / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": "homogeneous sweep lambda=1..16 (j=lambda/2), gamma=1.2, dl=10, "
-                                       "shell-sum phase of the CPU oracle on uniformly sampled shells",
-                           "sample": "%d shells" % n_all},
+                "config": {"workload": workload_name(args.slices), "slices_per_pass": args.slices,
+                           "sample": "the CPU oracle's shell-sum phase on %d shells drawn uniformly from the sweep "
+                                     "(boosters random), on all host cores" % n_all},
                 "cpu_baseline": {"value": value, "unit": "shells/s", "cores": cores, "kind": "oracle",
                                  "sample": "%d shells drawn uniformly from the sweep's %d shells, boosters "
                                            "random (shell-sum phase only)" % (n_all, 16 * total_shells_per_vertex)},
@@ -493,18 +551,18 @@ def main():
     batched = None
     if args.batched_shells > 0 and world == 1:
         batched = batched_measure(args.batched_shells)
+    others_w = None
+    if not args.no_other_workloads and world == 1:
+        others_w = other_workloads()
 
     d2h = sum(h.numel() * 8 for h in host)
     h2d = len(verts) * 56
     line = {
-        "metric": "EPRL vertex shells/sec (mixed vs FP64 GPU path) at stated relative error",
+        "metric": METRIC,
         "value": value, "unit": "shells/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "mixed": "f64+f32", "mixed_ff": "f64+f32+f32x2"}[args.precision], "data": "synthetic",
-        "config": {"workload": "homogeneous sweep: 16 vertices, all spins j=lambda/2 for lambda=1..16, gamma=1.2, "
-                               "dl=10 (11^6 shells each), rule r_max=40 / 40 panels x 50 nodes; one step = 6j "
-                               "tables + d-tables + boosters of all 16 vertices + shell sum over a 1/%d slice "
-                               "of every vertex's group-major shell range" % S,
+        "config": {"workload": workload_name(S),
                    "slices_per_pass": S, "precision": args.precision, "cache": "working set < L2 per kernel; "
                    "no flush (compute-bound FP64 path)"},
         "roofline": dict(roof, traffic=traffic, kernel="k_shell<%d>" % PRECISIONS[args.precision],
@@ -516,6 +574,7 @@ def main():
         "path": args.precision,
         "other_paths": others,
         "batched": batched,
+        "other_workloads": others_w,
         "mixed_vs_fp64": {"rel_err": rel_err, "stated_bound": 1e-6,
                           "metric": "||A_mixed - A_fp64|| / ||A_fp64|| over the 16 vertices of one slice"},
     }

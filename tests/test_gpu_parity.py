@@ -82,6 +82,41 @@ def test_6j_tables_exact_sampled_large(lib, tj, dl):
     assert _check_6j(t, tj, dl, max_per_table=400, seed=dl) == 2000
 
 
+def _racah_zmax(ta, tb, tc, td, te, tf):
+    return min((ta + tb + td + te) // 2, (ta + tc + td + tf) // 2, (tb + tc + te + tf) // 2)
+
+
+def test_6j_tables_exact_wide_limbs(lib):
+    """Spins 28 at dl 0, the largest the table kernel admits: the top S3 entries have Racah sums up
+    to z = 140, beyond the 8-limb width (z <= 76), so both limb widths that can occur (8 and 16;
+    the 24-limb path needs z > 167) are compared against the exact symbol."""
+    tj, dl = (56,) * 10, 0
+    t = _tables(tj, dl)
+    vals = sf.table_copy(t, 0, sf.SF_TAB_6J, 3).numpy()
+    (off, alo, blo, xlo, na, nb, nx, _), = sf.table_copy(t, 0, sf.SF_TAB_6J_SLOTS, 3).numpy()
+    widths = {8: 0, 16: 0}
+    rng = np.random.default_rng(5)
+    for it in range(4000):
+        # every other draw near the top of the box, where z is largest
+        if it % 2:
+            ia, ib = na - 1 - int(rng.integers(0, 1 + na // 6)), nb - 1 - int(rng.integers(0, 1 + nb // 6))
+        else:
+            ia, ib = int(rng.integers(0, na)), int(rng.integers(0, nb))
+        ix = int(rng.integers(0, nx))
+        args = _sixj_args(3, 0, dl + 1, tj, alo + 2 * ia, blo + 2 * ib, xlo + 2 * ix)
+        ref = ow.sixj(*args)
+        if ref == 0.0:
+            continue
+        z = _racah_zmax(*args)
+        w = 8 if z <= 76 else 16
+        if widths[w] >= 40:
+            continue
+        got = vals[off + (ia * nb + ib) * nx + ix]
+        assert abs(got - ref) <= np.spacing(abs(ref)), (args, got, ref)
+        widths[w] += 1
+    assert min(widths.values()) > 0, widths
+
+
 def test_rule_nodes(lib):
     t = _tables((2,) * 10, 0)
     sf.sf_boosters(t, (40.0, 40, 50))
