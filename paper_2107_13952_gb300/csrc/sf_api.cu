@@ -355,11 +355,23 @@ extern "C" int sf_6j_table(const sf_vertex* v, int32_t n, sf_tables** out, cudaS
         if (cudaMemsetAsync(t->d_status, 0, sizeof(int), stream) != cudaSuccess) { rc = sf_set_error(SF_ERR_CUDA, "memset"); break; }
         if ((rc = upload_vtxdev(t)) != SF_OK) break;
         if ((rc = sf_fact_table_build(t->d_fact, stream)) != SF_OK) break;
+        // triangle coefficients for every doubled spin that an argument of the tables reaches
+        int tri_m = 0;
+        for (const VertexHost& h : t->vs) {
+            for (int f = 0; f < 10; f++) tri_m = std::max(tri_m, h.v.two_j[f] + (f > F15 ? 2 * h.v.dl : 0));
+            for (int k = 0; k < 5; k++)
+                for (const SlotDesc& sd : h.S[k].slots)
+                    tri_m = std::max(tri_m, std::max(sd.alo + 2 * (sd.na - 1), std::max(sd.blo + 2 * (sd.nb - 1),
+                                                                                           sd.xlo + 2 * (sd.nx - 1))));
+        }
+        dd* d_tri = nullptr;
+        if ((rc = dev_alloc(t, (void**)&d_tri, (size_t)(tri_m + 1) * (tri_m + 1) * (tri_m + 1) * sizeof(dd))) != SF_OK) break;
+        if ((rc = sf_tri_table_build(tri_m, t->d_fact, d_tri, t->num_sms, stream)) != SF_OK) break;
         for (int i = 0; i < n && rc == SF_OK; i++) {
             VertexHost& h = t->vs[i];
             for (int k = 0; k < 5 && rc == SF_OK; k++)
                 rc = sf_sixj_table_build(k + 1, t->d_vtx + i, h.S[k].d_slots, (int)h.S[k].slots.size(), h.S[k].n,
-                                         h.S[k].d_vals, t->d_fact, t->d_status, t->num_sms, stream);
+                                         h.S[k].d_vals, d_tri, tri_m, t->d_status, t->num_sms, stream);
             if (rc == SF_OK) rc = sf_to_float(h.S[3].d_vals, h.d_S4f, h.S[3].n, t->num_sms, stream);
             if (rc == SF_OK) rc = sf_to_float(h.S[4].d_vals, h.d_S5f, h.S[4].n, t->num_sms, stream);
             for (int k = 0; k < 3 && rc == SF_OK; k++) rc = sf_to_ff(h.S[k].d_vals, h.d_Sff[k], h.S[k].n, t->num_sms, stream);

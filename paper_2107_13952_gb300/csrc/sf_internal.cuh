@@ -258,8 +258,10 @@ struct ReduceJob {             // one output tile's i3 range: items item0 + c * 
 // launchers implemented in the kernel translation units (return SF_OK or an error code)
 // ----------------------------------------------------------------------------------------------
 int sf_fact_table_build(dd* F, cudaStream_t s);
+// triangle coefficients of every triad with doubled spins up to m: (m+1)^3 double-doubles
+int sf_tri_table_build(int m, const dd* F, dd* d_out, int num_sms, cudaStream_t s);
 int sf_sixj_table_build(int table_id, const VtxDev* d_v, const SlotDesc* d_slots, int nslots, int64_t n,
-                        double* d_out, const dd* F, int* d_status, int num_sms, cudaStream_t s);
+                        double* d_out, const dd* d_tri, int tri_m, int* d_status, int num_sms, cudaStream_t s);
 int sf_to_float(const double* d_in, float* d_out, int64_t n, int num_sms, cudaStream_t s);
 // (hi, lo) float pairs: hi = fl32(d), lo = fl32(d - hi)
 int sf_to_ff(const double* d_in, float2* d_out, int64_t n, int num_sms, cudaStream_t s);

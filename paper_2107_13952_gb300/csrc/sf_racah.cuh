@@ -17,6 +17,14 @@ __device__ inline dd sf_delta(const dd* F, int x, int y, int z) {
     return dd_sqrt(dd_div(num, F[(x + y + z) / 2 + 1]));
 }
 
+// Triangle coefficients sf_delta(x, y, z) of every triad of doubled spins up to m, tabulated once
+// (x, y, z in [0, m]; zero where the triad fails): each {6j} takes four of them.
+struct TriTable {
+    const dd* d;
+    int m1;   // m + 1
+    __device__ dd at(int x, int y, int z) const { return d[((int64_t)x * m1 + y) * m1 + z]; }
+};
+
 // flush an accumulated numerator/denominator pair into t (exact: t*num/den is an integer)
 template <int NL> __device__ inline void sf_muldiv(BigUT<NL>& t, uint32_t num, uint32_t den, uint32_t& ovf) {
     ovf |= bi_mul(t, num);
@@ -27,7 +35,7 @@ template <int NL> __device__ inline void sf_muldiv(BigUT<NL>& t, uint32_t num, u
 // triangle coefficients, rounded once; NL limbs hold every term (see sf_sixj).
 template <int NL>
 __device__ inline double sf_sixj_sum(int ta, int tb, int tc, int td, int te, int tf, int zmin, int zmax, const int a[4],
-                                     const int b[3], const dd* F, int* status) {
+                                     const int b[3], const TriTable& tt, int* status) {
     uint32_t ovf = 0;
     // first term (zmin+1)! / prod of seven factorials whose arguments sum to zmin:
     // (zmin+1) times a multinomial, built one exact factor at a time
@@ -69,10 +77,10 @@ __device__ inline double sf_sixj_sum(int ta, int tb, int tc, int td, int te, int
     dd S;
     if (c > 0) { bi_sub(pos, neg); S = bi_to_dd(pos); }
     else { bi_sub(neg, pos); S = dd_neg(bi_to_dd(neg)); }
-    S = dd_mul(S, sf_delta(F, ta, tb, tc));
-    S = dd_mul(S, sf_delta(F, ta, te, tf));
-    S = dd_mul(S, sf_delta(F, td, tb, tf));
-    S = dd_mul(S, sf_delta(F, td, te, tc));
+    S = dd_mul(S, tt.at(ta, tb, tc));
+    S = dd_mul(S, tt.at(ta, te, tf));
+    S = dd_mul(S, tt.at(td, tb, tf));
+    S = dd_mul(S, tt.at(td, te, tc));
     return dd_to_d(S);
 }
 
@@ -80,7 +88,7 @@ __device__ inline double sf_sixj_sum(int ta, int tb, int tc, int td, int te, int
 // (z+1) times a multinomial coefficient of z into seven parts, so it is below (z+1) 7^z; with
 // 32 bits of headroom for the exact multiply-then-divide steps, 8, 16 or 24 limbs are chosen
 // from that bound at zmax (8 limbs up to zmax = 76, 16 up to 167).
-__device__ inline double sf_sixj(int ta, int tb, int tc, int td, int te, int tf, const dd* F, int* status) {
+__device__ inline double sf_sixj(int ta, int tb, int tc, int td, int te, int tf, const TriTable& tt, int* status) {
     if (!(sf_tri(ta, tb, tc) && sf_tri(ta, te, tf) && sf_tri(td, tb, tf) && sf_tri(td, te, tc))) return 0.0;
     const int a[4] = {(ta + tb + tc) / 2, (ta + te + tf) / 2, (td + tb + tf) / 2, (td + te + tc) / 2};
     const int b[3] = {(ta + tb + td + te) / 2, (ta + tc + td + tf) / 2, (tb + tc + te + tf) / 2};
@@ -88,9 +96,9 @@ __device__ inline double sf_sixj(int ta, int tb, int tc, int td, int te, int tf,
     const int zmax = imin_(imin_(b[0], b[1]), b[2]);
     if (zmin > zmax) return 0.0;
     const float bits = log2f((float)(zmax + 2)) + 2.8074f * (float)zmax + 34.0f;   // log2 7 = 2.8074
-    if (bits <= 256.0f) return sf_sixj_sum<8>(ta, tb, tc, td, te, tf, zmin, zmax, a, b, F, status);
-    if (bits <= 512.0f) return sf_sixj_sum<16>(ta, tb, tc, td, te, tf, zmin, zmax, a, b, F, status);
-    return sf_sixj_sum<SF_BI_LIMBS>(ta, tb, tc, td, te, tf, zmin, zmax, a, b, F, status);
+    if (bits <= 256.0f) return sf_sixj_sum<8>(ta, tb, tc, td, te, tf, zmin, zmax, a, b, tt, status);
+    if (bits <= 512.0f) return sf_sixj_sum<16>(ta, tb, tc, td, te, tf, zmin, zmax, a, b, tt, status);
+    return sf_sixj_sum<SF_BI_LIMBS>(ta, tb, tc, td, te, tf, zmin, zmax, a, b, tt, status);
 }
 
 // C(n, k) multiplied into t exactly (k steps of *(n-k+i)/i, batched)
