@@ -295,7 +295,8 @@ def batched_measure(shells, steps=3):
         errs[name] = num / den if den > 0 else None
     return {"workload": "256 irregular vertices (spins 1/2..6, dl 0..12, gamma 0.1/1.2/5.0, seed 0), shells "
                         "[0, %d) of every vertex, %d shells in all; one CUDA-graph replay of a planned launch "
-                        "per step, %d steps" % (shells, n, steps),
+                        "per step, %d steps; tables and boosters built once before the replays (not flushed "
+                        "between them)" % (shells, n, steps),
             "fp64": res["fp64"], "mixed": res["mixed"], "mixed_ff": res["mixed_ff"],
             "rel_err_vs_fp64": errs}
 
@@ -563,8 +564,10 @@ def main():
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "mixed": "f64+f32", "mixed_ff": "f64+f32+f32x2"}[args.precision], "data": "synthetic",
         "config": {"workload": workload_name(S),
-                   "slices_per_pass": S, "precision": args.precision, "cache": "working set < L2 per kernel; "
-                   "no flush (compute-bound FP64 path)"},
+                   "slices_per_pass": S, "precision": args.precision,
+                   "cache": "inputs larger than L2: every step rebuilds the {6j} tables, d-tables and boosters of "
+                            "all 16 vertices (the spin-8 S3 table alone, FP64 plus pair copy, is 384 MB, 3x the "
+                            "L2), so no step starts with its working set in L2; no separate flush"},
         "roofline": dict(roof, traffic=traffic, kernel="k_shell<%d>" % PRECISIONS[args.precision],
                          kernel_ms_per_step=1e3 * kern_s / args.steps),
         "cpu_baseline": cpu,
