@@ -150,7 +150,9 @@ int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t shell_begi
  *   partial tile (prod of dim_3..dim_5 doubles) per (vertex, i1, i2) tile; larger requests return
  *   SF_ERR_LIMIT with the size needed (split the shell range or the vertex set).
  *   The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *   that device current and caches it; make that first call before any stream capture.
+ *   that device current and caches it. Every call copies its work list from host memory and
+ *   synchronises the stream before returning, so it must not be issued while the stream is being
+ *   captured into a CUDA graph; replayable shell sums go through the sf_plan_* calls.
  *   Every call reuses the same array and leaves its contents behind; calls that overlap on the
  *   GPU (other streams, other host threads, same device) race on it and must be serialised by
  *   the caller. A_out: host array of device pointers, as in sf_vertex_amplitude. */
@@ -250,6 +252,16 @@ int sf_vertex_adjoint(sf_tables* t, const double* const psi[5], double* a_out,
 int64_t sf_table_size(const sf_tables* t, int32_t vertex, int32_t kind, int32_t index);
 int sf_table_copy(const sf_tables* t, int32_t vertex, int32_t kind, int32_t index, void* dst,
                   int64_t n_bytes, cudaStream_t stream);
+
+/* Self-check of the compensated-pair dot products of SF_MIXED_FF, on the device, by the very
+ * device steps its shell kernel uses (Ogita, Rump and Oishi's Dot2 on (hi, lo) float pairs with
+ * Dekker's FMA TwoProduct): n_dots dot products of length len, terms taken in increasing index.
+ *   kind 0: pair x float  (a: [n_dots][len][2] floats (hi, lo); b: [n_dots][len] floats)
+ *   kind 1: pair x pair   (a and b: [n_dots][len][2] floats)
+ *   out: [n_dots][2] floats, the normalised (hi, lo) result. All three are device pointers.
+ * Synchronises the stream. Errors: SF_ERR_ARG (kind, sizes or null pointers), SF_ERR_CUDA. */
+int sf_check_dot2(int32_t kind, int32_t n_dots, int32_t len, const float* a, const float* b, float* out,
+                  cudaStream_t stream);
 
 /* Number of kernels this library has launched in the process (all entry points). */
 int64_t sf_kernel_launches(void);

@@ -52,6 +52,7 @@ def booster(tj, tl, dtabs, wmeas, check_real=1e-12):
     irng = wigner.pair_range(*tj)
     krng = wigner.pair_range(*tl)
     B = np.zeros((len(irng), len(krng)), dtype=complex)
+    T = np.zeros((len(irng), len(krng)))      # sum over m of |term|: the scale of the rounding in B
     ms = [range(-t, t + 1, 2) for t in tj]
     for m1, m2, m3 in itertools.product(*ms[:3]):
         m4 = -(m1 + m2 + m3)
@@ -63,11 +64,15 @@ def booster(tj, tl, dtabs, wmeas, check_real=1e-12):
         wj = [float(wigner.fourjm_mp(tj, mm, ti)) for ti in irng]
         wl = [float(wigner.fourjm_mp(tl, mm, tk)) for tk in krng]
         B += np.outer(wj, wl) * integ
+        T += np.abs(np.outer(wj, wl)) * abs(integ)
     im = float(np.max(np.abs(B.imag))) if B.size else 0.0
     if check_real is not None and B.size:
-        scale = max(float(np.max(np.abs(B))), 1e-300)
+        # the imaginary parts of the m and -m terms cancel exactly, so only rounding of the
+        # m-sum remains: measured against the sum of |terms| (B itself vanishes identically when
+        # the sum of l - j over the four strands is odd, and then only rounding is left in it)
+        scale = max(float(np.max(T)), 1e-300)
         if im > check_real * scale:
-            raise ArithmeticError("booster is not real: max|Im|/max|B| = %g" % (im / scale))
+            raise ArithmeticError("booster is not real: max|Im| / (sum of |terms|) = %g" % (im / scale))
     return B.real.copy(), irng, krng, im
 
 

@@ -28,7 +28,7 @@ EXPORTS = ("sf_version", "sf_last_error", "sf_intertwiner_ranges", "sf_num_shell
            "sf_vertex_amplitude", "sf_vertex_adjoint", "sf_table_size", "sf_table_copy", "sf_kernel_launches",
            "sf_last_kernel_ms", "sf_vertex_amplitude_noalloc", "sf_plan_create", "sf_plan_autotune",
            "sf_plan_run", "sf_plan_graph_launch", "sf_plan_sync", "sf_plan_info", "sf_plan_free",
-           "sf_tables_free")
+           "sf_tables_free", "sf_check_dot2")
 
 
 class SfError(RuntimeError):
@@ -88,6 +88,7 @@ def _declare(lib):
                                         ctypes.POINTER(I64)]),
         "sf_plan_free": (None, [P]),
         "sf_tables_free": (None, [P]),
+        "sf_check_dot2": (ctypes.c_int, [I32, I32, I32, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -303,6 +304,23 @@ def sf_vertex_amplitude_noalloc(tables, out, shell_begin=0, shell_end=2 ** 63 - 
         assert o.dtype == torch.float64 and o.is_cuda and o.is_contiguous() and list(o.shape) == dim
     ptrs = (ctypes.c_void_p * len(out))(*[o.data_ptr() for o in out])
     _check(lib.sf_vertex_amplitude_noalloc(tables.ptr, int(shell_begin), int(shell_end), ptrs, _stream(stream)))
+    return out
+
+
+def check_dot2(kind, a, b, stream=None):
+    """Compensated-pair dot products on the device by the shell kernel's own steps (verification).
+
+    kind 0: a float32 [n, len, 2] (hi, lo) pairs, b float32 [n, len]; kind 1: both [n, len, 2].
+    Returns float32 [n, 2] (hi, lo) on the same device."""
+    import torch
+    lib = load()
+    a = a.contiguous()
+    b = b.contiguous()
+    assert a.dtype == torch.float32 and b.dtype == torch.float32 and a.is_cuda and b.is_cuda
+    n, ln = int(a.shape[0]), int(a.shape[1])
+    out = torch.empty((n, 2), dtype=torch.float32, device=a.device)
+    _check(lib.sf_check_dot2(int(kind), n, ln, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                             ctypes.c_void_p(out.data_ptr()), _stream(stream)))
     return out
 
 

@@ -71,7 +71,8 @@ struct sf_tables {
     bool have_rule = false;
     sf_quad_rule rule{};
     int nnodes = 0;
-    double *d_gl = nullptr, *d_x = nullptr, *d_w = nullptr, *d_r = nullptr, *d_W = nullptr;
+    const double* d_gl = nullptr;   // process-wide Gauss-Legendre library (not owned)
+    double *d_x = nullptr, *d_w = nullptr, *d_r = nullptr, *d_W = nullptr;
     double *d_Aj = nullptr, *d_Cj = nullptr;   // boundary-side 3j scratch (largest edge)
     // amplitude scratch (grown on demand)
     void* d_scratch = nullptr;
@@ -390,14 +391,14 @@ extern "C" int sf_boosters(sf_tables* t, const sf_quad_rule* q, cudaStream_t str
         return sf_set_error(SF_ERR_ARG, "bad quadrature rule");
     const int nnodes = q->n_panels * q->order;
     if (!t->have_rule || t->rule.n_panels != q->n_panels || t->rule.order != q->order || t->rule.r_max != q->r_max) {
-        if (!t->d_gl) SF_TRY(dev_alloc(t, (void**)&t->d_gl, 3 * 16864 * sizeof(double)));
+        if (!t->d_gl) SF_TRY(sf_gl_library(stream, &t->d_gl));
         if (nnodes > t->nnodes) {
             SF_TRY(dev_alloc(t, (void**)&t->d_x, nnodes * sizeof(double)));
             SF_TRY(dev_alloc(t, (void**)&t->d_w, nnodes * sizeof(double)));
             SF_TRY(dev_alloc(t, (void**)&t->d_r, nnodes * sizeof(double)));
             SF_TRY(dev_alloc(t, (void**)&t->d_W, nnodes * sizeof(double)));
         }
-        SF_TRY(sf_rule_build(q, t->d_gl, t->d_x, t->d_w, t->d_r, t->d_W, stream));
+        SF_TRY(sf_rule_build(q, t->d_x, t->d_w, t->d_r, t->d_W, stream));
         // d-tables are sized by the node count: reallocate for a different rule
         for (auto& h : t->vs)
             for (int f = 0; f < 10; f++) h.d_dtab[f] = nullptr;

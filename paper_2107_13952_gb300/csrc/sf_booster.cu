@@ -10,6 +10,7 @@
 //      B[i][k] = Re sum_m 4jm(j;m)^(i) 4jm(l;m)^(k) I(m).
 #include "sf_racah.cuh"
 #include <algorithm>
+#include <mutex>
 
 #define SF_PI 3.14159265358979323846
 
@@ -91,11 +92,35 @@ __global__ void k_rule_nodes(double r_max, int npan, int order, double* X, doubl
     Wm[n] = h * w * omx2 * omx2 / (16.0 * SF_PI * x * x * x);
 }
 
-int sf_rule_build(const sf_quad_rule* q, double* d_gl, double* d_x, double* d_w, double* d_r, double* d_W,
-                  cudaStream_t s) {
-    k_gl_library<<<(unsigned)((SF_GL_TOTAL + 255) / 256), 256, 0, s>>>(d_gl);
-    sf_note_launch(1);
-    SF_CUDA_TRY(cudaGetLastError());
+// The library does not depend on any argument, so it is built once per device, on the first
+// call that needs it, and kept until the process exits (0.4 MB per device).
+static std::mutex g_gl_mutex;
+static double* g_gl_lib[SF_MAX_DEVICES];
+
+int sf_gl_library(cudaStream_t s, const double** out) {
+    int dev = 0;
+    SF_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= SF_MAX_DEVICES) return sf_set_error(SF_ERR_LIMIT, "device ordinal %d beyond %d", dev, SF_MAX_DEVICES);
+    std::lock_guard<std::mutex> lock(g_gl_mutex);
+    if (!g_gl_lib[dev]) {
+        double* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, 3 * SF_GL_TOTAL * sizeof(double));
+        if (e != cudaSuccess) return sf_set_error(SF_ERR_OOM, "Gauss-Legendre library allocation failed: %s", cudaGetErrorString(e));
+        k_gl_library<<<(unsigned)((SF_GL_TOTAL + 255) / 256), 256, 0, s>>>(p);
+        sf_note_launch(1);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // complete before any other stream reads it
+        if (e != cudaSuccess) {
+            cudaFree(p);
+            return sf_set_error(SF_ERR_CUDA, "Gauss-Legendre library build failed: %s", cudaGetErrorString(e));
+        }
+        g_gl_lib[dev] = p;
+    }
+    *out = g_gl_lib[dev];
+    return SF_OK;
+}
+
+int sf_rule_build(const sf_quad_rule* q, double* d_x, double* d_w, double* d_r, double* d_W, cudaStream_t s) {
     int n = q->n_panels * q->order;
     k_rule_nodes<<<(n + 127) / 128, 128, 0, s>>>(q->r_max, q->n_panels, q->order, d_x, d_w, d_r, d_W);
     sf_note_launch(1);
@@ -106,10 +131,22 @@ int sf_rule_build(const sf_quad_rule* q, double* d_gl, double* d_x, double* d_w,
 // ---------------------------------------------------------------------------------------------
 // d-tables
 // ---------------------------------------------------------------------------------------------
+// Node count of the v-integral at rapidity r: the integrand oscillates as e^{i rho v} on
+// [-r, r] and its d-function factors carry polynomial degrees up to about (l + k)/2 in each of
+// t and 1 - t, so the count grows linearly in r with that band; at least 64 nodes.
 __device__ inline int sf_gl_count(double r, double rho, int tk, int tlmax) {
     double band = rho + 0.25 * (tlmax + tk) + 1.0;
     int N = (int)ceil((48.0 + r * band) / 32.0) * 32;
-    return N < 64 ? 64 : (N > 1024 ? 1024 : N);
+    return N < 64 ? 64 : N;
+}
+// The count is met by a composite rule: P equal panels of [-r, r], each with Np <= SF_GL_NMAX
+// library nodes (Np a multiple of 32, P Np >= N). P = 1 is the plain rule.
+__device__ inline void sf_gl_split(int N, int* P, int* Np) {
+    const int p = (N + SF_GL_NMAX - 1) / SF_GL_NMAX;
+    int n = (N + p - 1) / p;
+    n = ((n + 31) / 32) * 32;
+    *P = p;
+    *Np = n < 64 ? 64 : n;
 }
 
 __device__ inline double ipow_(double b, int e) {
@@ -160,21 +197,28 @@ __global__ void __launch_bounds__(SF_DT_NT) k_dtable(const __grid_constant__ Dta
         sqc = sqrt(c);
     }
     const int tlmax = tk + 2 * (nl - 1);
-    const int N = sf_gl_count(r, rho, tk, tlmax);
-    const int64_t go = sf_gl_offset(N);
+    int P = 1, Np = 64;
+    sf_gl_split(sf_gl_count(r, rho, tk, tlmax), &P, &Np);
+    const int64_t go = sf_gl_offset(Np);
     const double* gp = gl + go;
     const double* gm = gl + SF_GL_TOTAL + go;
     const double* gw = gl + 2 * SF_GL_TOTAL + go;
+    const double rp = r / P, wscale = 1.0 / P;
     for (int c0 = 0; c0 < nl; c0 += SF_DT_LCHUNK) {
         double are[SF_DT_LCHUNK], aim[SF_DT_LCHUNK];
 #pragma unroll
         for (int q = 0; q < SF_DT_LCHUNK; q++) { are[q] = 0.0; aim[q] = 0.0; }
-        for (int j = 0; j < N; j++) {
-            const double opx = gp[j], omx = gm[j], w = gw[j];
-            const double v = (opx <= omx) ? (-r + r * opx) : (r - r * omx);
+        for (int jj = 0; jj < P * Np; jj++) {
+            // panel pp covers 1 + xi in [2 pp / P, 2 (pp + 1) / P]; the distances of the node from
+            // both ends of [-r, r] are formed directly, so nothing cancels near either end
+            const int pp = jj / Np, j = jj - pp * Np;
+            const double opx = gp[j], omx = gm[j], w = gw[j] * wscale;
+            const double a1 = (P == 1) ? r * opx : rp * (2.0 * pp + opx);              // v + r
+            const double a2 = (P == 1) ? r * omx : rp * (2.0 * (P - 1 - pp) + omx);    // r - v
+            const double v = (a1 <= a2) ? (a1 - r) : (r - a2);
             const double ev = exp(v), emv = 1.0 / ev;
-            const double A = expm1(r * opx);   // e^{v+r} - 1
-            const double Bq = expm1(r * omx);  // e^{r-v} - 1
+            const double A = expm1(a1);   // e^{v+r} - 1
+            const double Bq = expm1(a2);  // e^{r-v} - 1
             const double t = fmin(1.0, emr * A / sh2), omt = fmin(1.0, ev * Bq / sh2);
             const double tr = fmin(1.0, emv * A / sh2), omtr = fmin(1.0, emr * Bq / sh2);
             const double dk = sqc * ipow_(sqrt(omt), kpm) * ipow_(sqrt(t), kmm);

@@ -19,6 +19,8 @@
 #define SF_RACAH_MAX 250       // every integer Racah argument (z+1, beta-z, ...) stays below 256
 #define SF_MAX_DL 40           // shells per face (dl+1) handled by one d-table pass set
 #define SF_DT_LCHUNK 12        // l values accumulated per d-table pass
+#define SF_GL_NMAX 1024        // largest Gauss-Legendre rule of the library (composite rules beyond)
+#define SF_MAX_DEVICES 128     // device ordinals with process-wide caches
 
 // ----------------------------------------------------------------------------------------------
 // error reporting (thread-local message, set by the host side of every entry point)
@@ -265,8 +267,10 @@ int sf_sixj_table_build(int table_id, const VtxDev* d_v, const SlotDesc* d_slots
 int sf_to_float(const double* d_in, float* d_out, int64_t n, int num_sms, cudaStream_t s);
 // (hi, lo) float pairs: hi = fl32(d), lo = fl32(d - hi)
 int sf_to_ff(const double* d_in, float2* d_out, int64_t n, int num_sms, cudaStream_t s);
-int sf_rule_build(const sf_quad_rule* q, double* d_gl, double* d_x, double* d_w, double* d_r, double* d_W,
-                  cudaStream_t s);
+// Gauss-Legendre library of the d-table kernel (sizes 64..SF_GL_NMAX in steps of 32), built once
+// per device and kept for the life of the process
+int sf_gl_library(cudaStream_t s, const double** out);
+int sf_rule_build(const sf_quad_rule* q, double* d_x, double* d_w, double* d_r, double* d_W, cudaStream_t s);
 // d-tables of the ten faces of one vertex (one launch): doubled boundary spins tk, l counts nl
 struct DtabFaces {
     int tk[10], nl[10];

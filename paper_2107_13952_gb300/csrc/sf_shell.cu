@@ -152,6 +152,41 @@ __device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
     return make_float2(h, l);
 }
 
+// Verification of the pair steps above on the device: n_dots dot products of length len with the
+// same step order as the kernel's contractions (k increasing, Dot2 accumulator, normalised at the
+// end). kind 0: pair x float (ff_dot_step, the S3 contraction); kind 1: pair x pair (ff_dot_step2,
+// the x-sum).
+__global__ void k_check_dot2(int kind, int n_dots, int len, const float2* __restrict__ a, const float* __restrict__ bf,
+                             const float2* __restrict__ bp, float2* __restrict__ out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_dots) return;
+    float sh = 0.0f, sl = 0.0f;
+    for (int k = 0; k < len; k++) {
+        const float2 x = a[(int64_t)q * len + k];
+        if (kind == 0) {
+            ff_dot_step(x.x, x.y, bf[(int64_t)q * len + k], sh, sl);
+        } else {
+            const float2 y = bp[(int64_t)q * len + k];
+            ff_dot_step2(x.x, x.y, y.x, y.y, sh, sl);
+        }
+    }
+    out[q] = ff_norm(sh, sl);
+}
+
+extern "C" int sf_check_dot2(int32_t kind, int32_t n_dots, int32_t len, const float* a, const float* b, float* out,
+                             cudaStream_t stream) {
+    if (kind != 0 && kind != 1) return sf_set_error(SF_ERR_ARG, "kind must be 0 (pair x float) or 1 (pair x pair)");
+    if (n_dots < 0 || len < 0 || (n_dots > 0 && (!a || !b || !out))) return sf_set_error(SF_ERR_ARG, "bad arguments");
+    if (n_dots == 0) return SF_OK;
+    k_check_dot2<<<(n_dots + 127) / 128, 128, 0, stream>>>(kind, n_dots, len, reinterpret_cast<const float2*>(a), b,
+                                                           reinterpret_cast<const float2*>(b),
+                                                           reinterpret_cast<float2*>(out));
+    sf_note_launch(1);
+    SF_CUDA_TRY(cudaGetLastError());
+    SF_CUDA_TRY(cudaStreamSynchronize(stream));
+    return SF_OK;
+}
+
 // floor(o / d) for 0 <= o < 2^31, 1 <= d: multiply by m = floor((2^32 - 1) / d), which
 // underestimates by at most one, then correct once
 struct FDiv { unsigned m; int d; };

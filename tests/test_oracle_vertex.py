@@ -25,6 +25,27 @@ def test_rule_integrates_polynomials():
         assert abs(s - ref) < 1e-30
 
 
+@pytest.mark.parametrize("r_max,n,order", [(40, 7, 6), (40, 40, 50), (12, 3, 4)])
+def test_rule_panel_geometry(r_max, n, order):
+    """Panel layout of Sec. 3 "Booster coefficients": the x-range is cut into n panels with
+    |I_k| = k |I_1|, the first (shortest) one at the x -> 0 end, so |I_1| = 2/(n(n+1)) of the
+    range. Written here from the paper's statement, not from the oracle: sorted by x, the k-th
+    run of `order` nodes must lie inside [x0 + |I_1| k(k-1)/2, x0 + |I_1| k(k+1)/2] and its
+    weights must add up to the panel length k |I_1| (a reversed or uniform partition fails)."""
+    xs, ws = quadrature.rule_nodes(r_max, n, order)
+    pairs = sorted(zip(xs, ws), key=lambda p: p[0])
+    x0 = mpmath.exp(-mpmath.mpf(r_max))
+    width = (1 - x0) * mpmath.mpf(2) / (n * (n + 1))
+    assert len(pairs) == n * order
+    for k in range(1, n + 1):
+        run = pairs[(k - 1) * order:k * order]
+        lo = x0 + width * k * (k - 1) / 2
+        hi = x0 + width * k * (k + 1) / 2
+        assert all(lo < x < hi for x, _ in run), k
+        assert abs(mpmath.fsum(w for _, w in run) - k * width) < mpmath.mpf(10) ** -35 * k * width
+    assert abs(x0 + width * n * (n + 1) / 2 - 1) < mpmath.mpf(10) ** -35
+
+
 @pytest.mark.parametrize("g", [0.5, 1.2])
 def test_booster_spin_zero_closed_form(g):
     """All spins 0: d_{000} = sin(g r)/(g sinh r), 4jm = 1, so
