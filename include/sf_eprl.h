@@ -58,11 +58,23 @@ extern "C" {
 #define SF_ERR_NUMERIC -6   /* a numerical self-check failed (e.g. non-real booster)              */
 #define SF_ERR_LIMIT   -7   /* spins or dimensions beyond the compiled limits                     */
 
-/* One vertex boundary (Sec. 3, framed algorithm step 1: ten spins and the number of shells). */
+/* One vertex boundary (Sec. 3, framed algorithm step 1: ten spins and the number of shells),
+ * with an optional reduced set of boundary intertwiners (the paper computes the vertex tensor for a
+ * reduced set of intertwiner indices when asked, Sec. 3 after the framed algorithm, and its
+ * interface offers a restricted intertwiner range, Sec. 4 "vertex_compute").
+ *   sub_first[e], sub_count[e]: the output covers intertwiners i_e = lo_e + 2 (sub_first[e] + n),
+ *     n = 0 .. sub_count[e] - 1, of edge e's range (lo_e, dim_e); sub_count[e] = 0 selects
+ *     everything from sub_first[e] to the end, so a zero-initialised struct means the whole
+ *     tensor. The output tensor of every amplitude call then has shape sub_count[0..4] (same
+ *     layout, i5 fastest) and equals the corresponding block of the whole tensor. Boosters keep
+ *     the whole intertwiner range. sub_first[e] < 0, beyond the range, or a count running past its
+ *     end is SF_ERR_ARG. The adjoint (sf_vertex_adjoint) needs the whole range. */
 typedef struct {
-    int32_t two_j[10];   /* doubled boundary spins, order above                                  */
-    double  gamma;       /* Barbero-Immirzi parameter; Y-map (rho, k) = (gamma (j+1), j)           */
-    int32_t dl;          /* shell cutoff Delta s: l_f in [j_f, j_f + dl]                          */
+    int32_t two_j[10];     /* doubled boundary spins, order above                                */
+    double  gamma;         /* Barbero-Immirzi parameter; Y-map (rho, k) = (gamma (j+1), j)         */
+    int32_t dl;            /* shell cutoff Delta s: l_f in [j_f, j_f + dl]                        */
+    int32_t sub_first[5];  /* first intertwiner index of the output per edge (0 = the range's lo) */
+    int32_t sub_count[5];  /* intertwiners per edge in the output (0 = through the range's end)   */
 } sf_vertex;
 
 /* Rapidity rule (Sec. 3 "Booster coefficients"): x = e^-r on [e^-r_max, 1] split into n_panels
@@ -97,8 +109,13 @@ const char* sf_version(void);
 const char* sf_last_error(void);
 
 /* Host helper (no device work): doubled lower bounds and dimensions of i_1..i_5
- * (framed algorithm step 2). Returns SF_ERR_EMPTY if a range is empty, SF_ERR_ARG on bad input. */
+ * (framed algorithm step 2), of the whole ranges: the sub-range fields of v are ignored.
+ * Returns SF_ERR_EMPTY if a range is empty, SF_ERR_ARG on bad input. */
 int sf_intertwiner_ranges(const sf_vertex* v, int32_t two_lo[5], int32_t dim[5]);
+
+/* Host helper: the output ranges of v (its sub-range applied): doubled lower bounds and counts,
+ * i.e. the shape of the tensors the amplitude calls write. SF_ERR_ARG for a bad sub-range. */
+int sf_output_ranges(const sf_vertex* v, int32_t two_lo[5], int32_t dim[5]);
 
 /* Host helper: number of shells (dl+1)^6 of a vertex, or a negative error code. */
 int64_t sf_num_shells(const sf_vertex* v);
@@ -131,12 +148,20 @@ int sf_boosters_download(const sf_tables* t, int32_t vertex, int32_t edge, doubl
  *   shell_begin, shell_end: linear shell range [begin, end) of every vertex (clamped to its shell
  *     count; pass 0 and INT64_MAX for all shells). Partial sums over disjoint ranges add up, so a
  *     long sum can be split or resumed.
- *   shell_list, n_list: optional host array of linear shell indices (single-vertex tables only);
+ *   shell_list, n_list: optional host or device array of linear shell indices (single-vertex tables only);
  *     when non-NULL it replaces the range. Duplicates count once.
- *   A_out: host array of n device pointers, A_out[v] -> prod_e dim_e doubles, overwritten.
+ *   A_out: host array of n device pointers, A_out[v] -> prod_e dim_e doubles, overwritten (dim_e
+ *     of the vertex's output ranges, sf_output_ranges).
+ *   kappa_out: optional (NULL to skip) host or device array of n doubles: kappa_out[v] =
+ *     sum over the selected non-empty shells s of ||C_s||_2, C_s the contribution of shell s to the
+ *     vertex's output tensor, prod sqrt(2i+1) included, in FP64 whatever the precision. Divided by
+ *     ||A_v||_2 it is the cancellation factor kappa of the shell sum, the scale of the mixed paths'
+ *     rounding errors (error ~ kappa times the FP32 unit roundoff). It costs one extra pass with
+ *     the shell sum unhoisted across shells (about a full framed-algorithm evaluation per shell,
+ *     several times the amplitude itself), so ask for it on shell lists or small ranges.
  * Uses library-owned scratch for per-block partial sums, reduced in a fixed order (deterministic). */
 int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t shell_begin, int64_t shell_end,
-                        const int64_t* shell_list, int64_t n_list, double* const* A_out,
+                        const int64_t* shell_list, int64_t n_list, double* const* A_out, double* kappa_out,
                         cudaStream_t stream);
 
 /* The FP64 shell sum of sf_vertex_amplitude (same tables, same range semantics, same output layout
@@ -232,9 +257,51 @@ void sf_plan_free(sf_plan* plan);
  *     derivative d a / d psi_e.
  *   grad_B[e-2] (optional): device, shape of the edge-e booster tensor, complex doubles:
  *     d a / d B_e[t][i][k] (zero on padded entries).
- * Precision: SF_FP64 only. */
-int sf_vertex_adjoint(sf_tables* t, const double* const psi[5], double* a_out,
+ * precision: SF_FP64 (the only value accepted: every step of the contraction and of its adjoint
+ *   runs in FP64; other values return SF_ERR_ARG). The tables must cover the whole intertwiner
+ *   range (no sub-range). With both grad_psi and grad_B NULL only a is computed. */
+int sf_vertex_adjoint(sf_tables* t, sf_precision precision, const double* const psi[5], double* a_out,
                       double* const grad_psi[5], double* const grad_B[4], cudaStream_t stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Vertex-tensor contractions (Sec. 3 "Tensor contractions", eq. vertex-contraction: vertex tensors
+ * are contracted with each other and with boundary states over their intertwiner indices; the
+ * paper times the complete contraction of two vertices and of one vertex with five boundary
+ * states on the GPU, Sec. 4 "Tensor contractions on CPU and GPU", fig. contractions).
+ * Tensors use the layout of the amplitude calls: A[i1][i2][i3][i4][i5], i5 fastest, FP64.
+ * ------------------------------------------------------------------------------------------- */
+
+/* Partial or complete contraction with boundary vectors over the trailing n_vec indices:
+ *   n_vec = 3: out[i1][i2] = sum_{i3 i4 i5} A psi_3[i3] psi_4[i4] psi_5[i5]   (D1 x D2 values)
+ *   n_vec = 4: out[i1]     = sum_{i2..i5} A psi_2 ... psi_5                    (D1 values)
+ *   n_vec = 5: out[0]      = sum_{i1..i5} A psi_1 ... psi_5                    (1 value)
+ * A: device, prod dim doubles. psi[e]: device, dim[e] complex doubles (interleaved re, im), read
+ * for e >= 5 - n_vec (others may be NULL). out: device complex doubles. dim: host, each 1..1024.
+ * FP64; every sum in a fixed order. Synchronises the stream. Errors: SF_ERR_ARG, SF_ERR_LIMIT
+ * (D3 D4 above 12,800), SF_ERR_CUDA, SF_ERR_OOM. */
+int sf_contract_vectors(const double* A, const int32_t dim[5], int32_t n_vec, const double* const psi[5],
+                        double* out, cudaStream_t stream);
+
+/* Complete contraction of two vertex tensors of n entries: *out = sum_i A[i] B[i] (FP64, fixed
+ * order). A, B: device, 16-byte aligned; out: device, one double. Synchronises the stream. */
+int sf_contract_vertices(const double* A, const double* B, int64_t n, double* out, cudaStream_t stream);
+
+/* The Delta_3 spin foam (three vertices joined pairwise by internal edges and sharing one
+ * internal face, Sec. 5 "The Delta_3 graph"): for each internal spin x the three vertices have
+ * equal tensors A_x (boundary spins (x, J, ..., J), so i1 and i2 run over the same internal range
+ * k = k_lo .. ) and each is contracted with three boundary vectors on (i3, i4, i5):
+ *   T_v[k][k'] = sum A_x[k][k'][i3][i4][i5] psi[3v][i3] psi[3v+1][i4] psi[3v+2][i5],  v = 0, 1, 2;
+ *   amps[x]  = (-1)^x (2x+1) sum_{k1 k2 k3} (-1)^(k1+k2+k3) T_0[k1][k2] T_2[k2][k3] T_1[k3][k1];
+ *   total    = sum_x amps[x]  (the amplitude of the graph, summed over the internal face's spin).
+ *   n_x: number of internal spins; A: host array of n_x device tensors; dims: host [n_x][5]
+ *   (dims[i][0] == dims[i][1]; dims[i][2..4] the same for every x); two_x, two_klo: host [n_x],
+ *   doubled x and lowest internal intertwiner (both integer spins); psi: host array of 9 device
+ *   vectors (complex doubles, lengths dims[.][2], dims[.][3], dims[.][4] in turn);
+ *   amps: device, n_x complex doubles; total: device, one complex double.
+ * FP64, fixed-order sums. Synchronises the stream. Errors: SF_ERR_ARG, SF_ERR_LIMIT, SF_ERR_CUDA. */
+int sf_delta3_amplitudes(int32_t n_x, const double* const* A, const int32_t* dims, const int32_t* two_x,
+                         const int32_t* two_klo, const double* const* psi, double* amps, double* total,
+                         cudaStream_t stream);
 
 /* Read-only access to internal tables for verification.
  *   kind SF_TAB_6J:    index 1..5 -> table S_index, all slots concatenated (doubles)

@@ -23,12 +23,13 @@ SF_FP64, SF_MIXED, SF_MIXED_FF = 0, 1, 2
 SF_TAB_6J, SF_TAB_6J_SLOTS, SF_TAB_D, SF_TAB_NODES = 1, 2, 3, 4
 
 # names of every symbol declared in include/sf_eprl.h
-EXPORTS = ("sf_version", "sf_last_error", "sf_intertwiner_ranges", "sf_num_shells", "sf_6j_table",
+EXPORTS = ("sf_version", "sf_last_error", "sf_intertwiner_ranges", "sf_output_ranges", "sf_num_shells", "sf_6j_table",
            "sf_boosters", "sf_booster_shape", "sf_boosters_upload", "sf_boosters_download",
            "sf_vertex_amplitude", "sf_vertex_adjoint", "sf_table_size", "sf_table_copy", "sf_kernel_launches",
            "sf_last_kernel_ms", "sf_vertex_amplitude_noalloc", "sf_plan_create", "sf_plan_autotune",
            "sf_plan_run", "sf_plan_graph_launch", "sf_plan_sync", "sf_plan_info", "sf_plan_free",
-           "sf_tables_free", "sf_check_dot2")
+           "sf_tables_free", "sf_check_dot2", "sf_contract_vectors", "sf_contract_vertices",
+           "sf_delta3_amplitudes")
 
 
 class SfError(RuntimeError):
@@ -38,7 +39,8 @@ class SfError(RuntimeError):
 
 
 class sf_vertex(ctypes.Structure):
-    _fields_ = [("two_j", ctypes.c_int32 * 10), ("gamma", ctypes.c_double), ("dl", ctypes.c_int32)]
+    _fields_ = [("two_j", ctypes.c_int32 * 10), ("gamma", ctypes.c_double), ("dl", ctypes.c_int32),
+                ("sub_first", ctypes.c_int32 * 5), ("sub_count", ctypes.c_int32 * 5)]
 
 
 class sf_quad_rule(ctypes.Structure):
@@ -50,12 +52,18 @@ class sf_tiling(ctypes.Structure):
                 ("i3_split", ctypes.c_int32)]
 
 
-def vertex(two_j, gamma, dl):
+def vertex(two_j, gamma, dl, sub=None):
+    """An ``sf_vertex``; ``sub`` (optional): five (first, count) pairs selecting a block of the
+    intertwiner ranges for the output (count 0 = through the end of the range)."""
     v = sf_vertex()
     for i, t in enumerate(two_j):
         v.two_j[i] = int(t)
     v.gamma = float(gamma)
     v.dl = int(dl)
+    if sub is not None:
+        for e, (f, c) in enumerate(sub):
+            v.sub_first[e] = int(f)
+            v.sub_count[e] = int(c)
     return v
 
 
@@ -65,14 +73,16 @@ def _declare(lib):
         "sf_version": (ctypes.c_char_p, []),
         "sf_last_error": (ctypes.c_char_p, []),
         "sf_intertwiner_ranges": (ctypes.c_int, [ctypes.POINTER(sf_vertex), ctypes.POINTER(I32), ctypes.POINTER(I32)]),
+        "sf_output_ranges": (ctypes.c_int, [ctypes.POINTER(sf_vertex), ctypes.POINTER(I32), ctypes.POINTER(I32)]),
         "sf_num_shells": (I64, [ctypes.POINTER(sf_vertex)]),
         "sf_6j_table": (ctypes.c_int, [ctypes.POINTER(sf_vertex), I32, ctypes.POINTER(P), P]),
         "sf_boosters": (ctypes.c_int, [P, ctypes.POINTER(sf_quad_rule), P]),
         "sf_booster_shape": (ctypes.c_int, [P, I32, I32, ctypes.POINTER(I64)]),
         "sf_boosters_upload": (ctypes.c_int, [P, I32, I32, P, P]),
         "sf_boosters_download": (ctypes.c_int, [P, I32, I32, P, P]),
-        "sf_vertex_amplitude": (ctypes.c_int, [P, ctypes.c_int, I64, I64, P, I64, ctypes.POINTER(P), P]),
-        "sf_vertex_adjoint": (ctypes.c_int, [P, ctypes.POINTER(P), P, ctypes.POINTER(P), ctypes.POINTER(P), P]),
+        "sf_vertex_amplitude": (ctypes.c_int, [P, ctypes.c_int, I64, I64, P, I64, ctypes.POINTER(P), P, P]),
+        "sf_vertex_adjoint": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(P), P, ctypes.POINTER(P), ctypes.POINTER(P),
+                                             P]),
         "sf_table_size": (I64, [P, I32, I32, I32]),
         "sf_table_copy": (ctypes.c_int, [P, I32, I32, I32, P, I64, P]),
         "sf_kernel_launches": (I64, []),
@@ -89,6 +99,10 @@ def _declare(lib):
         "sf_plan_free": (None, [P]),
         "sf_tables_free": (None, [P]),
         "sf_check_dot2": (ctypes.c_int, [I32, I32, I32, P, P, P, P]),
+        "sf_contract_vectors": (ctypes.c_int, [P, ctypes.POINTER(I32), I32, ctypes.POINTER(P), P, P]),
+        "sf_contract_vertices": (ctypes.c_int, [P, P, I64, P, P]),
+        "sf_delta3_amplitudes": (ctypes.c_int, [I32, ctypes.POINTER(P), ctypes.POINTER(I32), ctypes.POINTER(I32),
+                                                ctypes.POINTER(I32), ctypes.POINTER(P), P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -131,6 +145,15 @@ def intertwiner_ranges(two_j, gamma=1.2, dl=0):
     return list(lo), list(dim)
 
 
+def output_ranges(v):
+    """(two_lo[5], dim[5]) of the tensors written for the ``sf_vertex`` v (its sub-range applied)."""
+    lib = load()
+    lo = (ctypes.c_int32 * 5)()
+    dim = (ctypes.c_int32 * 5)()
+    _check(lib.sf_output_ranges(ctypes.byref(v), lo, dim))
+    return list(lo), list(dim)
+
+
 def num_shells(two_j, gamma=1.2, dl=0):
     lib = load()
     v = vertex(two_j, gamma, dl)
@@ -153,9 +176,8 @@ class Tables:
             self.ptr = None
 
     def dims(self, vtx=0):
-        v = self.vertices[vtx]
-        lo, dim = intertwiner_ranges(list(v.two_j), v.gamma, v.dl)
-        return lo, dim
+        """Output ranges (two_lo, dim) of vertex ``vtx`` (its sub-range applied)."""
+        return output_ranges(self.vertices[vtx])
 
 
 def sf_6j_table(vertices, stream=None):
@@ -200,17 +222,19 @@ def sf_boosters_upload(tables, vtx, edge, B, stream=None):
 
 
 def sf_vertex_amplitude(tables, precision=SF_FP64, shell_begin=0, shell_end=2 ** 63 - 1, shell_list=None,
-                        out=None, stream=None):
+                        out=None, stream=None, kappa=False):
     """Vertex tensors A[i1][i2][i3][i4][i5] (float64, cuda), one per vertex of ``tables``.
 
     precision: SF_FP64 (every step in FP64), SF_MIXED (booster contractions over k2, k3, k4 in
     FP32) or SF_MIXED_FF (the same, with the {6j} contractions in compensated FP32 pairs); both
-    mixed paths stay within 1e-6 (normwise, relative) of the FP64 result."""
+    mixed paths stay within 1e-6 (normwise, relative) of the FP64 result.
+    With ``kappa`` True returns (tensors, sums) where sums[v] = sum_s ||C_s||_2 over the selected
+    non-empty shells (one extra, unhoisted FP64 pass)."""
     import torch
     lib = load()
     outs = []
     for i, v in enumerate(tables.vertices):
-        _, dim = intertwiner_ranges(list(v.two_j), v.gamma, v.dl)
+        _, dim = output_ranges(v)
         if out is not None:
             o = out[i]
             assert o.dtype == torch.float64 and o.is_cuda and o.is_contiguous() and list(o.shape) == dim
@@ -225,8 +249,13 @@ def sf_vertex_amplitude(tables, precision=SF_FP64, shell_begin=0, shell_end=2 **
         if keep.device.type != "cuda":
             keep = keep.cuda()
         lp, nl = ctypes.c_void_p(keep.data_ptr()), int(keep.numel())
+    kap = None
+    if kappa:
+        kap = torch.zeros(len(outs), dtype=torch.float64, device="cuda")
     _check(lib.sf_vertex_amplitude(tables.ptr, int(precision), int(shell_begin), int(shell_end), lp, nl, ptrs,
-                                   _stream(stream)))
+                                   ctypes.c_void_p(kap.data_ptr()) if kap is not None else None, _stream(stream)))
+    if kappa:
+        return outs, [float(v) for v in kap.cpu()]
     return outs
 
 
@@ -241,7 +270,7 @@ class Plan:
         self.tables = tables
         self.outputs = []
         for v in tables.vertices:
-            _, dim = intertwiner_ranges(list(v.two_j), v.gamma, v.dl)
+            _, dim = output_ranges(v)
             self.outputs.append(torch.empty(dim, dtype=torch.float64, device="cuda"))
         ptrs = (ctypes.c_void_p * len(self.outputs))(*[o.data_ptr() for o in self.outputs])
         tl = sf_tiling(*(tuple(tiling or ()) + (0, 0, 0, 0))[:4])
@@ -299,7 +328,7 @@ def sf_vertex_amplitude_noalloc(tables, out, shell_begin=0, shell_end=2 ** 63 - 
     import torch
     lib = load()
     for i, v in enumerate(tables.vertices):
-        _, dim = intertwiner_ranges(list(v.two_j), v.gamma, v.dl)
+        _, dim = output_ranges(v)
         o = out[i]
         assert o.dtype == torch.float64 and o.is_cuda and o.is_contiguous() and list(o.shape) == dim
     ptrs = (ctypes.c_void_p * len(out))(*[o.data_ptr() for o in out])
@@ -324,6 +353,68 @@ def check_dot2(kind, a, b, stream=None):
     return out
 
 
+def _cplx(v, n):
+    import torch
+    v = torch.as_tensor(v).to(device="cuda", dtype=torch.complex128).contiguous()
+    assert v.numel() == n, (v.numel(), n)
+    return v
+
+
+def contract_vectors(A, psis, stream=None):
+    """Contract the vertex tensor A (cuda float64 [D1..D5]) with complex boundary vectors over its
+    trailing len(psis) in {3, 4, 5} indices (psis[0] pairs with index 5 - len(psis)); returns the
+    complex128 result on cuda: shape [D1, D2], [D1] or [] (Sec. 3, eq. vertex-contraction)."""
+    import torch
+    lib = load()
+    assert A.dtype == torch.float64 and A.is_cuda and A.is_contiguous() and A.dim() == 5
+    dims = list(A.shape)
+    nv = len(psis)
+    first = 5 - nv
+    vs = [None] * first + [_cplx(p, dims[first + q]) for q, p in enumerate(psis)]
+    ptrs = (ctypes.c_void_p * 5)(*[(v.data_ptr() if v is not None else None) for v in vs])
+    shape = [[dims[0], dims[1]], [dims[0]], []][nv - 3]
+    out = torch.empty(shape, dtype=torch.complex128, device="cuda")
+    d = (ctypes.c_int32 * 5)(*dims)
+    _check(lib.sf_contract_vectors(ctypes.c_void_p(A.data_ptr()), d, nv, ptrs, ctypes.c_void_p(out.data_ptr()),
+                                   _stream(stream)))
+    return out
+
+
+def contract_vertices(A, B, stream=None):
+    """sum_i A[i] B[i] of two vertex tensors of equal shape (cuda float64); a cuda float64 scalar."""
+    import torch
+    lib = load()
+    assert A.shape == B.shape and A.dtype == B.dtype == torch.float64 and A.is_contiguous() and B.is_contiguous()
+    out = torch.empty((), dtype=torch.float64, device="cuda")
+    _check(lib.sf_contract_vertices(ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()), A.numel(),
+                                    ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def delta3_amplitudes(tensors, two_x, two_klo, psis, stream=None):
+    """Delta_3 amplitudes per internal spin and their sum (Sec. 5): ``tensors`` the vertex tensors
+    A_x (cuda float64, one per x), ``two_x``/``two_klo`` their doubled internal spins and lowest
+    internal intertwiners, ``psis`` nine boundary vectors (three per vertex, on i3, i4, i5).
+    Returns (amps [n_x] complex128, total complex128 scalar), both on cuda."""
+    import torch
+    lib = load()
+    n = len(tensors)
+    dims = []
+    for A in tensors:
+        assert A.dtype == torch.float64 and A.is_cuda and A.is_contiguous() and A.dim() == 5
+        dims += list(A.shape)
+    bd = list(tensors[0].shape[2:]) * 3
+    vs = [_cplx(p, bd[q]) for q, p in enumerate(psis)]
+    amps = torch.empty(n, dtype=torch.complex128, device="cuda")
+    total = torch.empty((), dtype=torch.complex128, device="cuda")
+    _check(lib.sf_delta3_amplitudes(n, (ctypes.c_void_p * n)(*[A.data_ptr() for A in tensors]),
+                                    (ctypes.c_int32 * (5 * n))(*dims), (ctypes.c_int32 * n)(*two_x),
+                                    (ctypes.c_int32 * n)(*two_klo), (ctypes.c_void_p * 9)(*[v.data_ptr() for v in vs]),
+                                    ctypes.c_void_p(amps.data_ptr()), ctypes.c_void_p(total.data_ptr()),
+                                    _stream(stream)))
+    return amps, total
+
+
 def table_copy(tables, vtx, kind, index, stream=None):
     """Copy an internal table to a CPU torch tensor (verification only)."""
     import torch
@@ -343,8 +434,9 @@ def table_copy(tables, vtx, kind, index, stream=None):
     return out
 
 
-def sf_vertex_adjoint(tables, psis, want_grads=True, stream=None):
-    """(a, [d a/d psi_e], [d a/d B_e]) for complex boundary vectors psis (cuda complex128)."""
+def sf_vertex_adjoint(tables, psis, want_grads=True, precision=SF_FP64, stream=None):
+    """(a, [d a/d psi_e], [d a/d B_e]) for complex boundary vectors psis (cuda complex128); with
+    ``want_grads`` False only a is computed (the gradient lists are empty)."""
     import torch
     lib = load()
     psis = [torch.as_tensor(p, dtype=torch.complex128).contiguous().cuda() for p in psis]
@@ -357,7 +449,8 @@ def sf_vertex_adjoint(tables, psis, want_grads=True, stream=None):
         gbs = [torch.zeros(booster_shape(tables, 0, e), dtype=torch.complex128, device="cuda") for e in (2, 3, 4, 5)]
         gp = (ctypes.c_void_p * 5)(*[g.data_ptr() for g in gps])
         gb = (ctypes.c_void_p * 4)(*[g.data_ptr() for g in gbs])
-    _check(lib.sf_vertex_adjoint(tables.ptr, pp, ctypes.c_void_p(a.data_ptr()), gp, gb, _stream(stream)))
+    _check(lib.sf_vertex_adjoint(tables.ptr, int(precision), pp, ctypes.c_void_p(a.data_ptr()), gp, gb,
+                                 _stream(stream)))
     return a[0], gps, gbs
 
 
@@ -383,8 +476,12 @@ def _contraction_function():
             for e, B in zip((2, 3, 4, 5), (B2, B3, B4, B5)):
                 sf_boosters_upload(tables, 0, e, B.detach())
             psis = [p.detach() for p in (psi1, psi2, psi3, psi4, psi5)]
-            a, gpsi, gB = sf_vertex_adjoint(tables, psis, want_grads=True)
-            ctx.save_for_backward(*gpsi, *gB)
+            # the gradients come from the same kernels as a; skip them when nothing needs them
+            need = any(ctx.needs_input_grad[1:])
+            a, gpsi, gB = sf_vertex_adjoint(tables, psis, want_grads=need)
+            ctx.has_grads = need
+            if need:
+                ctx.save_for_backward(*gpsi, *gB)
             return a.clone()
 
         @staticmethod

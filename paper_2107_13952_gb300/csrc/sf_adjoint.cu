@@ -47,7 +47,8 @@ __device__ __forceinline__ void wmat(int DM, int nr, int nm, int nc, const cplx*
 // shared memory per warp: 14 matrices DM x DM, node weights [5][DM], derivative sums [5][DM]
 __global__ void __launch_bounds__(32 * SF_ADJ_WARPS) k_adjoint_shell(const VtxDev* __restrict__ vp, const cplx* __restrict__ phi1,
                                                                        const cplx* __restrict__ psi_all, int64_t nshell,
-                                                                       int stride_node, int DM, cplx* __restrict__ out) {
+                                                                       int stride_node, int DM, int want_nodes,
+                                                                       cplx* __restrict__ out) {
     extern __shared__ __align__(16) unsigned char adj_smem[];
     const VtxDev& v = *vp;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -152,6 +153,25 @@ __global__ void __launch_bounds__(32 * SF_ADJ_WARPS) k_adjoint_shell(const VtxDe
             wmat(DM, nd[0], nd[1], nd[2], M[0], M[1], M[10], lane);
             wmat(DM, nd[0], nd[2], nd[3], M[10], M[2], M[11], lane);
             wmat(DM, nd[0], nd[3], nd[4], M[11], M[3], M[12], lane);
+            if (!want_nodes) {
+                // the amplitude alone: a_x = tr(P4 M4) = sum_c sum_r P4[c][r] M4[r][c]
+                const double wx = sig * (double)(x + 1);
+                cplx part{0.0, 0.0};
+                for (int c = lane; c < nd[0]; c += 32) {
+                    cplx acc{0.0, 0.0};
+                    for (int r = 0; r < nd[4]; r++) acc = cfma(M[12][c * DM + r], M[4][r * DM + c], acc);
+                    part.x += wx * acc.x;
+                    part.y += wx * acc.y;
+                }
+                for (int off = 16; off > 0; off >>= 1) {
+                    part.x += __shfl_xor_sync(0xffffffffu, part.x, off);
+                    part.y += __shfl_xor_sync(0xffffffffu, part.y, off);
+                }
+                aval.x += part.x;
+                aval.y += part.y;
+                __syncwarp();
+                continue;
+            }
             // suffixes without the starting node's weight: R4 = L4 (node 4 -> node 0);
             // R3 = L3 M4, R2 = L2 M3 M4, R1 = L1 M2 M3 M4, R0 = L0 M1 M2 M3 M4. Q = M_n R_{n} reused.
             // R4 in M[9]; Q4 = M[4] (= W4 L4). R3 = L3 Q4 -> M[13]
@@ -224,7 +244,8 @@ __global__ void __launch_bounds__(32 * SF_ADJ_WARPS) k_adjoint_shell(const VtxDe
             __syncwarp();
         }
         if (lane == 0) o[0] = aval;
-        for (int n = 0; n < 5; n++)
+        if (want_nodes)
+            for (int n = 0; n < 5; n++)
             for (int c = lane; c < stride_node; c += 32)
                 o[1 + n * stride_node + c] = (c < nd[n]) ? sdp[n * DM + c] : cplx{0.0, 0.0};
         __syncwarp();
@@ -379,11 +400,12 @@ int sf_adjoint_launch(const VtxDev* d_v, const VtxDev& h, const double* const ps
     if (blocks > (int64_t)num_sms * 64) blocks = (int64_t)num_sms * 64;
     const size_t smem = (size_t)SF_ADJ_WARPS * (14 * mx * mx + 10 * mx) * sizeof(cplx);
     SF_CUDA_TRY(cudaFuncSetAttribute(k_adjoint_shell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int want_nodes = (grad_psi || grad_B) ? 1 : 0;
     k_adjoint_shell<<<(unsigned)blocks, 32 * SF_ADJ_WARPS, smem, s>>>(d_v, phi1, psi_all, h.nshell, stride_node, mx,
-                                                                       shell_out);
+                                                                       want_nodes, shell_out);
     sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
-    for (int e = 0; e < 4; e++) {
+    for (int e = 0; e < 4 && want_nodes; e++) {
         cplx* gB = grad_B ? (cplx*)grad_B[e] : nullptr;   // optional: the psi gradients only need P
         k_adjoint_triples<<<(unsigned)h.ntrip, 64, 0, s>>>(d_v, e + 2, psi_all, shell_out, stride_node, gB,
                                                            P + (int64_t)e * h.ntrip * 32);

@@ -42,6 +42,7 @@ struct VertexHost {
     sf_vertex v;
     int D = 0;
     int32_t ilo[5], di[5];
+    int32_t olo[5], od[5];   // output sub-range: first index within each range and count
     int64_t nshell = 0;
     Table6j S[5];
     float* d_S4f = nullptr;
@@ -111,6 +112,31 @@ static void ranges_of(const sf_vertex* v, int32_t lo[5], int32_t n[5]) {
     sf_pair_range(j[F34], j[F35], j[F13], j[F23], &lo[2], &n[2]);
     sf_pair_range(j[F45], j[F14], j[F24], j[F34], &lo[3], &n[3]);
     sf_pair_range(j[F15], j[F25], j[F35], j[F45], &lo[4], &n[4]);
+}
+
+// output sub-range of a vertex (first index, count) within its ranges n[5]
+static int sub_range_of(const sf_vertex* v, const int32_t n[5], int32_t first[5], int32_t count[5]) {
+    for (int e = 0; e < 5; e++) {
+        const int f = v->sub_first[e], c = v->sub_count[e];
+        if (f < 0 || c < 0 || f >= n[e] || (c > 0 && f + c > n[e]))
+            return sf_set_error(SF_ERR_ARG, "sub-range of edge %d (first %d, count %d) outside its %d intertwiners",
+                                e + 1, f, c, n[e]);
+        first[e] = f;
+        count[e] = c > 0 ? c : n[e] - f;
+    }
+    return SF_OK;
+}
+
+extern "C" int sf_output_ranges(const sf_vertex* v, int32_t two_lo[5], int32_t dim[5]) {
+    int32_t lo[5], n[5], f[5], c[5];
+    SF_TRY(sf_intertwiner_ranges(v, lo, n));
+    if (!two_lo || !dim) return sf_set_error(SF_ERR_ARG, "null output");
+    SF_TRY(sub_range_of(v, n, f, c));
+    for (int e = 0; e < 5; e++) {
+        two_lo[e] = lo[e] + 2 * f[e];
+        dim[e] = c[e];
+    }
+    return SF_OK;
 }
 
 extern "C" int sf_intertwiner_ranges(const sf_vertex* v, int32_t two_lo[5], int32_t dim[5]) {
@@ -259,7 +285,7 @@ static int upload_vtxdev(sf_tables* t) {
         d.gamma = h.v.gamma;
         d.dl = h.v.dl;
         d.D = h.D;
-        for (int e = 0; e < 5; e++) { d.ilo[e] = h.ilo[e]; d.di[e] = h.di[e]; }
+        for (int e = 0; e < 5; e++) { d.ilo[e] = h.ilo[e]; d.di[e] = h.di[e]; d.olo[e] = h.olo[e]; d.od[e] = h.od[e]; }
         d.nshell = h.nshell;
         for (int k = 0; k < 5; k++) { d.S[k] = h.S[k].d_vals; d.slot[k] = h.S[k].d_slots; }
         d.S4f = h.d_S4f;
@@ -306,6 +332,10 @@ extern "C" int sf_6j_table(const sf_vertex* v, int32_t n, sf_tables** out, cudaS
         ranges_of(&v[i], lo, dim);
         for (int e = 0; e < 5; e++)
             if (dim[e] == 0) return sf_set_error(SF_ERR_EMPTY, "vertex %d: intertwiner range of edge %d is empty", i, e + 1);
+        {
+            int32_t f[5], c[5];
+            SF_TRY(sub_range_of(&v[i], dim, f, c));
+        }
         // integer Racah arguments and factorials stay within the compiled widths
         int maxl = 0;
         for (int f = 0; f < 10; f++) maxl = std::max(maxl, v[i].two_j[f] + (f > F15 ? 2 * v[i].dl : 0));
@@ -323,6 +353,7 @@ extern "C" int sf_6j_table(const sf_vertex* v, int32_t n, sf_tables** out, cudaS
             h.v = v[i];
             h.D = v[i].dl + 1;
             ranges_of(&v[i], h.ilo, h.di);
+            sub_range_of(&v[i], h.di, h.olo, h.od);   // validated above
             h.nshell = (int64_t)h.D * h.D * h.D * h.D * h.D * h.D;
             h.ngroups = (int64_t)h.D * h.D * h.D;
             plan_6j(h);
@@ -514,11 +545,11 @@ struct ShellDims {
 static ShellDims shell_dims(const sf_tables* t) {
     ShellDims d;
     for (const VertexHost& h : t->vs) {
-        for (int e = 2; e < 5; e++) d.mdi = std::max(d.mdi, (int)h.di[e]);
+        for (int e = 2; e < 5; e++) d.mdi = std::max(d.mdi, (int)h.od[e]);
         for (int e = 0; e < 4; e++) d.mdk = std::max(d.mdk, (int)h.dkmax[e]);
         d.mk3u = std::max(d.mk3u, h.mk3u);
         d.Dmax = std::max(d.Dmax, h.D);
-        d.mdi3 = std::max(d.mdi3, (int)h.di[2]);
+        d.mdi3 = std::max(d.mdi3, (int)h.od[2]);
     }
     return d;
 }
@@ -528,8 +559,8 @@ static size_t shell_smem_limit(int nt) { return nt == 256 ? 109 * 1024 : 200 * 1
 // the register-resident output tile (blocks of 2 i5 x 4 i3 per i4) fits SF_TRT blocks per thread
 static bool shell_tile_fits(const sf_tables* t, int nt, int split) {
     for (const VertexHost& h : t->vs) {
-        const int ni3 = (h.di[2] + split - 1) / split;
-        if ((int64_t)h.di[3] * ((h.di[4] + 1) / 2) * ((ni3 + 3) / 4) > 2 * (int64_t)nt) return false;
+        const int ni3 = (h.od[2] + split - 1) / split;
+        if ((int64_t)h.od[3] * ((h.od[4] + 1) / 2) * ((ni3 + 3) / 4) > 2 * (int64_t)nt) return false;
     }
     return true;
 }
@@ -610,10 +641,10 @@ static int schedule_shells(const sf_tables* t, bool whole_range, int64_t shell_b
         }
         g_lo[i] = lo;
         g_n[i] = std::max<int64_t>(hi - lo, 0);
-        ns[i] = std::min(cfg.split, (int)h.di[2]);
-        double dmax = std::max(std::max(h.di[2], h.di[3]), h.di[4]);
+        ns[i] = std::min(cfg.split, (int)h.od[2]);
+        double dmax = std::max(std::max(h.od[2], h.od[3]), h.od[4]);
         item_cost_v[i] = (double)g_n[i] * per_group * dmax * dmax * dmax * dmax / ns[i];
-        total_cost += item_cost_v[i] * h.di[0] * h.di[1] * ns[i];
+        total_cost += item_cost_v[i] * h.od[0] * h.od[1] * ns[i];
     }
     const double item_cost = std::max(1.0, total_cost / ((double)t->num_sms * std::max(1, cfg.items_per_sm)));
     std::vector<int> order(nv);
@@ -622,7 +653,7 @@ static int schedule_shells(const sf_tables* t, bool whole_range, int64_t shell_b
     std::vector<int> item0(nv), nchunk(nv);
     for (int i : order) {
         const VertexHost& h = t->vs[i];
-        const int64_t ntile = (int64_t)h.di[0] * h.di[1];
+        const int64_t ntile = (int64_t)h.od[0] * h.od[1];
         const int64_t ng = g_n[i];
         int C = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(ng, 1),
                                                             (int64_t)std::ceil(item_cost_v[i] / item_cost)));
@@ -633,14 +664,14 @@ static int schedule_shells(const sf_tables* t, bool whole_range, int64_t shell_b
                 for (int hp = 0; hp < ns[i]; hp++) {
                     WorkItem w{};
                     w.vtx = i;
-                    w.i1 = (int)(tile / h.di[1]);
-                    w.i2 = (int)(tile % h.di[1]);
+                    w.i1 = (int)(h.olo[0] + tile / h.od[1]);
+                    w.i2 = (int)(h.olo[1] + tile % h.od[1]);
                     w.g0 = (int)(g_lo[i] + ng * c / C);
                     w.g1 = (int)(g_lo[i] + ng * (c + 1) / C);
-                    w.i3b = (int16_t)(h.di[2] * hp / ns[i]);
-                    w.ni3 = (int16_t)(h.di[2] * (hp + 1) / ns[i] - w.i3b);
+                    w.i3b = (int16_t)(h.olo[2] + h.od[2] * hp / ns[i]);
+                    w.ni3 = (int16_t)(h.olo[2] + h.od[2] * (hp + 1) / ns[i] - w.i3b);
                     w.part_off = sc->part_total;
-                    sc->part_total += (int64_t)w.ni3 * h.di[3] * h.di[4];
+                    sc->part_total += (int64_t)w.ni3 * h.od[3] * h.od[4];
                     sc->items.push_back(w);
                 }
             }
@@ -653,18 +684,18 @@ static int schedule_shells(const sf_tables* t, bool whole_range, int64_t shell_b
     sc->mni3 = (sc->dims.mdi3 + cfg.split - 1) / cfg.split;
     for (int i = 0; i < nv; i++) {
         const VertexHost& h = t->vs[i];
-        const int64_t n3 = (int64_t)h.di[2] * h.di[3] * h.di[4];
-        for (int tile = 0; tile < h.di[0] * h.di[1]; tile++) {
+        const int64_t n3 = (int64_t)h.od[2] * h.od[3] * h.od[4];
+        for (int tile = 0; tile < h.od[0] * h.od[1]; tile++) {
             for (int hp = 0; hp < ns[i]; hp++) {
                 ReduceJob j{};
                 j.vtx = i;
                 j.tile = tile;
                 j.item0 = item0[i] + tile * ns[i] + hp;
                 j.nchunk = nchunk[i];
-                j.stride = h.di[0] * h.di[1] * ns[i];
-                j.i3b = h.di[2] * hp / ns[i];
-                j.ni3 = h.di[2] * (hp + 1) / ns[i] - j.i3b;
-                j.A = A_out[i] + tile * n3 + (int64_t)j.i3b * h.di[3] * h.di[4];
+                j.stride = h.od[0] * h.od[1] * ns[i];
+                j.i3b = h.olo[2] + h.od[2] * hp / ns[i];
+                j.ni3 = h.olo[2] + h.od[2] * (hp + 1) / ns[i] - j.i3b;
+                j.A = A_out[i] + tile * n3 + (int64_t)(j.i3b - h.olo[2]) * h.od[3] * h.od[4];
                 sc->jobs.push_back(j);
             }
         }
@@ -672,8 +703,132 @@ static int schedule_shells(const sf_tables* t, bool whole_range, int64_t shell_b
     return SF_OK;
 }
 
+// per-shell norms of the kappa pass: for each shell q of a batch, the square root of the sum of its
+// items' squared tile norms (nper consecutive items per shell), summed in item order
+__global__ void k_kappa_shells(const double* __restrict__ q2, int64_t nshells, int nper, double* __restrict__ out) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nshells) return;
+    double s = 0.0;
+    for (int c = 0; c < nper; c++) s += q2[q * nper + c];
+    out[q] = sqrt(s);
+}
+
+// kappa_out[v] = sum over the selected non-empty shells s of ||C_s||_2 (FP64): one work item per
+// (shell, output tile, i3 piece) restricted to that shell, in batches of at most KAPPA_BATCH items
+#define KAPPA_BATCH (1 << 21)
+static int kappa_pass(sf_tables* t, const int64_t* shell_list, int64_t n_list, int64_t shell_begin, int64_t shell_end,
+                      ShellFilter filt, double* kappa_out, cudaStream_t stream) {
+    ShellConfig cfg;
+    SF_TRY(shell_config(t, 0, sf_tiling{}, &cfg));
+    const ShellDims dm = shell_dims(t);
+    const int mni3 = (dm.mdi3 + cfg.split - 1) / cfg.split;
+    std::vector<int64_t> list;
+    if (shell_list) {
+        // the list may be host or device memory (the shell-sum pass copies it the same way)
+        list.resize((size_t)n_list);
+        if (n_list > 0)
+            SF_CUDA_TRY(cudaMemcpy(list.data(), shell_list, (size_t)n_list * sizeof(int64_t), cudaMemcpyDefault));
+        std::sort(list.begin(), list.end());
+        list.erase(std::unique(list.begin(), list.end()), list.end());
+    }
+    const size_t o_q2 = align256((size_t)KAPPA_BATCH * sizeof(WorkItem));
+    const size_t o_norm = align256(o_q2 + (size_t)KAPPA_BATCH * sizeof(double));
+    const size_t o_counter = align256(o_norm + (size_t)KAPPA_BATCH * sizeof(double));
+    const size_t need = o_counter + 256;
+    void* buf = nullptr;
+    {
+        cudaError_t e = cudaMalloc(&buf, need);
+        if (e != cudaSuccess) return sf_set_error(SF_ERR_OOM, "kappa pass: %zu bytes of scratch: %s", need, cudaGetErrorString(e));
+    }
+    WorkItem* d_items = (WorkItem*)buf;
+    double* d_q2 = (double*)((char*)buf + o_q2);
+    double* d_norm = (double*)((char*)buf + o_norm);
+    int* d_counter = (int*)((char*)buf + o_counter);
+    int grid = 0;
+    size_t smem = 0;
+    int rc = sf_shell_prepare(0, cfg.nt, dm.mdi, dm.mdk, dm.mk3u, cfg.xc, dm.Dmax, mni3, KAPPA_BATCH, t->num_sms, &grid, &smem);
+    std::vector<double> kap(t->vs.size(), 0.0);
+    std::vector<WorkItem> items;
+    std::vector<double> norms;
+    items.reserve(KAPPA_BATCH);
+    for (size_t vi = 0; vi < t->vs.size() && rc == SF_OK; vi++) {
+        const VertexHost& h = t->vs[vi];
+        const int D = h.D;
+        const int32_t* j = h.v.two_j;
+        const int ns = std::min(cfg.split, (int)h.od[2]);
+        const int nper = h.od[0] * h.od[1] * ns;
+        int64_t nsel = 0;
+        auto flush = [&]() -> int {
+            if (items.empty()) return SF_OK;
+            const int64_t nsh = (int64_t)items.size() / nper;
+            SF_CUDA_TRY(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, stream));
+            const int g = std::min<int>(grid, (int)items.size());
+            SF_TRY(sf_shell_launch_prepared(0, cfg.nt, g, smem, t->d_vtx, dm.mdi, dm.mdk, dm.mk3u, cfg.xc, dm.Dmax, mni3,
+                                            d_items, (int)items.size(), d_counter, d_q2, filt, stream));
+            k_kappa_shells<<<(unsigned)((nsh + 127) / 128), 128, 0, stream>>>(d_q2, nsh, nper, d_norm);
+            sf_note_launch(1);
+            SF_CUDA_TRY(cudaGetLastError());
+            norms.resize(nsh);
+            SF_CUDA_TRY(cudaMemcpyAsync(norms.data(), d_norm, nsh * sizeof(double), cudaMemcpyDeviceToHost, stream));
+            SF_CUDA_TRY(cudaStreamSynchronize(stream));
+            for (int64_t q = 0; q < nsh; q++) kap[vi] += norms[q];   // shell order: deterministic
+            items.clear();
+            return SF_OK;
+        };
+        auto add_shell = [&](int64_t s) -> int {
+            const int d23 = (int)(s % D), d34 = (int)((s / D) % D), d24 = (int)((s / ((int64_t)D * D)) % D);
+            const int64_t g = s / ((int64_t)D * D * D);
+            const int d45 = (int)(g % D), d35 = (int)((g / D) % D), d25 = (int)(g / ((int64_t)D * D));
+            const int l23 = j[F23] + 2 * d23, l24 = j[F24] + 2 * d24, l25 = j[F25] + 2 * d25;
+            const int l34 = j[F34] + 2 * d34, l35 = j[F35] + 2 * d35, l45 = j[F45] + 2 * d45;
+            int lo, n2, n3, n4, n5;
+            sf_pair_range(l23, l24, l25, j[F12], &lo, &n2);
+            sf_pair_range(l34, l35, j[F13], l23, &lo, &n3);
+            sf_pair_range(l45, j[F14], l24, l34, &lo, &n4);
+            sf_pair_range(j[F15], l25, l35, l45, &lo, &n5);
+            if (!n2 || !n3 || !n4 || !n5) return SF_OK;   // an empty shell contributes nothing
+            nsel++;
+            for (int64_t tile = 0; tile < (int64_t)h.od[0] * h.od[1]; tile++)
+                for (int hp = 0; hp < ns; hp++) {
+                    WorkItem w{};
+                    w.vtx = (int)vi;
+                    w.i1 = (int)(h.olo[0] + tile / h.od[1]);
+                    w.i2 = (int)(h.olo[1] + tile % h.od[1]);
+                    w.g0 = (int)g;
+                    w.g1 = (int)g + 1;
+                    w.i3b = (int16_t)(h.olo[2] + h.od[2] * hp / ns);
+                    w.ni3 = (int16_t)(h.olo[2] + h.od[2] * (hp + 1) / ns - w.i3b);
+                    w.part_off = (int64_t)items.size();
+                    w.single = 1 + 64 * (d24 * D + d34) + d23;
+                    items.push_back(w);
+                }
+            if (items.size() + (size_t)nper > (size_t)KAPPA_BATCH) return flush();
+            return SF_OK;
+        };
+        if (nper > KAPPA_BATCH) { rc = sf_set_error(SF_ERR_LIMIT, "kappa pass: too many tiles per shell"); break; }
+        if (shell_list) {
+            for (int64_t s : list)
+                if (s >= 0 && s < h.nshell && (rc = add_shell(s)) != SF_OK) break;
+        } else {
+            const int64_t b = std::min<int64_t>(std::max<int64_t>(shell_begin, 0), h.nshell);
+            const int64_t e = std::min<int64_t>(std::max<int64_t>(shell_end, 0), h.nshell);
+            for (int64_t s = b; s < e && rc == SF_OK; s++) rc = add_shell(s);
+        }
+        if (rc == SF_OK) rc = flush();
+    }
+    if (rc == SF_OK) {
+        cudaError_t e = cudaMemcpyAsync(kappa_out, kap.data(), kap.size() * sizeof(double), cudaMemcpyDefault, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) rc = sf_set_error(SF_ERR_CUDA, "kappa copy: %s", cudaGetErrorString(e));
+    }
+    cudaStreamSynchronize(stream);
+    cudaFree(buf);
+    return rc;
+}
+
 extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t shell_begin, int64_t shell_end,
-                                   const int64_t* shell_list, int64_t n_list, double* const* A_out, cudaStream_t stream) {
+                                   const int64_t* shell_list, int64_t n_list, double* const* A_out, double* kappa_out,
+                                   cudaStream_t stream) {
     if (!t || !A_out) return sf_set_error(SF_ERR_ARG, "null argument");
     if (precision != SF_FP64 && precision != SF_MIXED && precision != SF_MIXED_FF)
         return sf_set_error(SF_ERR_ARG, "unknown precision");
@@ -737,6 +892,10 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
     if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) g_last_kernel_ms = ms;
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
+    if (rc == SF_OK && kappa_out) {
+        rc = kappa_pass(t, shell_list, n_list, shell_begin, shell_end, filt, kappa_out, stream);
+        if (rc == SF_OK) rc = check_status(t, stream, "sf_vertex_amplitude (kappa)");
+    }
     return rc;
 }
 
@@ -969,9 +1128,10 @@ extern "C" int sf_plan_autotune(sf_plan* p, int64_t sample_shells, sf_tiling* ch
     return SF_OK;
 }
 
-extern "C" int sf_vertex_adjoint(sf_tables* t, const double* const psi[5], double* a_out, double* const grad_psi[5],
-                                 double* const grad_B[4], cudaStream_t stream) {
+extern "C" int sf_vertex_adjoint(sf_tables* t, sf_precision precision, const double* const psi[5], double* a_out,
+                                 double* const grad_psi[5], double* const grad_B[4], cudaStream_t stream) {
     if (!t || !psi || !a_out) return sf_set_error(SF_ERR_ARG, "null argument");
+    if (precision != SF_FP64) return sf_set_error(SF_ERR_ARG, "the adjoint runs in FP64 only (precision %d)", (int)precision);
     if (t->vs.size() != 1) return sf_set_error(SF_ERR_ARG, "the adjoint needs single-vertex tables");
     if (!t->vs[0].boosters_ready) return sf_set_error(SF_ERR_ARG, "boosters were never computed or uploaded");
     for (int e = 0; e < 5; e++) if (!psi[e]) return sf_set_error(SF_ERR_ARG, "null boundary vector %d", e + 1);
@@ -980,6 +1140,9 @@ extern "C" int sf_vertex_adjoint(sf_tables* t, const double* const psi[5], doubl
     if (grad_B)
         for (int e = 0; e < 4; e++) if (!grad_B[e]) return sf_set_error(SF_ERR_ARG, "null grad_B[%d]", e);
     const VertexHost& hv = t->vs[0];
+    for (int e = 0; e < 5; e++)
+        if (hv.olo[e] != 0 || hv.od[e] != hv.di[e])
+            return sf_set_error(SF_ERR_ARG, "the adjoint needs the whole intertwiner range (edge %d has a sub-range)", e + 1);
     VtxDev h;
     memset(&h, 0, sizeof(h));
     for (int e = 0; e < 5; e++) { h.di[e] = hv.di[e]; h.ilo[e] = hv.ilo[e]; }
@@ -1118,23 +1281,23 @@ extern "C" int sf_vertex_amplitude_noalloc(sf_tables* t, int64_t shell_begin, in
         int64_t b = std::min<int64_t>(shell_begin, h.nshell), e = std::min<int64_t>(std::max<int64_t>(shell_end, 0), h.nshell);
         int64_t lo = b / per_group, hi = (e > b) ? (e + per_group - 1) / per_group : lo;
         item0[i] = (int)items.size();
-        const int64_t per = (int64_t)h.di[2] * h.di[3] * h.di[4];
-        for (int64_t tile = 0; tile < (int64_t)h.di[0] * h.di[1]; tile++) {
+        const int64_t per = (int64_t)h.od[2] * h.od[3] * h.od[4];
+        for (int64_t tile = 0; tile < (int64_t)h.od[0] * h.od[1]; tile++) {
             WorkItem w{};
             w.vtx = i;
-            w.i1 = (int)(tile / h.di[1]);
-            w.i2 = (int)(tile % h.di[1]);
+            w.i1 = (int)(h.olo[0] + tile / h.od[1]);
+            w.i2 = (int)(h.olo[1] + tile % h.od[1]);
             w.g0 = (int)lo;
             w.g1 = (int)hi;
-            w.i3b = 0;
-            w.ni3 = (int16_t)h.di[2];
+            w.i3b = (int16_t)h.olo[2];
+            w.ni3 = (int16_t)h.od[2];
             w.part_off = part_total;
             part_total += per;
             items.push_back(w);
         }
-        if ((int64_t)h.di[3] * ((h.di[4] + 1) / 2) * ((h.di[2] + 3) / 4) > 4 * 256)
+        if ((int64_t)h.od[3] * ((h.od[4] + 1) / 2) * ((h.od[2] + 3) / 4) > 4 * 256)
             return sf_set_error(SF_ERR_LIMIT, "vertex %d: intertwiner dimensions too large for the register-resident tile", i);
-        for (int k = 2; k < 5; k++) mdi = std::max(mdi, (int)h.di[k]);
+        for (int k = 2; k < 5; k++) mdi = std::max(mdi, (int)h.od[k]);
         for (int k = 0; k < 4; k++) mdk = std::max(mdk, (int)h.dkmax[k]);
         mk3u = std::max(mk3u, h.mk3u);
         Dmax = std::max(Dmax, h.D);
@@ -1167,7 +1330,7 @@ extern "C" int sf_vertex_amplitude_noalloc(sf_tables* t, int64_t shell_begin, in
                                 t->num_sms, stream));
     for (int i = 0; i < nv; i++) {
         VertexHost& h = t->vs[i];
-        SF_TRY(sf_reduce_launch(t->d_vtx, i, h.di[0] * h.di[1], d_items, item0[i], 1, d_part, A_out[i], stream));
+        SF_TRY(sf_reduce_launch(t->d_vtx, i, h.od[0] * h.od[1], d_items, item0[i], 1, d_part, A_out[i], stream));
     }
     return check_status(t, stream, "sf_vertex_amplitude_noalloc");
 }

@@ -187,8 +187,8 @@ __global__ void __launch_bounds__(SF_DT_NT) k_dtable(const __grid_constant__ Dta
     __syncthreads();
     if (n >= nnodes) return;
     const double r = R[n];
-    const double er = exp(r), emr = exp(-r);
-    const double sh2 = er - emr;   // 2 sinh r
+    const double emr = exp(-r);
+    const double sh2 = 2.0 * sinh(r);   // 2 sinh r (not e^r - e^-r, which cancels at small r)
     const int kpm = (tk + tm) / 2, kmm = (tk - tm) / 2;
     double sqc = 1.0;              // sqrt(C(2k, k+m))
     {

@@ -221,6 +221,7 @@ struct VtxDev {
     double gamma;
     int32_t dl, D;             // D = dl + 1
     int32_t ilo[5], di[5];     // intertwiner ranges
+    int32_t olo[5], od[5];     // output sub-range per edge: first index within the range, count
     int64_t nshell;            // D^6
     const double* S[5];        // {6j} tables S1..S5
     const float* S4f;          // S4 rounded to FP32 once (mixed paths)
@@ -246,6 +247,9 @@ struct WorkItem {              // output tile (i1, i2), i3 in [i3b, i3b + ni3), 
     int32_t vtx, i1, i2, g0, g1;
     int16_t i3b, ni3;
     int64_t part_off;          // its partial tile [i3 - i3b][i4][i5] in the partials buffer
+    int32_t single;            // 0: every selected shell of the groups; 1 + 64 p + d23: that one shell only
+                               // (p = d24 D + d34 within group g0), whose squared output-tile norm is
+                               // written to part[part_off] instead of the tile
 };
 struct ShellFilter {
     int64_t begin, end;          // linear shell range

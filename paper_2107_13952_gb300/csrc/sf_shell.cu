@@ -397,7 +397,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
         const int j12 = v.tj[F12], j13 = v.tj[F13], j14 = v.tj[F14], j15 = v.tj[F15];
         const int i1 = v.ilo[0] + 2 * w.i1;
         const int ci2 = w.i2;
-        const int di3 = w.ni3, i3b = w.i3b, di3f = v.di[2], di4 = v.di[3], di5 = v.di[4];
+        // output block: i3 in [i3b, i3b + ni3) of the whole range, i4 and i5 from the vertex's
+        // sub-range (rows o4.., o5.. of the edge-4 and edge-5 boosters)
+        const int di3 = w.ni3, i3b = w.i3b, di3f = v.di[2], di4 = v.od[3], di5 = v.od[4];
+        const int o4 = v.olo[3], o5 = v.olo[4];
         const int dk1 = v.dkmax[1];
         const int jsum = j12 + j13 + j14 + j15 + v.ilo[0];
         // output tile T[i4][i5][i3] in registers: blocks (i4, 2 i5, 4 i3), block b = tid + r * nth
@@ -418,11 +421,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
             __syncthreads();
             const int t5 = (d25 * D + d35) * D + d45;
             {
-                const double* B5 = v.B[3] + (int64_t)t5 * di5 * v.dkmax[3];
+                const double* B5 = v.B[3] + (int64_t)t5 * v.di[4] * v.dkmax[3];
                 for (int q = tid; q < di5 * nk5; q += nth) {
                     const int i5 = q / nk5, c5 = q % nk5;
                     const double f = (double)(k5lo + 2 * c5 + 1) * ((c5 & 1) ? -1.0 : 1.0);
-                    sm.B5[q] = f * B5[i5 * v.dkmax[3] + c5];
+                    sm.B5[q] = f * B5[(i5 + o5) * v.dkmax[3] + c5];
                 }
             }
             for (int q = tid; q < di4 * nk5 * di3; q += nth) sm.Y[q] = 0.0;
@@ -439,7 +442,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
             const int x_lo_b = (j14 < k5lo) ? (k5lo - j14) : (j14 > k5hi ? j14 - k5hi : ((j14 + k5lo) & 1));
             const int x_hi_b = k5hi + j14;
             bool gany = false;
-            for (int p = 0; p < D * D; p++) {
+            const int p_lo = w.single ? ((w.single - 1) >> 6) : 0, p_hi = w.single ? p_lo + 1 : D * D;
+            const int d_one = w.single ? ((w.single - 1) & 63) : -1;
+            for (int p = p_lo; p < p_hi; p++) {
                 const int d24 = p / D, d34 = p % D;
                 const int l24 = v.tj[F24] + 2 * d24, l34 = v.tj[F34] + 2 * d34;
                 int k4lo, nk4;
@@ -460,7 +465,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                     sf_pair_range(l23, l24, l25, j12, &k2lo, &nk2);
                     sf_pair_range(l34, l35, j13, l23, &k3lo, &nk3);
                     const int64_t s = (((int64_t)g * D + d24) * D + d34) * D + d;   // group-major order
-                    if (nk2 == 0 || nk3 == 0 || !shell_selected(filt, s)) { nk2 = 0; nk3 = 0; }
+                    if (nk2 == 0 || nk3 == 0 || !shell_selected(filt, s) || (d_one >= 0 && d != d_one)) { nk2 = 0; nk3 = 0; }
                     s_k2lo[d] = k2lo; s_nk2[d] = nk2; s_k3lo[d] = k3lo; s_nk3[d] = nk3;
                     const int E2 = jsum + k2lo + k3lo + k4lo + k5lo + l23 + l24 + l25 + l34 + l35 + l45;
                     s_sig[d] = ((E2 >> 1) & 1) ? -1.0 : 1.0;
@@ -484,18 +489,18 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                 const FDiv f_nk3u = fdiv_make(nk3u), f_di3 = fdiv_make(di3), f_mdk5 = fdiv_make(mdk);
                 const int t4 = (d45 * D + d24) * D + d34;
                 if constexpr (FF) {
-                    const float* B4 = v.Bf[2] + (int64_t)t4 * di4 * v.dkmax[2];
+                    const float* B4 = v.Bf[2] + (int64_t)t4 * v.di[3] * v.dkmax[2];
                     for (int q = tid; q < di4 * nk4; q += nth) {
                         const int i4 = q / nk4, c4 = q % nk4;
                         const float f = (float)(k4lo + 2 * c4 + 1) * ((c4 & 1) ? -1.0f : 1.0f);
-                        sm.B4f[q] = f * B4[i4 * v.dkmax[2] + c4];
+                        sm.B4f[q] = f * B4[(i4 + o4) * v.dkmax[2] + c4];
                     }
                 } else {
-                    const double* B4 = v.B[2] + (int64_t)t4 * di4 * v.dkmax[2];
+                    const double* B4 = v.B[2] + (int64_t)t4 * v.di[3] * v.dkmax[2];
                     for (int q = tid; q < di4 * nk4; q += nth) {
                         const int i4 = q / nk4, c4 = q % nk4;
                         const double f = (double)(k4lo + 2 * c4 + 1) * ((c4 & 1) ? -1.0 : 1.0);
-                        sm.B4[q] = f * B4[i4 * v.dkmax[2] + c4];
+                        sm.B4[q] = f * B4[(i4 + o4) * v.dkmax[2] + c4];
                     }
                 }
                 // raw B3 rows of every l23, transposed to [d][c3][i3] (read along c3: coalesced)
@@ -803,6 +808,40 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                 }
             }
         }
+        if (w.single) {
+            // one shell's contribution: the squared 2-norm of its output tile, with the factors
+            // prod_e sqrt(2 i_e + 1) that the reduction applies (the sign does not matter here)
+            const double s12 = (double)(v.ilo[0] + 2 * w.i1 + 1) * (double)(v.ilo[1] + 2 * w.i2 + 1);
+            double q2 = 0.0;
+#pragma unroll
+            for (int rr = 0; rr < SF_TRT; rr++) {
+                const int b = tid + rr * nth;
+                if (b < di4 * tper) {
+                    const int i4 = b / tper, r = b - i4 * tper;
+                    const int m0 = (r / tb3) * 2, n0 = (r - (r / tb3) * tb3) * 4;
+#pragma unroll
+                    for (int i = 0; i < 2; i++)
+#pragma unroll
+                        for (int j = 0; j < 4; j++)
+                            if (m0 + i < di5 && n0 + j < di3) {
+                                const double f = (double)(v.ilo[2] + 2 * (i3b + n0 + j) + 1) *
+                                                 (double)(v.ilo[3] + 2 * (o4 + i4) + 1) *
+                                                 (double)(v.ilo[4] + 2 * (o5 + m0 + i) + 1);
+                                q2 = fma(f * T[rr][i][j], T[rr][i][j], q2);
+                            }
+                }
+            }
+            for (int off = 16; off > 0; off >>= 1) q2 += __shfl_xor_sync(0xffffffffu, q2, off);
+            __syncthreads();   // the chunk buffers are free: reuse the first NT / 32 doubles
+            if ((tid & 31) == 0) smem[tid >> 5] = q2;
+            __syncthreads();
+            if (tid == 0) {
+                double tot = 0.0;
+                for (int q = 0; q < NT / 32; q++) tot += smem[q];
+                part[w.part_off] = s12 * tot;
+            }
+            continue;
+        }
         // partial tile in [i3][i4][i5] order
         double* out = part + w.part_off;
 #pragma unroll
@@ -884,14 +923,15 @@ __global__ void k_reduce(const VtxDev* __restrict__ V, int vtx, const WorkItem* 
                          int nchunk, const double* __restrict__ part, double* __restrict__ A) {
     const VtxDev& v = V[vtx];
     const int tile = blockIdx.x;
-    const int ci1 = tile / v.di[1], ci2 = tile % v.di[1];
-    const int n3 = v.di[2] * v.di[3] * v.di[4];
+    const int ci1 = v.olo[0] + tile / v.od[1], ci2 = v.olo[1] + tile % v.od[1];
+    const int n3 = v.od[2] * v.od[3] * v.od[4];
     const double s12 = sqrt((double)(v.ilo[0] + 2 * ci1 + 1)) * sqrt((double)(v.ilo[1] + 2 * ci2 + 1)) *
                        ((ci1 & 1) ? -1.0 : 1.0);
     for (int q = threadIdx.x; q < n3; q += blockDim.x) {
         double acc = 0.0;
         for (int c = 0; c < nchunk; c++) acc += part[items[item0 + tile * nchunk + c].part_off + q];
-        const int c5 = q % v.di[4], c4 = (q / v.di[4]) % v.di[3], c3 = q / (v.di[4] * v.di[3]);
+        const int c5 = v.olo[4] + q % v.od[4], c4 = v.olo[3] + (q / v.od[4]) % v.od[3],
+                  c3 = v.olo[2] + q / (v.od[4] * v.od[3]);
         const double s = s12 * sqrt((double)(v.ilo[2] + 2 * c3 + 1)) * sqrt((double)(v.ilo[3] + 2 * c4 + 1)) *
                          sqrt((double)(v.ilo[4] + 2 * c5 + 1));
         A[(int64_t)tile * n3 + q] = s * acc;
@@ -911,14 +951,15 @@ __global__ void k_reduce_jobs(const VtxDev* __restrict__ V, const ReduceJob* __r
                               const WorkItem* __restrict__ items, const double* __restrict__ part) {
     const ReduceJob jb = jobs[blockIdx.x];
     const VtxDev& v = V[jb.vtx];
-    const int ci1 = jb.tile / v.di[1], ci2 = jb.tile % v.di[1];
-    const int n3 = jb.ni3 * v.di[3] * v.di[4];
+    const int ci1 = v.olo[0] + jb.tile / v.od[1], ci2 = v.olo[1] + jb.tile % v.od[1];
+    const int n3 = jb.ni3 * v.od[3] * v.od[4];
     const double s12 = sqrt((double)(v.ilo[0] + 2 * ci1 + 1)) * sqrt((double)(v.ilo[1] + 2 * ci2 + 1)) *
                        ((ci1 & 1) ? -1.0 : 1.0);
     for (int q = threadIdx.x; q < n3; q += blockDim.x) {
         double acc = 0.0;
         for (int c = 0; c < jb.nchunk; c++) acc += part[items[jb.item0 + c * jb.stride].part_off + q];
-        const int c5 = q % v.di[4], c4 = (q / v.di[4]) % v.di[3], c3 = jb.i3b + q / (v.di[4] * v.di[3]);
+        const int c5 = v.olo[4] + q % v.od[4], c4 = v.olo[3] + (q / v.od[4]) % v.od[3],
+                  c3 = jb.i3b + q / (v.od[4] * v.od[3]);
         const double s = s12 * sqrt((double)(v.ilo[2] + 2 * c3 + 1)) * sqrt((double)(v.ilo[3] + 2 * c4 + 1)) *
                          sqrt((double)(v.ilo[4] + 2 * c5 + 1));
         jb.A[q] = s * acc;

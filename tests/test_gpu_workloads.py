@@ -53,7 +53,10 @@ def test_full_size_shell_subsets(lib, name):
     bs = ob.random_boosters(tj, dl, int(g["booster_seed"]))
     _upload(t, 0, bs)
     shells = g["shells"]
-    a64 = sf.sf_vertex_amplitude(t, shell_list=shells)[0].cpu().numpy()
+    outs, kap = sf.sf_vertex_amplitude(t, shell_list=shells, kappa=True)
+    a64 = outs[0].cpu().numpy()
+    # sum over the subset of the shells' contribution norms (the numerator of kappa)
+    assert abs(kap[0] - float(g["kappa"])) <= 1e-10 * float(g["kappa"]), (kap[0], float(g["kappa"]))
     amx = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED, shell_list=shells)[0].cpu().numpy()
     aff = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED_FF, shell_list=shells)[0].cpu().numpy()
     ref = g["A"]
@@ -64,13 +67,16 @@ def test_full_size_shell_subsets(lib, name):
         else:
             got = a
         assert _rel(got, ref) <= bound
-        # elementwise form of the same comparison: relative error on every (sampled) entry of at
-        # least 1e-8 of the largest, with an absolute floor of bound/1000 of the largest entry
-        # (below it the oracle's own FP64 rounding of a cancelling 10^4-term sum dominates)
+        # elementwise form of the same comparison: relative error on every (sampled) entry, with
+        # an absolute floor at the scale of the largest entry, because rounding errors follow the
+        # size of the shell contributions, not of the entry they cancel into: 1e-13 of the largest
+        # entry for FP64 (a few units of 1e-16 times the sum of the 10^4 contributions' sizes) and
+        # the stated bound of the largest entry for the mixed paths (FP32 rounding of the same)
         amax = np.abs(ref).max()
+        floor = 1e-3 * bound * amax if bound == FP64_BOUND else bound * amax
         big = np.abs(ref) >= 1e-8 * amax
         dev = np.abs(got - ref)
-        assert np.all(dev <= bound * np.abs(ref) + 1e-3 * bound * amax), (bound, float(dev.max() / amax))
+        assert np.all(dev <= bound * np.abs(ref) + floor), (bound, float(dev.max() / amax))
         rel_el = float((dev[big] / np.abs(ref[big])).max())
         print("%s bound %g: normwise %.2e, elementwise max rel (entries >= 1e-8 max) %.2e"
               % (name, bound, _rel(got, ref), rel_el))
@@ -127,8 +133,10 @@ def test_boosters_sampled_against_oracle(lib, name):
 def test_dtables_composite_rule(lib):
     """rho = 70 (spin 6, gamma 10): on the 2000-node rule the nodes of largest r ask for more
     Gauss-Legendre points than the largest library rule, so the d-table kernel integrates them
-    with a composite rule; entries against the closed form, relative 1e-10 where nothing cancels
-    (|m| = k) and 1e-12 of the face maximum everywhere."""
+    with a composite rule; entries against the closed form, 1e-12 of the face maximum everywhere
+    (the nodes of largest r, one in the middle and the smallest r, where l > k entries vanish
+    like r^(l-k)), and relative 1e-10 at the composite-rule nodes where |m| = k (no cancellation
+    in the integral there: the entry decays only as e^-r)."""
     tj, dl, gamma = (12,) * 10, 2, 10.0
     t = sf.sf_6j_table([sf.vertex(tj, gamma, dl)])
     sf.sf_boosters(t, FULL_RULE)
@@ -149,7 +157,7 @@ def test_dtables_composite_rule(lib):
                         -mpmath.log(mpmath.mpf(x[n])), 25))
                     err = abs(tab[p, im, n] - ref)
                     assert err <= 1e-12 * scale, (f, p, im, n, err)
-                    if im in (0, 12):
+                    if im in (0, 12) and n in far:
                         assert err <= 1e-10 * abs(ref), (f, p, im, n, err, abs(ref))
 
 
