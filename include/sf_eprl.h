@@ -90,7 +90,7 @@ typedef enum {
     SF_MIXED = 1,   /* booster contractions over k2, k3, k4 with FP32 inputs and FP32 accumulation
                        within one (l24, l34) set of shells; the {6j} contractions, the k5 contraction
                        and every sum across shells in FP64                                        */
-    SF_MIXED_FF = 2 /* booster contractions as SF_MIXED; the {6j} contractions (the S3 contraction
+    SF_MIXED_FF = 2, /* booster contractions as SF_MIXED; the {6j} contractions (the S3 contraction
                        over k3 and the x-sum with S1 S2) in compensated FP32 pairs: operands are
                        (hi, lo) float pairs holding about 48 significant bits, products are formed
                        exactly (Dekker) and summed with an error-compensated dot product (Ogita,
@@ -98,6 +98,15 @@ typedef enum {
                        keep nearly FP64 accuracy on the FP32 pipe; the sums across the (l24, l34)
                        sets of one (l25, l35, l45) group also in pairs; the k5 contraction and the
                        sums across groups in FP64                                                 */
+    SF_MIXED_TC = 3 /* the booster contractions over the virtual intertwiners in FP32-class
+                       arithmetic, the {15j} auxiliary-spin sum and the sums across shells in FP64:
+                       the k4 contraction with the edge-4 booster on the tensor cores (mma.sync
+                       m16n8k16, operands split into three BF16 pieces holding 24 significant
+                       bits, the six piece products of order <= 2 accumulated in FP32: split-BF16
+                       with FP32 accumulation); the k2 contraction (with S4, S5 and B2), the l23
+                       sum with B3 and the k3 contraction with S3 in FP32 on the CUDA cores; the
+                       x-sum (2x+1) S1 S2 of eq. 15j, the k5 contraction, and the sums across the
+                       (l24, l34) sets and groups in FP64                                         */
 } sf_precision;
 
 typedef struct sf_tables sf_tables;

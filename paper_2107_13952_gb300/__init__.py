@@ -19,7 +19,7 @@ _LIB_PATH = _build.LIB
 
 SF_OK, SF_ERR_ARG, SF_ERR_EMPTY, SF_ERR_OOM, SF_ERR_CUDA, SF_ERR_TIMEOUT, SF_ERR_NUMERIC, SF_ERR_LIMIT = \
     0, -1, -2, -3, -4, -5, -6, -7
-SF_FP64, SF_MIXED, SF_MIXED_FF = 0, 1, 2
+SF_FP64, SF_MIXED, SF_MIXED_FF, SF_MIXED_TC = 0, 1, 2, 3
 SF_TAB_6J, SF_TAB_6J_SLOTS, SF_TAB_D, SF_TAB_NODES = 1, 2, 3, 4
 
 # names of every symbol declared in include/sf_eprl.h

@@ -21,6 +21,7 @@
 // and their fixed-order reduction are deterministic.
 #include "sf_internal.cuh"
 #include <type_traits>
+#include <cuda_bf16.h>
 
 // {6j} table read with box and parity checks (zero outside: the symbol vanishes there)
 __device__ __forceinline__ double s6(const double* __restrict__ S, const SlotDesc& sd, int a, int b, int x) {
@@ -224,13 +225,14 @@ __device__ __forceinline__ void gather_loop(int L, int tid, int nth, LoadF ld, S
 //   GEMM_FF_D: A (hi, lo) pairs, B floats, Dot2 accumulation, C = the normalised pair;
 //   GEMM_FF_F: A and B pairs, Dot2 accumulation, C += the pair (pair addition);
 //   GEMM_F32:  A and B floats, FP32 FMA accumulation, C (double) += the float result.
-//   GEMM_F32_FF: as GEMM_F32, with C a pair (C += the float result, pair addition).
-enum { GEMM_FF_D = 0, GEMM_FF_F = 1, GEMM_F32 = 2, GEMM_F32_FF = 3 };
+//   GEMM_F32_FF: as GEMM_F32, with C a pair (C += the float result, pair addition);
+//   GEMM_F32_SET: as GEMM_F32, C (double) = the float result.
+enum { GEMM_FF_D = 0, GEMM_FF_F = 1, GEMM_F32 = 2, GEMM_F32_FF = 3, GEMM_F32_SET = 4 };
 template <int KIND, int RM>
 __device__ __forceinline__ void rows_gemm(int nbatch, int M, int N, int K, const void* Av, int a_bs, int am,
                                           const void* Bv, int b_bs, int bk, void* Cv, int c_bs, int cm, int tid,
                                           int nth) {
-    constexpr bool F32 = KIND == GEMM_F32 || KIND == GEMM_F32_FF;
+    constexpr bool F32 = KIND == GEMM_F32 || KIND == GEMM_F32_FF || KIND == GEMM_F32_SET;
     using TA = typename std::conditional<F32, float, float2>::type;
     using TB = typename std::conditional<KIND == GEMM_FF_F, float2, float>::type;
     const TA* A = reinterpret_cast<const TA*>(Av);
@@ -266,6 +268,8 @@ __device__ __forceinline__ void rows_gemm(int nbatch, int M, int N, int K, const
                 const int co = bt * c_bs + m * cm + n;
                 if constexpr (KIND == GEMM_F32) {
                     reinterpret_cast<double*>(Cv)[co] += (double)sh[i];
+                } else if constexpr (KIND == GEMM_F32_SET) {
+                    reinterpret_cast<double*>(Cv)[co] = (double)sh[i];
                 } else if constexpr (KIND == GEMM_F32_FF) {
                     float2* cp = reinterpret_cast<float2*>(Cv) + co;
                     *cp = ff_add(*cp, make_float2(sh[i], 0.0f));
@@ -297,11 +301,89 @@ __device__ __forceinline__ float s6f(const float* __restrict__ S, const SlotDesc
     return i < 0 ? 0.0f : __ldg(S + sd.off + i);
 }
 
+// ----------------------------------------------------------------------------------------------
+// Tensor-core booster contraction (SF_MIXED_TC). An FP32 value v is split into three BF16 pieces,
+// h0 = bf16(v), h1 = bf16(v - h0), h2 = bf16(v - h0 - h1) (each difference exact in FP32), which
+// hold its 24 significant bits; a product a b is formed from the six piece products of order
+// <= 2 (a0 b0, a0 b1, a1 b0, a0 b2, a1 b1, a2 b0; the dropped ones are below 2^-23 |a b|),
+// accumulated in FP32 by mma.sync m16n8k16 (BF16 inputs, FP32 accumulators): FP32-class accuracy
+// on the tensor pipe. BF16 keeps the FP32 exponent range, so no scaling is needed.
+// Operand planes in shared memory: piece-major, rows of ks = Kp + 8 BF16 (the 8-element pad puts
+// the eight rows that one fragment load touches on distinct banks).
+// ----------------------------------------------------------------------------------------------
+__host__ __device__ inline int tc_ks(int mdk) { return ((mdk + 15) / 16) * 16 + 8; }
+__host__ __device__ inline size_t tc_ap_doubles(int mdk, int mni3) {   // V^T planes, 3 x Mp x ks BF16
+    const size_t mp = (((size_t)mdk * mni3 + 15) / 16) * 16;
+    return (3 * mp * tc_ks(mdk) * 2 + 7) / 8;
+}
+__host__ __device__ inline size_t tc_bp_doubles(int mdi, int mdk) {    // B4' planes, 3 x Np x ks BF16
+    const size_t np = (((size_t)mdi + 7) / 8) * 8;
+    return (3 * np * tc_ks(mdk) * 2 + 7) / 8;
+}
+__device__ __forceinline__ void split3_bf16(float v, unsigned short& h0, unsigned short& h1, unsigned short& h2) {
+    const __nv_bfloat16 b0 = __float2bfloat16_rn(v);
+    const float r1 = __fsub_rn(v, __bfloat162float(b0));
+    const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+    const float r2 = __fsub_rn(r1, __bfloat162float(b1));
+    const __nv_bfloat16 b2 = __float2bfloat16_rn(r2);
+    h0 = __bfloat16_as_ushort(b0);
+    h1 = __bfloat16_as_ushort(b1);
+    h2 = __bfloat16_as_ushort(b2);
+}
+__device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// Y[n][m] += sum_k A[m][k] B[n][k] for m < M, n < N, k < K from the planes Ap (Mp x ks per piece)
+// and Bp (Np x ks per piece); each warp takes 16 x 8 output tiles in turn.
+__device__ __forceinline__ void tc_gemm_acc(const unsigned short* __restrict__ Ap, const unsigned short* __restrict__ Bp,
+                                            int M, int N, int K, int ks, double* __restrict__ Y, int tid, int nth) {
+    const int Mp = (M + 15) & ~15, Np = (N + 7) & ~7, Kp = (K + 15) & ~15;
+    const int planeA = Mp * ks, planeB = Np * ks;
+    const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    const int nmt = Mp >> 4, nnt = Np >> 3;
+    for (int job = warp; job < nmt * nnt; job += nth >> 5) {
+        const int mt = job % nmt, nt = job / nmt;
+        float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int k0 = 0; k0 < Kp; k0 += 16) {
+            uint32_t a[3][4], b[3][2];
+#pragma unroll
+            for (int pc = 0; pc < 3; pc++) {
+                const unsigned short* ab = Ap + pc * planeA + (mt * 16 + g) * ks + k0 + 2 * t;
+                a[pc][0] = *reinterpret_cast<const uint32_t*>(ab);
+                a[pc][1] = *reinterpret_cast<const uint32_t*>(ab + 8 * ks);
+                a[pc][2] = *reinterpret_cast<const uint32_t*>(ab + 8);
+                a[pc][3] = *reinterpret_cast<const uint32_t*>(ab + 8 * ks + 8);
+                const unsigned short* bb = Bp + pc * planeB + (nt * 8 + g) * ks + k0 + 2 * t;
+                b[pc][0] = *reinterpret_cast<const uint32_t*>(bb);
+                b[pc][1] = *reinterpret_cast<const uint32_t*>(bb + 8);
+            }
+            // smallest products first
+            mma_bf16_16816(c, a[2], b[0]);
+            mma_bf16_16816(c, a[1], b[1]);
+            mma_bf16_16816(c, a[0], b[2]);
+            mma_bf16_16816(c, a[1], b[0]);
+            mma_bf16_16816(c, a[0], b[1]);
+            mma_bf16_16816(c, a[0], b[0]);
+        }
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                const int m = mt * 16 + g + 8 * h, n = nt * 8 + 2 * t + j;
+                if (m < M && n < N) Y[n * M + m] += (double)c[2 * h + j];
+            }
+    }
+}
+
 #define SF_TRT 2   // output-tile register blocks per thread (2 x 4 doubles each)
 
 struct ShellSmem {
     double *Y, *V, *B3s, *B4, *B5, *S3s, *Q, *R, *P, *SB, *U;
     float *Vf, *B4f;   // mixed path: FP32 copies for the k4 booster contraction
+    unsigned short *Ap, *Bp;   // tensor-core path: BF16 planes of V^T and of B4'
 };
 
 // Shared-memory layout of one CTA. mni3: largest i3 extent of a work item. Buffers whose
@@ -314,7 +396,7 @@ __host__ __device__ inline size_t shell_chunk_doubles(int mdk, int mk3u, int xc,
     return (size_t)xc * mdk * mk3u + (size_t)mdk * mdk * xc + rp + su;
 }
 
-__device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int xc, int D, int mni3) {
+__device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int xc, int D, int mni3, bool tc) {
     ShellSmem s;
     double* p = base;
     s.Y = p;   p += mdi * mdk * mni3;
@@ -324,7 +406,10 @@ __device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int 
     s.B5 = p;  p += mdi * mdk;
     s.B4f = reinterpret_cast<float*>(p);
     p += (mdi * mdk + 1) / 2;
+    s.Bp = reinterpret_cast<unsigned short*>(p);
+    if (tc) p += tc_bp_doubles(mdi, mdk);
     double* chunk = p;
+    s.Ap = reinterpret_cast<unsigned short*>(chunk);   // after the x loop, over the chunk buffers
     s.S3s = p; p += xc * mdk * mk3u;
     s.Q = p;   p += mdk * mdk * xc;
     s.R = p;
@@ -337,11 +422,12 @@ __device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int 
 }
 
 size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, int mni3, int mode) {
-    const bool mix = mode >= 1;
+    const bool mix = mode >= 1, tc = mode == 3;
     const size_t chunk = shell_chunk_doubles(mdk, mk3u, xc, D, mni3);
-    const size_t vf = mix ? ((size_t)mdk * mdk * mni3 + 1) / 2 : 0;
+    size_t over = mix ? ((size_t)mdk * mdk * mni3 + 1) / 2 : 0;   // Vf, or the V^T planes
+    if (tc) over = tc_ap_doubles(mdk, mni3);
     return (size_t)mdi * mdk * mni3 + (size_t)mdk * mdk * mni3 + (size_t)D * mdk * mni3 + 2ull * mdi * mdk +
-           ((size_t)mdi * mdk + 1) / 2 + (chunk > vf ? chunk : vf);
+           ((size_t)mdi * mdk + 1) / 2 + (tc ? tc_bp_doubles(mdi, mdk) : 0) + (chunk > over ? chunk : over);
 }
 
 // MODE 0: every phase in FP64 (the FP64 path). MODE 1 (the mixed path): the booster
@@ -362,6 +448,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                                                         ShellFilter filt) {
     constexpr bool MIX = MODE >= 1;
     constexpr bool FF = MODE == 2;
+    constexpr bool TC = MODE == 3;   // k4 contraction on the tensor cores, S3 contraction FP32, x-sum FP64
     constexpr int GU = FF ? 4 : 2;   // staging elements in flight per thread (FP64 values: register budget)
     extern __shared__ double smem[];
     __shared__ int s_item;
@@ -374,7 +461,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
     __shared__ VtxDev s_v;          // the current work item's vertex record
     __shared__ int s_vtx;
     if (threadIdx.x == 0) s_vtx = -1;
-    const ShellSmem sm = carve(smem, mdi, mdk, mk3u, XC, Dmax, mni3);
+    const ShellSmem sm = carve(smem, mdi, mdk, mk3u, XC, Dmax, mni3, TC);
     const int tid = threadIdx.x, nth = NT;
     for (;;) {
         __syncthreads();
@@ -488,7 +575,28 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                 const int nk3u = (k3uhi - k3ulo) / 2 + 1;
                 const FDiv f_nk3u = fdiv_make(nk3u), f_di3 = fdiv_make(di3), f_mdk5 = fdiv_make(mdk);
                 const int t4 = (d45 * D + d24) * D + d34;
-                if constexpr (FF) {
+                if constexpr (TC) {
+                    // B4'[i4][c4] as BF16 planes [piece][i4][c4] (zero-padded to whole tiles)
+                    const float* B4 = v.Bf[2] + (int64_t)t4 * v.di[3] * v.dkmax[2];
+                    const int ks = tc_ks(mdk), Np = (di4 + 7) & ~7, Kp2 = ((nk4 + 15) & ~15) / 2;
+                    for (int q = tid; q < Np * Kp2; q += nth) {
+                        const int n = q / Kp2, k0 = 2 * (q - n * Kp2);
+                        float w0 = 0.0f, w1 = 0.0f;
+                        if (n < di4) {
+                            const float* row = B4 + (int64_t)(n + o4) * v.dkmax[2];
+                            if (k0 < nk4) w0 = (float)(k4lo + 2 * k0 + 1) * ((k0 & 1) ? -1.0f : 1.0f) * row[k0];
+                            if (k0 + 1 < nk4) w1 = (float)(k4lo + 2 * k0 + 3) * ((k0 & 1) ? 1.0f : -1.0f) * row[k0 + 1];
+                        }
+                        unsigned short a0, a1, a2, b0, b1, b2;
+                        split3_bf16(w0, a0, a1, a2);
+                        split3_bf16(w1, b0, b1, b2);
+                        uint32_t* dst = reinterpret_cast<uint32_t*>(sm.Bp + n * ks + k0);
+                        const int pl = (Np * ks) / 2;   // one plane, in 32-bit words
+                        dst[0] = (uint32_t)a0 | ((uint32_t)b0 << 16);
+                        dst[pl] = (uint32_t)a1 | ((uint32_t)b1 << 16);
+                        dst[2 * pl] = (uint32_t)a2 | ((uint32_t)b2 << 16);
+                    }
+                } else if constexpr (FF) {
                     const float* B4 = v.Bf[2] + (int64_t)t4 * v.di[3] * v.dkmax[2];
                     for (int q = tid; q < di4 * nk4; q += nth) {
                         const int i4 = q / nk4, c4 = q % nk4;
@@ -512,7 +620,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                         d = fdiv_q(r, f_di3);
                         i3 = r - d * di3;
                     };
-                    if constexpr (FF) {
+                    if constexpr (FF || TC) {
                         gather_loop<4>(D * mdk * di3, tid, nth, [&](int q) {
                             int d, i3, c3;
                             b3_at(q, d, i3, c3);
@@ -613,7 +721,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                             }, [&](int q, double val) {
                                 int xc, c4, ku;
                                 s3_at(q, xc, c4, ku);
-                                sm.S3s[(xc * nk4 + c4) * nk3u + ku] = val;
+                                if constexpr (TC) reinterpret_cast<float*>(sm.S3s)[(xc * nk4 + c4) * nk3u + ku] = (float)val;
+                                else sm.S3s[(xc * nk4 + c4) * nk3u + ku] = val;
                             });
                         }
                     }
@@ -711,7 +820,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                                     if (i30 + 2 < di3) f2 = fmaf(rr, bp[2], f2);
                                     if (i30 + 3 < di3) f3 = fmaf(rr, bp[3], f3);
                                 }
-                                if constexpr (FF) {
+                                if constexpr (FF || TC) {
                                     float* up = reinterpret_cast<float*>(sm.U) + (ku * nxc + xc) * di3 + i30;
                                     up[0] = f0;
                                     if (i30 + 1 < di3) up[1] = f1;
@@ -746,6 +855,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                     if constexpr (FF)
                         rows_gemm<GEMM_FF_D, 2>(nxc, nk4, di3, nk3u, sm.S3s, nk4 * nk3u, nk3u, sm.U, di3, nxc * di3,
                                                 sm.P, di3, nxc * di3, tid, nth);
+                    else if constexpr (TC)
+                        rows_gemm<GEMM_F32_SET, 2>(nxc, nk4, di3, nk3u, sm.S3s, nk4 * nk3u, nk3u, sm.U, di3, nxc * di3,
+                                                   sm.P, di3, nxc * di3, tid, nth);
                     else
                         flat_gemm<double, false>(nxc, nk4, di3, nk3u, sm.S3s, nk4 * nk3u, nk3u, 1, sm.U, di3, nxc * di3, 1,
                                                  sm.P, di3, nxc * di3, 1, tid, nth);
@@ -760,7 +872,26 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                 }
                 __syncthreads();
                 // G: Y[i4][k5][i3] += sum_k4 B4'[i4][k4] V[k4][k5][i3]             (batch over k5)
-                if constexpr (MIX) {
+                if constexpr (TC) {
+                    // on the tensor cores: C[m = (k5, i3)][n = i4] = sum_k4 V[k4][m] B4'[n][k4], V^T split
+                    // into BF16 planes over the (now free) chunk buffers, the FP32 result added to Y
+                    const int Mv = nk5 * di3, ks = tc_ks(mdk), Mp = (Mv + 15) & ~15, Kp2 = ((nk4 + 15) & ~15) / 2;
+                    const int pl = (Mp * ks) / 2;   // one plane, in 32-bit words
+                    for (int q = tid; q < Mp * Kp2; q += nth) {
+                        const int kk = q / Mp, m = q - kk * Mp, k0 = 2 * kk;
+                        const float w0 = (m < Mv && k0 < nk4) ? (float)sm.V[k0 * Mv + m] : 0.0f;
+                        const float w1 = (m < Mv && k0 + 1 < nk4) ? (float)sm.V[(k0 + 1) * Mv + m] : 0.0f;
+                        unsigned short a0, a1, a2, b0, b1, b2;
+                        split3_bf16(w0, a0, a1, a2);
+                        split3_bf16(w1, b0, b1, b2);
+                        uint32_t* dst = reinterpret_cast<uint32_t*>(sm.Ap + m * ks + k0);
+                        dst[0] = (uint32_t)a0 | ((uint32_t)b0 << 16);
+                        dst[pl] = (uint32_t)a1 | ((uint32_t)b1 << 16);
+                        dst[2 * pl] = (uint32_t)a2 | ((uint32_t)b2 << 16);
+                    }
+                    __syncthreads();
+                    tc_gemm_acc(sm.Ap, sm.Bp, Mv, di4, nk4, ks, sm.Y, tid, nth);
+                } else if constexpr (MIX) {
                     for (int q = tid; q < nk4 * nk5 * di3; q += nth) {
                         if constexpr (FF) {
                             const float2 vv = reinterpret_cast<const float2*>(sm.V)[q];
@@ -864,14 +995,15 @@ template <int MODE, int NT>
 static const void* shell_fn() { return (const void*)k_shell<MODE, NT>; }
 
 static const void* shell_kernel(int mode, int nt) {
-    if (nt == 256) return mode == 2 ? shell_fn<2, 256>() : mode == 1 ? shell_fn<1, 256>() : shell_fn<0, 256>();
-    return mode == 2 ? shell_fn<2, 512>() : mode == 1 ? shell_fn<1, 512>() : shell_fn<0, 512>();
+    if (nt == 256)
+        return mode == 3 ? shell_fn<3, 256>() : mode == 2 ? shell_fn<2, 256>() : mode == 1 ? shell_fn<1, 256>() : shell_fn<0, 256>();
+    return mode == 3 ? shell_fn<3, 512>() : mode == 2 ? shell_fn<2, 512>() : mode == 1 ? shell_fn<1, 512>() : shell_fn<0, 512>();
 }
 
 int sf_shell_prepare(int mode, int nt, int mdi, int mdk, int mk3u, int xc, int Dmax, int mni3, int n_items, int num_sms,
                      int* grid, size_t* smem) {
     if (nt != 256 && nt != 512) return sf_set_error(SF_ERR_ARG, "shell kernel runs 256 or 512 threads per CTA");
-    if (mode < 0 || mode > 2) return sf_set_error(SF_ERR_ARG, "unknown shell-kernel mode %d", mode);
+    if (mode < 0 || mode > 3) return sf_set_error(SF_ERR_ARG, "unknown shell-kernel mode %d", mode);
     const size_t bytes = sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax, mni3, mode) * sizeof(double);
     if (bytes > 200 * 1024) return sf_set_error(SF_ERR_LIMIT, "shell kernel needs %zu bytes of shared memory", bytes);
     const void* fn = shell_kernel(mode, nt);
@@ -892,13 +1024,15 @@ int sf_shell_launch_prepared(int mode, int nt, int grid, size_t smem, const VtxD
     SF_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(int), s));
 #define SF_SHELL_GO(M, N)                                                                                     \
     k_shell<M, N><<<grid, N, smem, s>>>(d_v, mdi, mdk, mk3u, xc, Dmax, mni3, d_items, n_items, d_counter, d_part, filt)
-    if (mode < 0 || mode > 2) return sf_set_error(SF_ERR_ARG, "unknown shell-kernel mode %d", mode);
+    if (mode < 0 || mode > 3) return sf_set_error(SF_ERR_ARG, "unknown shell-kernel mode %d", mode);
     if (nt == 256) {
-        if (mode == 2) SF_SHELL_GO(2, 256);
+        if (mode == 3) SF_SHELL_GO(3, 256);
+        else if (mode == 2) SF_SHELL_GO(2, 256);
         else if (mode == 1) SF_SHELL_GO(1, 256);
         else SF_SHELL_GO(0, 256);
     } else {
-        if (mode == 2) SF_SHELL_GO(2, 512);
+        if (mode == 3) SF_SHELL_GO(3, 512);
+        else if (mode == 2) SF_SHELL_GO(2, 512);
         else if (mode == 1) SF_SHELL_GO(1, 512);
         else SF_SHELL_GO(0, 512);
     }

@@ -59,8 +59,9 @@ def test_full_size_shell_subsets(lib, name):
     assert abs(kap[0] - float(g["kappa"])) <= 1e-10 * float(g["kappa"]), (kap[0], float(g["kappa"]))
     amx = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED, shell_list=shells)[0].cpu().numpy()
     aff = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED_FF, shell_list=shells)[0].cpu().numpy()
+    atc = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED_TC, shell_list=shells)[0].cpu().numpy()
     ref = g["A"]
-    for a, bound in ((a64, FP64_BOUND), (amx, MIXED_BOUND), (aff, MIXED_BOUND)):
+    for a, bound in ((a64, FP64_BOUND), (amx, MIXED_BOUND), (aff, MIXED_BOUND), (atc, MIXED_BOUND)):
         if "idx" in g:      # large tensor: a seeded sample of entries plus the norm of the whole
             assert abs(np.linalg.norm(a) - float(g["A_norm"])) <= bound * float(g["A_norm"])
             got = a.reshape(-1)[g["idx"]]
@@ -207,6 +208,7 @@ def test_random_batch_256_against_oracle(lib, batch256):
     out64 = sf.sf_vertex_amplitude(t, shell_end=BATCH_SHELL_END)
     outmx = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED, shell_end=BATCH_SHELL_END)
     outff = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED_FF, shell_end=BATCH_SHELL_END)
+    outtc = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED_TC, shell_end=BATCH_SHELL_END)
     small = [i for i, b in enumerate(batch) if b["dl"] <= 2]
     assert small
     rng = np.random.default_rng(7)
@@ -216,6 +218,7 @@ def test_random_batch_256_against_oracle(lib, batch256):
         assert _rel(out64[int(i)].cpu().numpy(), ref) <= FP64_BOUND
         assert _rel(outmx[int(i)].cpu().numpy(), ref) <= MIXED_BOUND
         assert _rel(outff[int(i)].cpu().numpy(), ref) <= MIXED_BOUND
+        assert _rel(outtc[int(i)].cpu().numpy(), ref) <= MIXED_BOUND
 
 
 def test_random_batch_256_against_single_launches(lib, batch256):
