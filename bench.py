@@ -5,13 +5,23 @@ j = lambda/2, lambda = 1..16, gamma = 1.2, dl = 10 (11^6 = 1,771,561 shells each
 r_max = 40, 40 panels x 50 Gauss-Legendre nodes. One step runs the whole path through the C ABI:
 {6j} tables, d-tables and boosters of all sixteen vertices, then the shell sum over one slice of
 every vertex (the same 1/S range of its group-major shell index), so S consecutive steps cover the
-sweep exactly once. Ranks of a multi-GPU run take different slices (weak scaling, no collective on
-the data path).
+sweep exactly once. Shells are counted when they are non-empty (all four virtual-intertwiner
+ranges non-empty); the count over the whole grid is reported beside. Ranks of a multi-GPU run take
+different slices (weak scaling, no collective on the data path).
+
+``value`` is the path whose precision split keeps the {6j} values exact-then-FP64, the {15j}
+auxiliary-spin sum and every sum across shells in FP64 and runs the booster contractions in
+FP32-class arithmetic with the k4 contraction on the tensor cores (SF_MIXED_TC); the FP64 path and
+the other mixed paths are timed over the same steps beside it, with their errors against the FP64
+path per lambda. The remaining workloads (all 256 irregular vertices in full, the spin-4 dl-20
+vertex in full, the boundary-contracted adjoint, the spin-1 simplex, the vertex-tensor
+contractions and the Delta_3 network) are timed after it.
 
 Prints one JSON line (rank 0). ``--impl reference`` times the CPU oracle on a bounded sample of
 the same workload instead.
 """
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -27,32 +37,37 @@ if ROOT not in sys.path:
 
 RULE = (40.0, 40, 50)
 METRIC = "EPRL vertex shells/sec (mixed vs FP64 GPU path) at stated relative error"
+SWEEP = [(lam, 10) for lam in range(1, 17)]
+GAMMA = 1.2
+CLOCK_GHZ = 2.070
+# FP64 FMA pipe of the GB300: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.070 GHz (max SM clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * CLOCK_GHZ / 1e3
+# FP32 pipe: 152 SMs x 128 lanes x 2.070 GHz, in lane operations (FFMA, FADD, FMUL) per second
+FP32_PEAK_TOPS = 152 * 128 * CLOCK_GHZ / 1e3
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_ff": 2, "mixed_tc": 3}
+DTYPES = {"fp64": "f64", "mixed": "f64+f32", "mixed_ff": "f64+f32+f32x2", "mixed_tc": "f64+f32+bf16x3"}
+HEADLINE = "mixed_tc"
+# precision split of each path: phases B (k2), C (l23 sum with B3), D (k3 with S3), F (x-sum),
+# G (k4 with B4), H (k5 with B5); "64" FP64, "32" FP32 CUDA cores, "ff" compensated pairs, "tc"
+# tensor cores (split BF16)
+PHASE_PRECISION = {"fp64": dict(B="64", C="64", D="64", F="64", G="64", H="64"),
+                   "mixed": dict(B="32", C="32", D="64", F="64", G="32", H="64"),
+                   "mixed_ff": dict(B="32", C="32", D="ff", F="ff", G="32", H="64"),
+                   "mixed_tc": dict(B="32", C="32", D="32", F="64", G="tc", H="64")}
+FF_OPS = {"D": 11, "F": 12}   # FP32 lane operations per multiply-add of the pair phases
+# DRAM bytes (read + write) per launch of the headline shell-sum kernel from one ncu capture of the
+# benchmark's first timed launch, valid while the kernel source hashes to "sha1"
+NCU_TRAFFIC = {"sha1": None, "bytes_per_launch": None}
 
 
 def workload_name(slices):
     return ("homogeneous sweep: 16 vertices, all spins j=lambda/2 for lambda=1..16, gamma=1.2, dl=10 (11^6 shells "
             "each), rule r_max=40 / 40 panels x 50 nodes; one step = 6j tables + d-tables + boosters of all 16 "
             "vertices + shell sum over a 1/%d slice of every vertex's group-major shell range" % slices)
-SWEEP = [(lam, 10) for lam in range(1, 17)]
-GAMMA = 1.2
-# FP64 FMA pipe of the GB300: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.070 GHz (max SM clock)
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-# FP32 pipe: 152 SMs x 128 lanes x 2.070 GHz, in lane operations (FFMA, FADD, FMUL) per second
-FP32_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12
-PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_ff": 2}
-# FP32 lane operations per multiply-add of the compensated-pair phases (SF_MIXED_FF): D is a Dot2
-# step with a pair times a float (FMUL, 2 FFMA, TwoSum = 6, 2 FADD), F a pair times a pair (one
-# more FFMA); the FP32 booster phases take one FFMA per multiply-add
-FF_OPS = {"D": 11, "F": 12}
-# DRAM bytes (read + write) of the benchmark's shell-sum launch from one ncu capture (the first timed
-# launch, slice 3 of the sweep; profiles/k_shell_mixed_ff_sweep_traffic.md), valid while the kernel
-# source hashes to "sha1"
-NCU_TRAFFIC = {"sha1": "77e3c11e9e92", "bytes_per_launch": {"mixed_ff": 32906166784 + 118807808, "mixed": None, "fp64": None}}
 
 
 def kernel_sha1():
-    """sha1 prefix of the shell kernel's source: sf_shell.cu up to its host-side launchers (the
-    kernel and the device helpers it uses)."""
+    """sha1 prefix of the shell kernel's source: sf_shell.cu up to its host-side launchers."""
     p = os.path.join(ROOT, "paper_2107_13952_gb300", "csrc", "sf_shell.cu")
     src = open(p, "rb").read()
     cut = src.find(b"int sf_shell_prepare(")
@@ -60,7 +75,7 @@ def kernel_sha1():
 
 
 # ------------------------------------------------------------------------------------------
-# executed FP64 FMA count of the shell-sum kernel (trip counts of its loops), for the roofline
+# shell bookkeeping on the host (numpy): non-empty shells, executed and canonical operation counts
 # ------------------------------------------------------------------------------------------
 def _pair(a, b, c, d):
     import numpy as np
@@ -71,23 +86,84 @@ def _pair(a, b, c, d):
     return lo, n
 
 
-def executed_fmas(tj, dl, g0, g1):
-    """FMAs the shell kernel executes for groups [g0, g1) of one vertex (all tiles), per phase."""
+def _shell_axes(tj, dl):
+    """The six free-face spins on a broadcast grid, axes (d25, d35, d45, d24, d34, d23): the
+    group-major linear shell order of the library, so the flattened grid is indexed by s."""
     import numpy as np
-    from paper_2107_13952_gb300 import intertwiner_ranges
-    lo, dim = intertwiner_ranges(tj, GAMMA, dl)
     D = dl + 1
-    j12, j13, j14, j15, j23, j24, j25, j34, j35, j45 = tj
     d = np.arange(D)
-    # axes: 0 d25, 1 d35, 2 d45, 3 d24, 4 d34, 5 d23
     sh = [1] * 6
 
     def ax(i):
         s = list(sh)
         s[i] = D
         return d.reshape(s)
-    l25, l35, l45, l24, l34, l23 = (j25 + 2 * ax(0), j35 + 2 * ax(1), j45 + 2 * ax(2), j24 + 2 * ax(3),
-                                    j34 + 2 * ax(4), j23 + 2 * ax(5))
+    j12, j13, j14, j15, j23, j24, j25, j34, j35, j45 = tj
+    return (j25 + 2 * ax(0), j35 + 2 * ax(1), j45 + 2 * ax(2), j24 + 2 * ax(3), j34 + 2 * ax(4), j23 + 2 * ax(5))
+
+
+def nonempty_shells(tj, dl):
+    """Boolean array over the linear shell index: all four k ranges of the shell non-empty."""
+    import numpy as np
+    j12, j13, j14, j15 = tj[:4]
+    l25, l35, l45, l24, l34, l23 = _shell_axes(tj, dl)
+    ok = ((_pair(j15, l25, l35, l45)[1] > 0) & (_pair(l45, j14, l24, l34)[1] > 0)
+          & (_pair(l23, l24, l25, j12)[1] > 0) & (_pair(l34, l35, j13, l23)[1] > 0))
+    return np.broadcast_to(ok, (dl + 1,) * 6).reshape(-1)
+
+
+def canonical_flops(tj, dl):
+    """Per-shell FP64 flop count of the framed algorithm (W by the x-sum, then four mode products,
+    FMA = 2 flops) over the linear shell index; zero for empty shells."""
+    import numpy as np
+    from paper_2107_13952_gb300 import intertwiner_ranges
+    lo, dim = intertwiner_ranges(tj, GAMMA, dl)
+    j12, j13, j14, j15 = tj[:4]
+    l25, l35, l45, l24, l34, l23 = _shell_axes(tj, dl)
+    k5lo, n5 = _pair(j15, l25, l35, l45)
+    k4lo, n4 = _pair(l45, j14, l24, l34)
+    k2lo, n2 = _pair(l23, l24, l25, j12)
+    k3lo, n3 = _pair(l34, l35, j13, l23)
+    shape = (dl + 1,) * 6
+    i1 = lo[0] + 2 * np.arange(dim[0])
+
+    def count_tri(lo_, n_, a, x):
+        # labels k = lo_ + 2c, c < n_, with |k - a| <= x <= k + a and k + a + x even
+        c = np.arange(int(np.max(n_)) + 1 if np.size(n_) else 1)
+        kk = np.asarray(lo_)[..., None] + 2 * c
+        valid = c < np.asarray(n_)[..., None]
+        okt = (np.abs(kk - np.asarray(a)[..., None]) <= x) & (x <= kk + np.asarray(a)[..., None]) & \
+              ((kk + np.asarray(a)[..., None] + x) % 2 == 0)
+        return (valid & okt).sum(axis=-1)
+    # the parity of x is that of i1 + l25 (fixed per shell), so only every other x contributes; each
+    # count is formed on the small grid of the faces it depends on and broadcast in the product
+    xmax = int(2 * max(tj) + 4 * dl + 2)
+    w = np.zeros(shape)
+    for x in range(0, xmax + 1):
+        m1 = ((np.abs(i1[None, :] - np.asarray(l25).reshape(-1, 1)) <= x)
+              & (x <= i1[None, :] + np.asarray(l25).reshape(-1, 1))
+              & ((i1[None, :] + np.asarray(l25).reshape(-1, 1) + x) % 2 == 0)).sum(axis=1).reshape(np.shape(l25))
+        if not m1.any():
+            continue
+        w += m1 * count_tri(k5lo, n5, j14, x) * count_tri(k4lo, n4, l35, x) * count_tri(k3lo, n3, l24, x) \
+            * count_tri(k2lo, n2, j13, x)
+    n2, n3, n4, n5 = (np.broadcast_to(v, shape) for v in (n2, n3, n4, n5))
+    d1, d2, d3, d4, d5 = dim
+    contr = (d1 * d2 * n2 * n3 * n4 * n5 + d1 * d2 * d3 * n3 * n4 * n5 + d1 * d2 * d3 * d4 * n4 * n5
+             + d1 * d2 * d3 * d4 * d5 * n5)
+    live = (n2 > 0) & (n3 > 0) & (n4 > 0) & (n5 > 0)
+    return np.where(live, 2.0 * w + 2.0 * contr, 0.0).reshape(-1)
+
+
+def executed_fmas(tj, dl, g0, g1):
+    """Multiply-adds the shell kernel executes for groups [g0, g1) of one vertex (all tiles), per
+    phase (trip counts of its loops)."""
+    import numpy as np
+    from paper_2107_13952_gb300 import intertwiner_ranges
+    lo, dim = intertwiner_ranges(tj, GAMMA, dl)
+    D = dl + 1
+    j12, j13, j14, j15 = tj[:4]
+    l25, l35, l45, l24, l34, l23 = _shell_axes(tj, dl)
     k5lo, nk5 = _pair(j15, l25, l35, l45)
     k4lo, nk4 = _pair(l45, j14, l24, l34)
     k2lo, nk2 = _pair(l23, l24, l25, j12)
@@ -129,26 +205,25 @@ def executed_fmas(tj, dl, g0, g1):
         for name, per5 in (("B", sum_nk3nk2 * nx), ("C", nx * di3 * sum_nk3), ("D", nk4b * nx * di3 * k3u),
                            ("F", nk4b * nk5b * di3 * nx), ("G", di4 * nk5b * di3 * nk4b)):
             total[name] += int(np.where(live, per5, 0).sum())
-    # H: once per group with a non-empty k5 range
     g_live = ((gidx >= g0) & (gidx < g1)) & (nk5[..., 0, 0, 0] > 0)
     total["H"] += int(dim[0] * np.where(g_live, di4 * di5 * di3 * nk5[..., 0, 0, 0], 0).sum())
     return {k: v * dim[1] for k, v in total.items()}
 
 
-FP32_PHASES_MIXED = ("B", "C", "G")   # booster contractions the mixed paths run in FP32
-
-
 def pipe_ops(phases, precision):
-    """(FP64 flops, FP32 lane ops) the shell kernel executes for a phase count dict."""
-    f64, f32 = 0, 0
+    """(FP64 flops, FP32 lane ops, tensor-core multiply-adds before padding) of a phase count."""
+    f64, f32, tc = 0, 0, 0
     for name, n in phases.items():
-        if precision != "fp64" and name in FP32_PHASES_MIXED:
+        p = PHASE_PRECISION[precision][name]
+        if p == "64":
+            f64 += 2 * n
+        elif p == "32":
             f32 += n
-        elif precision == "mixed_ff" and name in FF_OPS:
+        elif p == "ff":
             f32 += FF_OPS[name] * n
         else:
-            f64 += 2 * n
-    return f64, f32
+            tc += n
+    return f64, f32, tc
 
 
 # ------------------------------------------------------------------------------------------
@@ -237,13 +312,13 @@ def _oracle_worker(args):
                 bs[e] = {"B": rng.standard_normal((D ** 3, di, max(1, int(nk.max())))), "klo": klo}
             cache[lam] = bs
         s = int(rng.integers(0, (dl + 1) ** 6))
-        ov.shell_contribution(tj, dl, s, cache[lam], six)
-        done += 1
+        if ov.shell_contribution(tj, dl, s, cache[lam], six) is not None:   # count non-empty shells
+            done += 1
     return done
 
 
 def oracle_rate(seconds, seed=0):
-    """Oracle shell-sum throughput (shells/s) on all host cores for `seconds` of wall time."""
+    """Oracle shell-sum throughput (non-empty shells/s) on all host cores for `seconds` of wall time."""
     import multiprocessing as mp
     cores = os.cpu_count() or 1
     lam_list = [lam for lam, _ in SWEEP]
@@ -258,113 +333,215 @@ def oracle_rate(seconds, seed=0):
 
 
 # ------------------------------------------------------------------------------------------
-def batched_measure(shells, steps=3):
-    """The batched workload: 256 irregular vertices (ten spins uniform in {1/2..6}, redrawn until all
-    five intertwiner ranges are non-empty; dl uniform in 0..12; gamma from {0.1, 1.2, 5.0}; seed 0),
-    the first ``shells`` shells of every vertex, as one planned launch (persistent shell kernel +
-    one reduction) replayed as a CUDA graph, tiling autotuned on a sample, in both precisions."""
+# the other workloads
+# ------------------------------------------------------------------------------------------
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def batched_measure(precisions):
+    """All 256 irregular vertices (ten spins uniform in {1/2..6}, redrawn until all five
+    intertwiner ranges are non-empty; dl uniform in 0..12; gamma from {0.1, 1.2, 5.0}; seed 0), every
+    shell of every vertex, as one planned launch (persistent shell kernel + one reduction) replayed
+    as a CUDA graph, tiling autotuned on the first 2048 shells of every vertex."""
     import torch
     import paper_2107_13952_gb300 as sf
     from paper_2107_13952_gb300 import inputs
     batch = inputs.random_batch(256, seed=0)
     t = sf.sf_6j_table([sf.vertex(b["two_j"], b["gamma"], b["dl"]) for b in batch])
     sf.sf_boosters(t, RULE)
-    n = sum(min(shells, (b["dl"] + 1) ** 6) for b in batch)
+    n_all = sum((b["dl"] + 1) ** 6 for b in batch)
+    n_ne = int(sum(int(nonempty_shells(b["two_j"], b["dl"]).sum()) for b in batch))
     stream = torch.cuda.current_stream()
     res, outs = {}, {}
-    for name, prec in PRECISIONS.items():
-        plan = sf.Plan(t, prec, 0, shells)
-        tiling = plan.autotune(min(shells, 2048))
+    for name in precisions:
+        plan = sf.Plan(t, PRECISIONS[name])
+        tiling = plan.autotune(2048)
         plan.graph_launch()
         plan.sync()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1 = _events()
         e0.record(stream)
-        for _ in range(steps):
-            plan.graph_launch()
+        plan.graph_launch()
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
-        res[name] = {"value": n / (ms / 1e3), "unit": "shells/s", "ms_per_launch": ms,
-                     "tiling": {"x_chunk": tiling[0], "items_per_sm": tiling[1]}}
+        ms = e0.elapsed_time(e1)
+        res[name] = {"value": n_ne / (ms / 1e3), "unit": "non-empty shells/s", "all_shells_per_s": n_all / (ms / 1e3),
+                     "ms_per_launch": ms, "tiling": dict(zip(("x_chunk", "items_per_sm", "threads", "i3_split"), tiling))}
         outs[name] = [o.clone() for o in plan.outputs]
         del plan
-    den = sum(float(b.norm()) ** 2 for b in outs["fp64"]) ** 0.5
-    errs = {}
-    for name in ("mixed", "mixed_ff"):
-        num = sum(float((a - b).norm()) ** 2 for a, b in zip(outs[name], outs["fp64"])) ** 0.5
-        errs[name] = num / den if den > 0 else None
-    return {"workload": "256 irregular vertices (spins 1/2..6, dl 0..12, gamma 0.1/1.2/5.0, seed 0), shells "
-                        "[0, %d) of every vertex, %d shells in all; one CUDA-graph replay of a planned launch "
-                        "per step, %d steps; tables and boosters built once before the replays (not flushed "
-                        "between them)" % (shells, n, steps),
-            "fp64": res["fp64"], "mixed": res["mixed"], "mixed_ff": res["mixed_ff"],
-            "rel_err_vs_fp64": errs}
+    if "fp64" in outs:
+        den = sum(float(b.norm()) ** 2 for b in outs["fp64"]) ** 0.5
+        for name in outs:
+            if name != "fp64":
+                num = sum(float((a - b).norm()) ** 2 for a, b in zip(outs[name], outs["fp64"])) ** 0.5
+                res[name]["rel_err_vs_fp64"] = num / den
+    return dict(workload="256 irregular vertices (spins 1/2..6, dl 0..12, gamma 0.1/1.2/5.0, seed 0), all shells: "
+                         "%d (%d non-empty); one CUDA-graph replay of a planned launch, tiling autotuned; tables "
+                         "and boosters built before the replay" % (n_all, n_ne), **res)
 
 
-def other_workloads(large_fraction=32):
-    """The two remaining workloads, timed once each after a warm-up (CUDA events):
-    * spin 4, gamma 1.2, dl 20 (21^6 = 85,766,121 shells): the first 1/large_fraction of its
-      group-major shell range in the pair path and the FP64 path, and the relative error between them;
-    * spin 3, gamma 1.2, dl 8 (9^6 shells): the boundary-contracted amplitude and its gradients with
-      respect to the five seeded boundary vectors and the four booster tensors (adjoint kernels)."""
+def large_shell_measure(precisions):
+    """All spins 4, gamma 1.2, dl 20: all 21^6 = 85,766,121 shells (55,341,615 non-empty) in one call
+    per path, and the relative error of the mixed paths against the FP64 path."""
     import torch
     import paper_2107_13952_gb300 as sf
     from paper_2107_13952_gb300 import inputs
-    stream = torch.cuda.current_stream()
-
-    def timed(fn):
-        fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        out = fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1), out
-
-    res = {}
     w = inputs.large_shell()
     t = sf.sf_6j_table([sf.vertex(w["two_j"], w["gamma"], w["dl"])])
     sf.sf_boosters(t, RULE)
-    D = w["dl"] + 1
-    end = (D ** 3 // large_fraction) * D ** 3
-    lg = {"workload": "all spins 4, gamma 1.2, dl 20: shells [0, %d) of 85,766,121 (group-major)" % end}
-    outs = {}
-    for name, p in (("mixed_ff", sf.SF_MIXED_FF), ("fp64", sf.SF_FP64)):
-        ms, o = timed(lambda: sf.sf_vertex_amplitude(t, p, 0, end)[0].clone())
-        lg[name] = {"value": end / (ms / 1e3), "unit": "shells/s", "ms": ms}
-        outs[name] = o
-    lg["mixed_ff_vs_fp64_rel_err"] = float((outs["mixed_ff"] - outs["fp64"]).norm() / outs["fp64"].norm())
-    res["large_shell"] = lg
-    del t
+    n_ne = int(nonempty_shells(w["two_j"], w["dl"]).sum())
+    stream = torch.cuda.current_stream()
+    res, outs = {}, {}
+    for name in precisions:
+        e0, e1 = _events()
+        e0.record(stream)
+        A = sf.sf_vertex_amplitude(t, PRECISIONS[name])[0]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res[name] = {"value": n_ne / (ms / 1e3), "unit": "non-empty shells/s", "ms": ms,
+                     "kernel_ms": sf.last_kernel_ms()}
+        outs[name] = A.clone()
+    for name in outs:
+        if name != "fp64" and "fp64" in outs:
+            res[name]["rel_err_vs_fp64"] = float((outs[name] - outs["fp64"]).norm() / outs["fp64"].norm())
+    return dict(workload="all spins 4, gamma 1.2, dl 20: all 85,766,121 shells (%d non-empty), one call per path"
+                         % n_ne, **res)
+
+
+def adjoint_measure():
+    """All spins 3, gamma 1.2, dl 8 (531,441 shells): contracted amplitude and gradients with respect
+    to the five seeded boundary vectors and the four booster tensors (adjoint kernels, FP64), and the
+    amplitude alone."""
+    import torch
+    import paper_2107_13952_gb300 as sf
+    from paper_2107_13952_gb300 import inputs
     w = inputs.boundary_contraction_vertex()
     t = sf.sf_6j_table([sf.vertex(w["two_j"], w["gamma"], w["dl"])])
     sf.sf_boosters(t, RULE)
     dims = sf.intertwiner_ranges(w["two_j"], w["gamma"], w["dl"])[1]
     psis = [torch.tensor(v, dtype=torch.complex128, device="cuda") for v in inputs.boundary_vectors(dims)]
-    n = (w["dl"] + 1) ** 6
-    ms, _ = timed(lambda: sf.sf_vertex_adjoint(t, psis, want_grads=True))
-    res["adjoint"] = {"workload": "all spins 3, gamma 1.2, dl 8 (531,441 shells): contracted amplitude and "
-                                  "gradients w.r.t. five boundary vectors and four booster tensors, FP64",
-                      "value": n / (ms / 1e3), "unit": "shells/s", "ms": ms}
-    return res
+    n_ne = int(nonempty_shells(w["two_j"], w["dl"]).sum())
+    stream = torch.cuda.current_stream()
+    out = {}
+    for label, want in (("with_gradients", True), ("amplitude_only", False)):
+        sf.sf_vertex_adjoint(t, psis, want_grads=want)
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record(stream)
+        sf.sf_vertex_adjoint(t, psis, want_grads=want)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[label] = {"value": n_ne / (ms / 1e3), "unit": "non-empty shells/s", "ms": ms}
+    return dict(workload="all spins 3, gamma 1.2, dl 8 (531,441 shells, %d non-empty): boundary-contracted "
+                         "amplitude, FP64" % n_ne, **out)
 
 
+def simplex_measure():
+    """All spins 1, gamma 1.2, dl = 0..3, full rule: tables, boosters and the whole tensor per dl
+    (the smallest workload; launch-bound)."""
+    import torch
+    import paper_2107_13952_gb300 as sf
+    stream = torch.cuda.current_stream()
+    out = {}
+    for dl in range(4):
+        def run():
+            t = sf.sf_6j_table([sf.vertex((2,) * 10, 1.2, dl)])
+            sf.sf_boosters(t, RULE)
+            return sf.sf_vertex_amplitude(t, sf.SF_FP64)[0]
+        run()
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["dl%d" % dl] = {"ms_end_to_end": e0.elapsed_time(e1), "non_empty_shells": int(nonempty_shells((2,) * 10, dl).sum())}
+    return dict(workload="all spins 1, gamma 1.2, dl 0..3, FP64, tables + boosters + tensor per call", **out)
+
+
+def contraction_measure(hbm_peak, reps=5):
+    """The paper's GPU workload (Sec. 4, fig. contractions): complete contraction of two vertex
+    tensors and of one vertex tensor with five boundary vectors, all spins J = 2, 4, ..., 24 at
+    dl = 0 ((2J+1)^5 entries), seeded random FP64 tensors of those shapes (the cost depends on the
+    shape only); CUDA events over `reps` back-to-back launches after a warm one."""
+    import numpy as np
+    import torch
+    import paper_2107_13952_gb300 as sf
+    stream = torch.cuda.current_stream()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(2107)
+    rng = np.random.default_rng(13952)
+    rows = []
+    for J in range(2, 25, 2):
+        D = 2 * J + 1
+        A = torch.randn((D,) * 5, dtype=torch.float64, device="cuda", generator=g)
+        B = torch.randn((D,) * 5, dtype=torch.float64, device="cuda", generator=g)
+        psis = [rng.standard_normal(D) + 1j * rng.standard_normal(D) for _ in range(5)]
+        row = {"J": J, "entries": D ** 5, "bytes": 8 * D ** 5}
+        for label, fn, nbytes, fmas in (("vertex_vertex", lambda: sf.contract_vertices(A, B), 16 * D ** 5, D ** 5),
+                                        ("vertex_5_vectors", lambda: sf.contract_vectors(A, psis), 8 * D ** 5,
+                                         2 * D ** 5)):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = _events()
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            gbs = nbytes / (ms / 1e3) / 1e9
+            row[label] = {"ms": ms, "GB_per_s": gbs, "hbm_frac": gbs / hbm_peak,
+                          "fp64_frac": 2 * fmas / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
+        rows.append(row)
+        del A, B
+    return {"workload": "vertex tensors (2J+1)^5, J = 2..24 step 2, seeded random FP64; each launch synchronises "
+                        "(the timing includes one host round trip per call); inputs above the 129 MB L2 from J = 14",
+            "rows": rows}
+
+
+def delta3_measure():
+    """The Delta_3 network (Sec. 5) for boundary spins J = 1 and 2 at dl = 2, gamma 1.2: all
+    internal spins x, vertex tensors by the shell sum (one batched launch), contractions and the sum
+    over x on the GPU; end-to-end time per network."""
+    import numpy as np
+    import torch
+    import paper_2107_13952_gb300 as sf
+    from paper_2107_13952_gb300 import network as net
+    out = {}
+    stream = torch.cuda.current_stream()
+    for two_J in (2, 4):
+        D = two_J + 1
+        rng = np.random.default_rng(two_J)
+        psis = [v / np.linalg.norm(v) for v in (rng.standard_normal((9, D)) + 1j * rng.standard_normal((9, D)))]
+        net.delta3(two_J, 2, 1.2, psis, rule=RULE)
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record(stream)
+        xs, amps, tot, _ = net.delta3(two_J, 2, 1.2, psis, rule=RULE)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["J%d" % (two_J // 2)] = {"ms": e0.elapsed_time(e1), "internal_spins": len(xs),
+                                     "amplitude": [float(complex(tot).real), float(complex(tot).imag)]}
+    return dict(workload="Delta_3 graph, boundary spins J, dl 2, gamma 1.2, seeded unit boundary vectors, FP64", **out)
+
+
+# ------------------------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed_ff", choices=list(PRECISIONS),
-                    help="path timed for `value`; the other paths are timed for one step beside it")
-    ap.add_argument("--slices", type=int, default=16, help="steps per full pass over the sweep")
+    ap.add_argument("--precision", default=HEADLINE, choices=list(PRECISIONS), help="path timed for `value`")
+    ap.add_argument("--slices", type=int, default=32, help="steps per full pass over the sweep")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batched-shells", type=int, default=16384,
-                    help="shells per vertex of the 256-vertex batched measurement (0: skip)")
+    ap.add_argument("--no-other-workloads", action="store_true", help="time the sweep only")
     ap.add_argument("--case", default=None, help="lambda:groups:precision -- one shell-sum launch (profiling)")
-    ap.add_argument("--no-other-workloads", action="store_true", help="skip the spin-4 dl-20 and adjoint timings")
     args = ap.parse_args()
 
     if args.case:
@@ -381,31 +558,41 @@ def main():
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    total_shells_per_vertex = 11 ** 6
+    S = args.slices
+    G = 11 ** 3
+
+    def slice_bounds(k):
+        g0, g1 = G * k // S, G * (k + 1) // S
+        return g0 * 121 * 11, g1 * 121 * 11, g0, g1
+
+    import numpy as np
+    nonempty = {lam: np.cumsum(np.concatenate([[0], nonempty_shells((lam,) * 10, dl)])) for lam, dl in SWEEP}
+
+    def slice_shells(k):
+        b, e, _, _ = slice_bounds(k % S)
+        return sum(int(c[e] - c[b]) for c in nonempty.values()), 16 * (e - b)
 
     if args.impl == "reference":
         if rank != 0:
             return
-        rates = []
         n_all, t_all = 0, 0.0
         for i in range(args.warmup + args.steps):
             r, cores, n, el = oracle_rate(max(2.0, args.cpu_seconds / max(1, args.steps)), seed=i)
             if i >= args.warmup:
-                rates.append(r)
                 n_all += n
                 t_all += el
         value = n_all / t_all
-        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "shells/s",
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "non-empty shells/s",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * t_all / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": workload_name(args.slices), "slices_per_pass": args.slices,
-                           "sample": "the CPU oracle's shell-sum phase on %d shells drawn uniformly from the sweep "
-                                     "(boosters random), on all host cores" % n_all},
-                "cpu_baseline": {"value": value, "unit": "shells/s", "cores": cores, "kind": "oracle",
-                                 "sample": "%d shells drawn uniformly from the sweep's %d shells, boosters "
-                                           "random (shell-sum phase only)" % (n_all, 16 * total_shells_per_vertex)},
-                "e2e": {"value": value, "unit": "shells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                "config": {"workload": workload_name(S), "slices_per_pass": S,
+                           "sample": "the CPU oracle's shell-sum phase on %d non-empty shells drawn uniformly from the "
+                                     "sweep (boosters random), on all host cores" % n_all},
+                "cpu_baseline": {"value": value, "unit": "non-empty shells/s", "cores": cores, "kind": "oracle",
+                                 "sample": "%d non-empty shells drawn uniformly from the sweep's %d shells, boosters "
+                                           "random (shell-sum phase only)" % (n_all, 16 * 11 ** 6)},
+                "e2e": {"value": value, "unit": "non-empty shells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
 
@@ -417,177 +604,193 @@ def main():
     torch.cuda.set_device(local)
     import paper_2107_13952_gb300 as sf
     sf.load()
-    prec = PRECISIONS[args.precision]
+    hbm_peak = 6791.0
+    try:
+        hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        pass
     verts = [sf.vertex((lam,) * 10, GAMMA, dl) for lam, dl in SWEEP]
     dims = [sf.intertwiner_ranges((lam,) * 10, GAMMA, dl)[1] for lam, dl in SWEEP]
-    S = args.slices
-    N = total_shells_per_vertex
-    G = 11 ** 3
     outs = [torch.empty(d, dtype=torch.float64, device="cuda") for d in dims]
     host = [torch.empty(d, dtype=torch.float64, pin_memory=True) for d in dims]
     stream = torch.cuda.current_stream()
 
-    def slice_bounds(k):
-        g0, g1 = G * k // S, G * (k + 1) // S
-        return g0 * 121 * 11, g1 * 121 * 11, g0, g1
-
-    def step(k, to_host, p=None):
+    def step(k, prec, to_host):
         b, e, _, _ = slice_bounds(k % S)
         t = sf.sf_6j_table(verts)
         sf.sf_boosters(t, RULE)
-        sf.sf_vertex_amplitude(t, prec if p is None else p, b, e, out=outs)
+        sf.sf_vertex_amplitude(t, prec, b, e, out=outs)
         kms = sf.last_kernel_ms()
         if to_host:
             for o, h in zip(outs, host):
                 h.copy_(o, non_blocking=True)
         del t
-        return kms, 16 * (e - b)
+        return kms
 
     def barrier():
         if world > 1:
             dist.barrier()
 
-    # warm-up
-    for i in range(args.warmup):
-        step(i * world + rank, False)
-    torch.cuda.synchronize()
-
-    def timed(to_host, first):
+    def timed(prec, first, to_host):
         barrier()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        kms_all, shells, slices = [], 0, []
+        e0, e1 = _events()
+        kms_all, ne, alls, ks = [], 0, 0, []
         launches0 = sf.kernel_launches()
         e0.record(stream)
         for i in range(args.steps):
             k = (first + i) * world + rank
-            kms, n = step(k, to_host)
-            kms_all.append(kms)
-            shells += n
-            slices.append(k % S)
+            kms_all.append(step(k, prec, to_host))
+            a, b = slice_shells(k)
+            ne += a
+            alls += b
+            ks.append(k % S)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1)
-        return ms, kms_all, shells, slices, sf.kernel_launches() - launches0
+        return e0.elapsed_time(e1), kms_all, ne, alls, ks, sf.kernel_launches() - launches0
 
+    head = PRECISIONS[args.precision]
+    for i in range(args.warmup):
+        step(i * world + rank, head, False)
+    torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
-    ms, kms_all, shells, slices, launches = timed(False, args.warmup)
+    ms, kms_all, ne, alls, slices, launches = timed(head, args.warmup, False)
     clocks = clk.stop()
-    ms_e2e, _, shells_e2e, _, _ = timed(True, args.warmup + args.steps)
+    last = {args.precision: [o.clone() for o in outs]}
+    ms_e2e, _, ne_e2e, _, _, _ = timed(head, args.warmup, True)
 
-    # every path on one slice, timed the same way (one warm step each), and the relative error of
-    # the mixed paths against the FP64 path on that slice
-    kk = (args.warmup + 2 * args.steps) * world + rank
-    others, res_slice = {}, {}
+    # every other path over the same steps (same slices), and its last step's tensors
+    others = {}
     for name, p in PRECISIONS.items():
-        step(kk, False, p)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        kms_o, n_o = step(kk, False, p)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_o = e0.elapsed_time(e1)
-        res_slice[name] = [o.clone() for o in outs]
-        if name != args.precision:
-            others[name] = {"value": n_o * world / (ms_o / 1e3), "unit": "shells/s", "ms_per_step": ms_o,
-                            "kernel_ms_per_step": kms_o}
-    den = sum(float(r.norm()) ** 2 for r in res_slice["fp64"]) ** 0.5
-    rel_err = {}
-    for name in ("mixed", "mixed_ff"):
-        num = sum(float((o - r).norm()) ** 2 for o, r in zip(res_slice[name], res_slice["fp64"])) ** 0.5
-        rel_err[name] = num / den if den > 0 else None
-    # the same per vertex (per lambda), for both mixed paths
+        if name == args.precision:
+            continue
+        step(args.warmup * world + rank, p, False)
+        ms_o, kms_o, ne_o, all_o, _, _ = timed(p, args.warmup, False)
+        others[name] = {"value": ne_o * world / (ms_o / 1e3), "unit": "non-empty shells/s",
+                        "all_shells_per_s": all_o * world / (ms_o / 1e3), "ms_per_step": ms_o / args.steps,
+                        "kernel_ms_per_step": sum(kms_o) / args.steps, "dtype": DTYPES[name]}
+        last[name] = [o.clone() for o in outs]
+    # errors of the mixed paths against the FP64 path on the last slice, per lambda
     rel_err_per_lambda = {}
-    for name in ("mixed", "mixed_ff"):
+    for name in PRECISIONS:
+        if name == "fp64":
+            continue
         per = {}
-        for (lam, _), o, r in zip(SWEEP, res_slice[name], res_slice["fp64"]):
+        for (lam, _), o, r in zip(SWEEP, last[name], last["fp64"]):
             rn = float(r.norm())
             per[str(lam)] = float((o - r).norm()) / rn if rn > 0 else None
         rel_err_per_lambda[name] = per
 
-    # max over ranks
     if world > 1:
         tm = torch.tensor([ms, ms_e2e], device="cuda")
         dist.all_reduce(tm, op=dist.ReduceOp.MAX)
         ms, ms_e2e = float(tm[0]), float(tm[1])
-    total_shells = shells * world
-    value = total_shells / (ms / 1e3)
-    e2e_value = shells_e2e * world / (ms_e2e / 1e3)
+    value = ne * world / (ms / 1e3)
+    e2e_value = ne_e2e * world / (ms_e2e / 1e3)
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel (the shell sum): executed FP64 flops / event-timed duration
-    flops, ops32 = 0, 0
+    # cancellation factor per lambda on the last slice: kappa = sum_s ||C_s|| / ||A_slice||, the sum
+    # estimated from a seeded sample of the slice's non-empty shells (kappa pass of the library)
+    kappa = {}
+    kl = slices[-1]
+    b, e, _, _ = slice_bounds(kl)
+    rng = np.random.default_rng(13952)
+    for (lam, dl), r in zip(SWEEP, last["fp64"]):
+        ne_mask = nonempty_shells((lam,) * 10, dl)[b:e]
+        idx = np.nonzero(ne_mask)[0] + b
+        if len(idx) == 0 or float(r.norm()) == 0.0:
+            continue
+        pick = np.sort(rng.choice(idx, size=min(256, len(idx)), replace=False))
+        t1 = sf.sf_6j_table([sf.vertex((lam,) * 10, GAMMA, dl)])
+        sf.sf_boosters(t1, RULE)
+        _, ks = sf.sf_vertex_amplitude(t1, sf.SF_FP64, shell_list=pick, kappa=True)
+        kappa[str(lam)] = ks[0] * len(idx) / len(pick) / float(r.norm())
+        del t1
+    u32 = 2.0 ** -24
+    err_model = {name: {lam: (per[lam] / (kappa[lam] * u32) if lam in kappa and per[lam] is not None else None)
+                        for lam in per} for name, per in rel_err_per_lambda.items()}
+
+    # roofline of the dominant kernel (the shell sum of the timed path)
+    f64, f32, tcm, canon = 0, 0, 0, 0.0
+    canon_cum = {lam: np.cumsum(np.concatenate([[0.0], canonical_flops((lam,) * 10, dl)])) for lam, dl in SWEEP}
     for k in slices:
-        _, _, g0, g1 = slice_bounds(k)
+        bb, ee, g0, g1 = slice_bounds(k)
         for lam, dl in SWEEP:
-            f64, f32 = pipe_ops(executed_fmas((lam,) * 10, dl, g0, g1), args.precision)
-            flops += f64
-            ops32 += f32
+            a64, a32, atc = pipe_ops(executed_fmas((lam,) * 10, dl, g0, g1), args.precision)
+            f64 += a64
+            f32 += a32
+            tcm += atc
+            canon += float(canon_cum[lam][ee] - canon_cum[lam][bb])
     kern_s = sum(kms_all) / 1e3
-    fp64_tflops = flops / kern_s / 1e12 if kern_s > 0 else None
-    fp32_tops = ops32 / kern_s / 1e12 if kern_s > 0 else None
-    if args.precision == "mixed_ff":
-        # the FP32 pipe carries the kernel: lane operations (FFMA, FADD, FMUL) per second
-        roof = {"bound": "alu", "achieved": fp32_tops, "peak": FP32_PEAK_TOPS, "unit": "Tops/s (FP32 lane ops)",
-                "frac": (fp32_tops / FP32_PEAK_TOPS) if fp32_tops else None,
-                "ops_counted": "FP32 lane operations of the loops (compensated-pair steps at 11-12 operations per "
-                               "multiply-add, FP32 booster contractions at one FFMA), trip counts x operations",
-                "fp64_tflops": fp64_tflops, "fp64_frac": (fp64_tflops / FP64_PEAK_TFLOPS) if fp64_tflops else None}
-    else:
-        roof = {"bound": "alu", "achieved": fp64_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": (fp64_tflops / FP64_PEAK_TFLOPS) if fp64_tflops else None,
-                "flops_counted": "FP64-pipe FMAs the kernel executes x 2 (loop trip counts); the FP32 phases of the "
-                                 "mixed path are reported separately",
-                "fp32_tops": fp32_tops}
+    fp64_tflops = f64 / kern_s / 1e12
+    roof = {"bound": "alu", "achieved": fp64_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": fp64_tflops / FP64_PEAK_TFLOPS,
+            "peak_note": "FP64 pipe, derived: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (no measured FP64 figure)",
+            "counted": "FP64 flops the kernel's loops execute in this path's FP64 phases (x-sum and k5 contraction "
+                       "for mixed_tc), 2 per multiply-add, from the trip counts",
+            "fp32_lane_ops_per_s": f32 / kern_s / 1e12, "fp32_frac": f32 / kern_s / 1e12 / FP32_PEAK_TOPS,
+            "tensor_mma_macs": tcm, "tensor_tflops_unpadded": 2 * tcm / kern_s / 1e12,
+            "canonical_tflops": canon / kern_s / 1e12, "canonical_frac": canon / kern_s / 1e12 / FP64_PEAK_TFLOPS,
+            "canonical_note": "the framed algorithm's FP64 flop count (W by the x-sum plus four mode products per "
+                              "non-empty shell) over the kernel time: above 1 because the hoisted order executes a "
+                              "fraction of those operations",
+            "kernel": "k_shell<%d>" % head, "kernel_ms_per_step": 1e3 * kern_s / args.steps}
     traffic = None
-    if NCU_TRAFFIC["sha1"] == kernel_sha1():
-        traffic = NCU_TRAFFIC["bytes_per_launch"].get(args.precision)
+    if NCU_TRAFFIC["sha1"] == kernel_sha1() and NCU_TRAFFIC["bytes_per_launch"]:
+        traffic = NCU_TRAFFIC["bytes_per_launch"]
+    roof["traffic"] = traffic
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         r, cores, n, el = oracle_rate(args.cpu_seconds)
-        cpu = {"value": r, "unit": "shells/s", "cores": cores, "kind": "oracle",
-               "sample": "%d shells drawn uniformly from the sweep (%.1f s on %d processes), boosters random "
-                         "(shell-sum phase only)" % (n, el, cores)}
+        cpu = {"value": r, "unit": "non-empty shells/s", "cores": cores, "kind": "oracle",
+               "sample": "%d non-empty shells drawn uniformly from the sweep (%.1f s on %d processes), boosters "
+                         "random (shell-sum phase only)" % (n, el, cores)}
 
-    batched = None
-    if args.batched_shells > 0 and world == 1:
-        batched = batched_measure(args.batched_shells)
-    others_w = None
+    extra = {}
     if not args.no_other_workloads and world == 1:
-        others_w = other_workloads()
+        main_paths = ["mixed_tc", "fp64", "mixed_ff"]
+        extra["batched_256"] = batched_measure(main_paths)
+        extra["large_shell_j4_dl20"] = large_shell_measure(main_paths)
+        extra["adjoint_j3_dl8"] = adjoint_measure()
+        extra["simplex_j1"] = simplex_measure()
+        extra["contractions"] = contraction_measure(hbm_peak)
+        extra["delta3"] = delta3_measure()
 
     d2h = sum(h.numel() * 8 for h in host)
-    h2d = len(verts) * 56
+    h2d = len(verts) * ctypes.sizeof(sf.sf_vertex) + ctypes.sizeof(sf.sf_quad_rule)
     line = {
         "metric": METRIC,
-        "value": value, "unit": "shells/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "value": value, "unit": "non-empty shells/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "mixed": "f64+f32", "mixed_ff": "f64+f32+f32x2"}[args.precision], "data": "synthetic",
-        "config": {"workload": workload_name(S),
-                   "slices_per_pass": S, "precision": args.precision,
+        "dtype": DTYPES[args.precision], "data": "synthetic",
+        "config": {"workload": workload_name(S), "slices_per_pass": S, "precision": args.precision,
+                   "counting": "non-empty shells (all four virtual-intertwiner ranges non-empty); all_shells_per_s "
+                               "counts the whole (dl+1)^6 grid",
                    "cache": "inputs larger than L2: every step rebuilds the {6j} tables, d-tables and boosters of "
                             "all 16 vertices (the spin-8 S3 table alone, FP64 plus pair copy, is 384 MB, 3x the "
                             "L2), so no step starts with its working set in L2; no separate flush"},
-        "roofline": dict(roof, traffic=traffic, kernel="k_shell<%d>" % PRECISIONS[args.precision],
-                         kernel_ms_per_step=1e3 * kern_s / args.steps),
+        "all_shells_per_s": alls * world / (ms / 1e3),
+        "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": "shells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": "non-empty shells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clocks,
         "path": args.precision,
+        "precision_split": PHASE_PRECISION[args.precision],
         "other_paths": others,
-        "batched": batched,
-        "other_workloads": others_w,
-        "mixed_vs_fp64": {"rel_err": rel_err, "rel_err_per_lambda": rel_err_per_lambda, "stated_bound": 1e-6,
-                          "metric": "||A_mixed - A_fp64|| / ||A_fp64|| over the 16 vertices of one slice"},
+        "speedup_vs_fp64": value / others["fp64"]["value"] if "fp64" in others else None,
+        "mixed_vs_fp64": {"rel_err_per_lambda": rel_err_per_lambda, "kappa_per_lambda": kappa,
+                          "rel_err_over_kappa_u32": err_model, "stated_bound": 1e-6,
+                          "metric": "||A_mixed - A_fp64|| / ||A_fp64|| per vertex on the last timed slice; kappa "
+                                    "estimated from 256 seeded non-empty shells of that slice per vertex"},
+        **extra,
     }
     print(json.dumps(line))
     if world > 1:

@@ -47,6 +47,7 @@ struct VertexHost {
     Table6j S[5];
     float* d_S4f = nullptr;
     float* d_S5f = nullptr;
+    double* d_S1x = nullptr;
     float2* d_Sff[3] = {nullptr, nullptr, nullptr};
     int64_t ntrip = 0;
     int32_t dkmax[4];
@@ -289,6 +290,7 @@ static int upload_vtxdev(sf_tables* t) {
         d.nshell = h.nshell;
         for (int k = 0; k < 5; k++) { d.S[k] = h.S[k].d_vals; d.slot[k] = h.S[k].d_slots; }
         d.S4f = h.d_S4f;
+        d.S1x = h.d_S1x;
         d.S5f = h.d_S5f;
         for (int k = 0; k < 3; k++) d.Sff[k] = h.d_Sff[k];
         for (int e = 0; e < 4; e++) {
@@ -361,6 +363,7 @@ extern "C" int sf_6j_table(const sf_vertex* v, int32_t n, sf_tables** out, cudaS
             for (int k = 0; k < 5 && rc == SF_OK; k++) {
                 if (k == 3) rc = dev_alloc(t, (void**)&h.d_S4f, h.S[3].n * sizeof(float));
                 if (k == 4) rc = dev_alloc(t, (void**)&h.d_S5f, h.S[4].n * sizeof(float));
+                if (k == 0 && rc == SF_OK) rc = dev_alloc(t, (void**)&h.d_S1x, h.S[0].n * sizeof(double));
                 if (k < 3) rc = dev_alloc(t, (void**)&h.d_Sff[k], h.S[k].n * sizeof(float2));
                 if (rc != SF_OK) break;
                 rc = dev_alloc(t, (void**)&h.S[k].d_slots, h.S[k].slots.size() * sizeof(SlotDesc));
@@ -405,6 +408,7 @@ extern "C" int sf_6j_table(const sf_vertex* v, int32_t n, sf_tables** out, cudaS
                 rc = sf_sixj_table_build(k + 1, t->d_vtx + i, h.S[k].d_slots, (int)h.S[k].slots.size(), h.S[k].n,
                                          h.S[k].d_vals, d_tri, tri_m, t->d_status, t->num_sms, stream);
             if (rc == SF_OK) rc = sf_to_float(h.S[3].d_vals, h.d_S4f, h.S[3].n, t->num_sms, stream);
+            if (rc == SF_OK) rc = sf_scale_x(h.S[0].d_vals, h.S[0].d_slots, (int)h.S[0].slots.size(), h.d_S1x, stream);
             if (rc == SF_OK) rc = sf_to_float(h.S[4].d_vals, h.d_S5f, h.S[4].n, t->num_sms, stream);
             for (int k = 0; k < 3 && rc == SF_OK; k++) rc = sf_to_ff(h.S[k].d_vals, h.d_Sff[k], h.S[k].n, t->num_sms, stream);
         }

@@ -224,6 +224,7 @@ struct VtxDev {
     int32_t olo[5], od[5];     // output sub-range per edge: first index within the range, count
     int64_t nshell;            // D^6
     const double* S[5];        // {6j} tables S1..S5
+    const double* S1x;         // S1 times the x-sum weight (2x+1), rounded once (FP64 paths)
     const float* S4f;          // S4 rounded to FP32 once (mixed paths)
     const float* S5f;          // S5 rounded to FP32 once (SF_MIXED_FF)
     const float2* Sff[3];      // S1, S2, S3 as (hi, lo) float pairs, hi + lo = S to about 2^-48 (SF_MIXED_FF)
@@ -269,6 +270,8 @@ int sf_tri_table_build(int m, const dd* F, dd* d_out, int num_sms, cudaStream_t 
 int sf_sixj_table_build(int table_id, const VtxDev* d_v, const SlotDesc* d_slots, int nslots, int64_t n,
                         double* d_out, const dd* d_tri, int tri_m, int* d_status, int num_sms, cudaStream_t s);
 int sf_to_float(const double* d_in, float* d_out, int64_t n, int num_sms, cudaStream_t s);
+// (2x+1) S[entry] per slot entry (x = the entry's third argument, doubled)
+int sf_scale_x(const double* d_in, const SlotDesc* d_slots, int nslots, double* d_out, cudaStream_t s);
 // (hi, lo) float pairs: hi = fl32(d), lo = fl32(d - hi)
 int sf_to_ff(const double* d_in, float2* d_out, int64_t n, int num_sms, cudaStream_t s);
 // Gauss-Legendre library of the d-table kernel (sizes 64..SF_GL_NMAX in steps of 32), built once

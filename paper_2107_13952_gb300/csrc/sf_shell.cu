@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                             d = fdiv_q(r, f_mdk);
                             c2 = r - d * mdk;
                         };
-                        using T2 = typename std::conditional<FF, float2, double2>::type;
+                        using T2 = typename std::conditional<FF || TC, float2, double2>::type;
                         gather_loop<GU>(D * mdk * nxc, tid, nth, [&](int q) {
                             int d, c2, xc;
                             sb_at(q, d, c2, xc);
@@ -669,7 +669,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                             if (c2 < s_nk2[d]) {
                                 const int k2 = s_k2lo[d] + 2 * c2, x = xc0 + 2 * xc;
                                 const int64_t bi = ((int64_t)((d * D + d24) * D + d25) * v.di[1] + ci2) * v.dkmax[0] + c2;
-                                if constexpr (FF) {
+                                if constexpr (FF || TC) {
                                     val.x = __ldg(v.Bf[0] + bi);
                                     val.y = s6f(v.S5f, sd5, k2, i1, x);
                                 } else {
@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                             sb_at(q, d, c2, xc);
                             if (c2 >= s_nk2[d]) return;
                             const int k2 = s_k2lo[d] + 2 * c2;
-                            if constexpr (FF) {
+                            if constexpr (FF || TC) {
                                 const float f = (float)(k2 + 1) * ((c2 & 1) ? -s_sigf[d] : s_sigf[d]);
                                 reinterpret_cast<float*>(sm.SB)[(d * mdk + c2) * XC + xc] = (f * val.x) * val.y;
                             } else {
@@ -703,7 +703,17 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                             c4 = fdiv_q(r, f_nk3u);
                             ku = r - c4 * nk3u;
                         };
-                        if constexpr (FF) {
+                        if constexpr (TC) {
+                            gather_loop<4>(nxc * nk4 * nk3u, tid, nth, [&](int q) {
+                                int xc, c4, ku;
+                                s3_at(q, xc, c4, ku);
+                                return s6ff(v.Sff[2], sd3, k4lo + 2 * c4, k3ulo + 2 * ku, xc0 + 2 * xc).x;
+                            }, [&](int q, float val) {
+                                int xc, c4, ku;
+                                s3_at(q, xc, c4, ku);
+                                reinterpret_cast<float*>(sm.S3s)[(xc * nk4 + c4) * nk3u + ku] = val;
+                            });
+                        } else if constexpr (FF) {
                             gather_loop<4>(nxc * nk4 * nk3u, tid, nth, [&](int q) {
                                 int xc, c4, ku;
                                 s3_at(q, xc, c4, ku);
@@ -721,8 +731,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                             }, [&](int q, double val) {
                                 int xc, c4, ku;
                                 s3_at(q, xc, c4, ku);
-                                if constexpr (TC) reinterpret_cast<float*>(sm.S3s)[(xc * nk4 + c4) * nk3u + ku] = (float)val;
-                                else sm.S3s[(xc * nk4 + c4) * nk3u + ku] = val;
+                                sm.S3s[(xc * nk4 + c4) * nk3u + ku] = val;
                             });
                         }
                     }
@@ -739,13 +748,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                                 ff_mul_f(ff_mul(make_float2(val.x, val.y), make_float2(val.z, val.w)), (float)(x + 1));
                         });
                     } else {
+                        // (2x+1) S1 comes from the prescaled copy S1x: the same rounding as forming
+                        // (x+1) * S1 here, so Q is bitwise the product ((x+1) S1) S2
                         gather_loop<GU>(nk5 * nk4 * nxc, tid, nth, [&](int q) {
                             const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, c5 = fdiv_q(r, f_nk4), c4 = r - c5 * nk4;
                             const int k5 = k5lo + 2 * c5, k4 = k4lo + 2 * c4, x = xc0 + 2 * xc;
-                            return make_double2(s6(v.S[0], sd1, i1, k5, x), s6(v.S[1], sd2, k5, k4, x));
+                            return make_double2(s6(v.S1x, sd1, i1, k5, x), s6(v.S[1], sd2, k5, k4, x));
                         }, [&](int q, double2 val) {
-                            const int x = xc0 + 2 * (q - fdiv_q(q, f_nxc) * nxc);
-                            sm.Q[q] = (double)(x + 1) * val.x * val.y;
+                            sm.Q[q] = val.x * val.y;
                         });
                     }
                     __syncthreads();
@@ -761,8 +771,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                         const int ia = (k3 - sd4.alo) >> 1, ix = (x - sd4.xlo) >> 1, ib0 = (k2lo - sd4.blo) >> 1;
                         const bool inbox = (unsigned)ix < (unsigned)sd4.nx && ((x - sd4.xlo) & 1) == 0;
                         const double* s4p = v.S[3] + sd4.off + ((int64_t)ia * sd4.nb + ib0) * sd4.nx + ix;
-                        const double sgn3 = (double)(k3 + 1) * ((c3 & 1) ? -1.0 : 1.0);
                         if constexpr (MIX) {
+                            const float sgn3 = (float)(k3 + 1) * ((c3 & 1) ? -1.0f : 1.0f);
                             const float* sbp = reinterpret_cast<const float*>(sm.SB) + (d * mdk) * XC + xc;
                             // the FP32 copy of S4 holds the same roundings as converting each entry here
                             const float* s4f = v.S4f + sd4.off + ((int64_t)ia * sd4.nb + ib0) * sd4.nx + ix;
@@ -780,8 +790,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                                 }
                                 for (; c2 < nk2; c2++) acc0 = fmaf(__ldg(s4f + c2 * nx), sbp[c2 * XC], acc0);
                             }
-                            reinterpret_cast<float*>(sm.R)[(d * mdk + c3) * XC + xc] = ((acc0 + acc1) + (acc2 + acc3)) * (float)sgn3;
+                            reinterpret_cast<float*>(sm.R)[(d * mdk + c3) * XC + xc] = ((acc0 + acc1) + (acc2 + acc3)) * sgn3;
                         } else {
+                            const double sgn3 = (double)(k3 + 1) * ((c3 & 1) ? -1.0 : 1.0);
                             const double* sbp = sm.SB + (d * mdk) * XC + xc;
                             double acc0 = 0.0, acc1 = 0.0;
                             if (inbox) {

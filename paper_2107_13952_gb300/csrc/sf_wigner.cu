@@ -115,6 +115,24 @@ __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ ou
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = (float)in[i];
 }
 
+// S1 with the weight (x+1) = 2x+1 (doubled x) of the x-sum folded in: one CTA per slot
+__global__ void k_scale_x(const double* __restrict__ in, const SlotDesc* __restrict__ slots, double* __restrict__ out) {
+    const SlotDesc sd = slots[blockIdx.x];
+    const int64_t n = (int64_t)sd.na * sd.nb * sd.nx;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const int ix = (int)(i % sd.nx);
+        out[sd.off + i] = (double)(sd.xlo + 2 * ix + 1) * in[sd.off + i];
+    }
+}
+
+int sf_scale_x(const double* d_in, const SlotDesc* d_slots, int nslots, double* d_out, cudaStream_t s) {
+    if (nslots <= 0) return SF_OK;
+    k_scale_x<<<nslots, 256, 0, s>>>(d_in, d_slots, d_out);
+    sf_note_launch(1);
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
 __global__ void k_to_ff(const double* __restrict__ in, float2* __restrict__ out, int64_t n) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
