@@ -77,82 +77,7 @@ def kernel_sha1():
 # ------------------------------------------------------------------------------------------
 # shell bookkeeping on the host (numpy): non-empty shells, executed and canonical operation counts
 # ------------------------------------------------------------------------------------------
-def _pair(a, b, c, d):
-    import numpy as np
-    a, b, c, d = np.broadcast_arrays(a, b, c, d)
-    lo = np.maximum(np.abs(a - b), np.abs(c - d))
-    hi = np.minimum(a + b, c + d)
-    n = np.where(((a + b + c + d) % 2 == 0) & (hi >= lo), (hi - lo) // 2 + 1, 0)
-    return lo, n
-
-
-def _shell_axes(tj, dl):
-    """The six free-face spins on a broadcast grid, axes (d25, d35, d45, d24, d34, d23): the
-    group-major linear shell order of the library, so the flattened grid is indexed by s."""
-    import numpy as np
-    D = dl + 1
-    d = np.arange(D)
-    sh = [1] * 6
-
-    def ax(i):
-        s = list(sh)
-        s[i] = D
-        return d.reshape(s)
-    j12, j13, j14, j15, j23, j24, j25, j34, j35, j45 = tj
-    return (j25 + 2 * ax(0), j35 + 2 * ax(1), j45 + 2 * ax(2), j24 + 2 * ax(3), j34 + 2 * ax(4), j23 + 2 * ax(5))
-
-
-def nonempty_shells(tj, dl):
-    """Boolean array over the linear shell index: all four k ranges of the shell non-empty."""
-    import numpy as np
-    j12, j13, j14, j15 = tj[:4]
-    l25, l35, l45, l24, l34, l23 = _shell_axes(tj, dl)
-    ok = ((_pair(j15, l25, l35, l45)[1] > 0) & (_pair(l45, j14, l24, l34)[1] > 0)
-          & (_pair(l23, l24, l25, j12)[1] > 0) & (_pair(l34, l35, j13, l23)[1] > 0))
-    return np.broadcast_to(ok, (dl + 1,) * 6).reshape(-1)
-
-
-def canonical_flops(tj, dl):
-    """Per-shell FP64 flop count of the framed algorithm (W by the x-sum, then four mode products,
-    FMA = 2 flops) over the linear shell index; zero for empty shells."""
-    import numpy as np
-    from paper_2107_13952_gb300 import intertwiner_ranges
-    lo, dim = intertwiner_ranges(tj, GAMMA, dl)
-    j12, j13, j14, j15 = tj[:4]
-    l25, l35, l45, l24, l34, l23 = _shell_axes(tj, dl)
-    k5lo, n5 = _pair(j15, l25, l35, l45)
-    k4lo, n4 = _pair(l45, j14, l24, l34)
-    k2lo, n2 = _pair(l23, l24, l25, j12)
-    k3lo, n3 = _pair(l34, l35, j13, l23)
-    shape = (dl + 1,) * 6
-    i1 = lo[0] + 2 * np.arange(dim[0])
-
-    def count_tri(lo_, n_, a, x):
-        # labels k = lo_ + 2c, c < n_, with |k - a| <= x <= k + a and k + a + x even
-        c = np.arange(int(np.max(n_)) + 1 if np.size(n_) else 1)
-        kk = np.asarray(lo_)[..., None] + 2 * c
-        valid = c < np.asarray(n_)[..., None]
-        okt = (np.abs(kk - np.asarray(a)[..., None]) <= x) & (x <= kk + np.asarray(a)[..., None]) & \
-              ((kk + np.asarray(a)[..., None] + x) % 2 == 0)
-        return (valid & okt).sum(axis=-1)
-    # the parity of x is that of i1 + l25 (fixed per shell), so only every other x contributes; each
-    # count is formed on the small grid of the faces it depends on and broadcast in the product
-    xmax = int(2 * max(tj) + 4 * dl + 2)
-    w = np.zeros(shape)
-    for x in range(0, xmax + 1):
-        m1 = ((np.abs(i1[None, :] - np.asarray(l25).reshape(-1, 1)) <= x)
-              & (x <= i1[None, :] + np.asarray(l25).reshape(-1, 1))
-              & ((i1[None, :] + np.asarray(l25).reshape(-1, 1) + x) % 2 == 0)).sum(axis=1).reshape(np.shape(l25))
-        if not m1.any():
-            continue
-        w += m1 * count_tri(k5lo, n5, j14, x) * count_tri(k4lo, n4, l35, x) * count_tri(k3lo, n3, l24, x) \
-            * count_tri(k2lo, n2, j13, x)
-    n2, n3, n4, n5 = (np.broadcast_to(v, shape) for v in (n2, n3, n4, n5))
-    d1, d2, d3, d4, d5 = dim
-    contr = (d1 * d2 * n2 * n3 * n4 * n5 + d1 * d2 * d3 * n3 * n4 * n5 + d1 * d2 * d3 * d4 * n4 * n5
-             + d1 * d2 * d3 * d4 * d5 * n5)
-    live = (n2 > 0) & (n3 > 0) & (n4 > 0) & (n5 > 0)
-    return np.where(live, 2.0 * w + 2.0 * contr, 0.0).reshape(-1)
+from paper_2107_13952_gb300.shells import _pair, _shell_axes, canonical_flops, nonempty_shells  # noqa: E402
 
 
 def executed_fmas(tj, dl, g0, g1):
@@ -631,14 +556,14 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def timed(prec, first, to_host):
+    def timed(prec, first, to_host, nsteps=None):
         barrier()
         torch.cuda.synchronize()
         e0, e1 = _events()
         kms_all, ne, alls, ks = [], 0, 0, []
         launches0 = sf.kernel_launches()
         e0.record(stream)
-        for i in range(args.steps):
+        for i in range(nsteps or args.steps):
             k = (first + i) * world + rank
             kms_all.append(step(k, prec, to_host))
             a, b = slice_shells(k)
@@ -659,26 +584,34 @@ def main():
     ms, kms_all, ne, alls, slices, launches = timed(head, args.warmup, False)
     clocks = clk.stop()
     last = {args.precision: [o.clone() for o in outs]}
-    ms_e2e, _, ne_e2e, _, _, _ = timed(head, args.warmup, True)
+    n_short = min(args.steps, 4)
+    ms_e2e, _, ne_e2e, _, _, _ = timed(head, args.warmup, True, n_short)
 
-    # every other path over the same steps (same slices), and its last step's tensors
+    # the FP64 path and SF_MIXED over the same steps (same slices), the pair path over the first
+    # min(steps, 4) of them (its last slice is then compared with the FP64 path's tensors of that
+    # slice, recomputed), and each path's tensors of its last step
     others = {}
     for name, p in PRECISIONS.items():
         if name == args.precision:
             continue
+        n = args.steps if name in ("fp64", "mixed") else n_short
         step(args.warmup * world + rank, p, False)
-        ms_o, kms_o, ne_o, all_o, _, _ = timed(p, args.warmup, False)
+        ms_o, kms_o, ne_o, all_o, ks_o, _ = timed(p, args.warmup, False, n)
         others[name] = {"value": ne_o * world / (ms_o / 1e3), "unit": "non-empty shells/s",
-                        "all_shells_per_s": all_o * world / (ms_o / 1e3), "ms_per_step": ms_o / args.steps,
-                        "kernel_ms_per_step": sum(kms_o) / args.steps, "dtype": DTYPES[name]}
+                        "all_shells_per_s": all_o * world / (ms_o / 1e3), "ms_per_step": ms_o / n, "steps": n,
+                        "kernel_ms_per_step": sum(kms_o) / n, "dtype": DTYPES[name]}
         last[name] = [o.clone() for o in outs]
+        if n != args.steps:   # compare on the slice it ended on: the FP64 path on that slice
+            step(ks_o[-1], PRECISIONS["fp64"], False)
+            last[name + "@fp64"] = [o.clone() for o in outs]
     # errors of the mixed paths against the FP64 path on the last slice, per lambda
     rel_err_per_lambda = {}
     for name in PRECISIONS:
         if name == "fp64":
             continue
         per = {}
-        for (lam, _), o, r in zip(SWEEP, last[name], last["fp64"]):
+        ref = last.get(name + "@fp64", last["fp64"])
+        for (lam, _), o, r in zip(SWEEP, last[name], ref):
             rn = float(r.norm())
             per[str(lam)] = float((o - r).norm()) / rn if rn > 0 else None
         rel_err_per_lambda[name] = per
@@ -695,26 +628,21 @@ def main():
             dist.destroy_process_group()
         return
 
-    # cancellation factor per lambda on the last slice: kappa = sum_s ||C_s|| / ||A_slice||, the sum
-    # estimated from a seeded sample of the slice's non-empty shells (kappa pass of the library)
+    # cancellation factor per lambda on the last slice: kappa = sum_s ||C_s|| / ||A_slice||, over
+    # every shell of the slice (kappa pass of the library, FP64)
     kappa = {}
-    kl = slices[-1]
-    b, e, _, _ = slice_bounds(kl)
-    rng = np.random.default_rng(13952)
-    for (lam, dl), r in zip(SWEEP, last["fp64"]):
-        ne_mask = nonempty_shells((lam,) * 10, dl)[b:e]
-        idx = np.nonzero(ne_mask)[0] + b
-        if len(idx) == 0 or float(r.norm()) == 0.0:
-            continue
-        pick = np.sort(rng.choice(idx, size=min(256, len(idx)), replace=False))
-        t1 = sf.sf_6j_table([sf.vertex((lam,) * 10, GAMMA, dl)])
-        sf.sf_boosters(t1, RULE)
-        _, ks = sf.sf_vertex_amplitude(t1, sf.SF_FP64, shell_list=pick, kappa=True)
-        kappa[str(lam)] = ks[0] * len(idx) / len(pick) / float(r.norm())
-        del t1
+    b, e, _, _ = slice_bounds(slices[-1])
+    tk = sf.sf_6j_table(verts)
+    sf.sf_boosters(tk, RULE)
+    _, ks = sf.sf_vertex_amplitude(tk, sf.SF_FP64, b, e, kappa=True)
+    for (lam, dl), r, kv in zip(SWEEP, last["fp64"], ks):
+        if float(r.norm()) > 0.0:
+            kappa[str(lam)] = kv / float(r.norm())
+    del tk
     u32 = 2.0 ** -24
     err_model = {name: {lam: (per[lam] / (kappa[lam] * u32) if lam in kappa and per[lam] is not None else None)
-                        for lam in per} for name, per in rel_err_per_lambda.items()}
+                        for lam in per} for name, per in rel_err_per_lambda.items()
+                 if name + "@fp64" not in last}   # the paths compared on the slice kappa is taken on
 
     # roofline of the dominant kernel (the shell sum of the timed path)
     f64, f32, tcm, canon = 0, 0, 0, 0.0
@@ -788,8 +716,8 @@ def main():
         "speedup_vs_fp64": value / others["fp64"]["value"] if "fp64" in others else None,
         "mixed_vs_fp64": {"rel_err_per_lambda": rel_err_per_lambda, "kappa_per_lambda": kappa,
                           "rel_err_over_kappa_u32": err_model, "stated_bound": 1e-6,
-                          "metric": "||A_mixed - A_fp64|| / ||A_fp64|| per vertex on the last timed slice; kappa "
-                                    "estimated from 256 seeded non-empty shells of that slice per vertex"},
+                          "metric": "||A_mixed - A_fp64|| / ||A_fp64|| per vertex on the last timed slice; kappa = "
+                                    "sum over that slice's shells of ||C_s|| / ||A_slice||"},
         **extra,
     }
     print(json.dumps(line))
