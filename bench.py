@@ -56,8 +56,9 @@ PHASE_PRECISION = {"fp64": dict(B="64", C="64", D="64", F="64", G="64", H="64"),
                    "mixed_tc": dict(B="32", C="32", D="32", F="64", G="tc", H="64")}
 FF_OPS = {"D": 11, "F": 12}   # FP32 lane operations per multiply-add of the pair phases
 # DRAM bytes (read + write) per launch of the headline shell-sum kernel from one ncu capture of the
-# benchmark's first timed launch, valid while the kernel source hashes to "sha1"
-NCU_TRAFFIC = {"sha1": None, "bytes_per_launch": None}
+# benchmark's first timed launch after three warm-up steps (slice 3 of 32), valid while the kernel
+# source hashes to "sha1"
+NCU_TRAFFIC = {"sha1": "39b46336c37b", "bytes_per_launch": 2244882432 + 75384064}
 
 
 def workload_name(slices):
@@ -423,8 +424,9 @@ def contraction_measure(hbm_peak, reps=5):
                           "fp64_frac": 2 * fmas / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
         rows.append(row)
         del A, B
-    return {"workload": "vertex tensors (2J+1)^5, J = 2..24 step 2, seeded random FP64; each launch synchronises "
-                        "(the timing includes one host round trip per call); inputs above the 129 MB L2 from J = 14",
+    return {"workload": "vertex tensors (2J+1)^5, J = 2..24 step 2, seeded random FP64; %d back-to-back stream-ordered "
+                        "calls per timing (each with its small stream-ordered scratch allocation); inputs above the "
+                        "129 MB L2 from J = 14" % reps,
             "rows": rows}
 
 
@@ -467,7 +469,25 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-workloads", action="store_true", help="time the sweep only")
     ap.add_argument("--case", default=None, help="lambda:groups:precision -- one shell-sum launch (profiling)")
+    ap.add_argument("--contract-case", type=int, default=None,
+                    help="J -- one vertex-vertex and one vertex-5-vectors contraction of (2J+1)^5 tensors (profiling)")
     args = ap.parse_args()
+
+    if args.contract_case:
+        import numpy as np
+        import torch
+        import paper_2107_13952_gb300 as sf
+        D = 2 * args.contract_case + 1
+        g = torch.Generator(device="cuda")
+        g.manual_seed(2107)
+        A = torch.randn((D,) * 5, dtype=torch.float64, device="cuda", generator=g)
+        B = torch.randn((D,) * 5, dtype=torch.float64, device="cuda", generator=g)
+        rng = np.random.default_rng(13952)
+        psis = [rng.standard_normal(D) + 1j * rng.standard_normal(D) for _ in range(5)]
+        vv = float(sf.contract_vertices(A, B))
+        a = complex(sf.contract_vectors(A, psis))
+        print(json.dumps({"contract_case": args.contract_case, "vertex_vertex": vv, "vertex_5_vectors": [a.real, a.imag]}))
+        return
 
     if args.case:
         # one shell-sum launch on a small range of one vertex (for profiler captures)

@@ -286,13 +286,16 @@ int sf_vertex_adjoint(sf_tables* t, sf_precision precision, const double* const 
  *   n_vec = 5: out[0]      = sum_{i1..i5} A psi_1 ... psi_5                    (1 value)
  * A: device, prod dim doubles. psi[e]: device, dim[e] complex doubles (interleaved re, im), read
  * for e >= 5 - n_vec (others may be NULL). out: device complex doubles. dim: host, each 1..1024.
- * FP64; every sum in a fixed order. Synchronises the stream. Errors: SF_ERR_ARG, SF_ERR_LIMIT
- * (D3 D4 above 12,800), SF_ERR_CUDA, SF_ERR_OOM. */
+ * FP64; every sum in a fixed order. Stream-ordered: the call enqueues its kernels (and a small
+ * stream-ordered scratch allocation) on `stream` and returns; errors during execution surface at
+ * the caller's next synchronisation. Errors: SF_ERR_ARG, SF_ERR_LIMIT (D3 D4 above 12,800),
+ * SF_ERR_CUDA, SF_ERR_OOM. */
 int sf_contract_vectors(const double* A, const int32_t dim[5], int32_t n_vec, const double* const psi[5],
                         double* out, cudaStream_t stream);
 
 /* Complete contraction of two vertex tensors of n entries: *out = sum_i A[i] B[i] (FP64, fixed
- * order). A, B: device, 16-byte aligned; out: device, one double. Synchronises the stream. */
+ * order). A, B: device, 16-byte aligned; out: device, one double. Stream-ordered, as
+ * sf_contract_vectors. */
 int sf_contract_vertices(const double* A, const double* B, int64_t n, double* out, cudaStream_t stream);
 
 /* The Delta_3 spin foam (three vertices joined pairwise by internal edges and sharing one

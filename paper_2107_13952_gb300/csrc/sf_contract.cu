@@ -154,9 +154,7 @@ extern "C" int sf_contract_vectors(const double* A, const int32_t dim[5], int32_
         if (e != cudaSuccess) rc = sf_set_error(SF_ERR_CUDA, "contraction launch: %s", cudaGetErrorString(e));
     }
     if (tmp) cudaFreeAsync(tmp, stream);
-    if (rc != SF_OK) return rc;
-    SF_CUDA_TRY(cudaStreamSynchronize(stream));
-    return SF_OK;
+    return rc;
 }
 
 // sum_i A[i] B[i]: CTA b takes the contiguous chunk [b n / G, (b+1) n / G) with 16-byte loads
@@ -226,7 +224,6 @@ extern "C" int sf_contract_vertices(const double* A, const double* B, int64_t n,
     }
     cudaFreeAsync(part, stream);
     if (e != cudaSuccess) return sf_set_error(SF_ERR_CUDA, "contraction launch: %s", cudaGetErrorString(e));
-    SF_CUDA_TRY(cudaStreamSynchronize(stream));
     return SF_OK;
 }
 
@@ -323,6 +320,7 @@ extern "C" int sf_delta3_amplitudes(int32_t n_x, const double* const* A, const i
     cudaFreeAsync(T, stream);
     if (d_meta) cudaFreeAsync(d_meta, stream);
     if (rc != SF_OK) return rc;
+    // the metadata was copied from this call's host vector: wait for the copy before it goes away
     SF_CUDA_TRY(cudaStreamSynchronize(stream));
     return SF_OK;
 }
