@@ -3,9 +3,10 @@
 Workload (the homogeneous scaling sweep): sixteen vertices with all ten boundary spins
 j = lambda/2, lambda = 1..16, gamma = 1.2, dl = 10 (11^6 = 1,771,561 shells each), rapidity rule
 r_max = 40, 40 panels x 50 Gauss-Legendre nodes. One step runs the whole path through the C ABI:
-{6j} tables, d-tables and boosters of all sixteen vertices, then the shell sum over one slice of
-every vertex (the same 1/S range of its group-major shell index), so S consecutive steps cover the
-sweep exactly once. Shells are counted when they are non-empty (all four virtual-intertwiner
+the shell sum over one slice of every vertex (the same 1/S range of its group-major shell index)
+together with the {6j} tables, d-tables and boosters that the slice's shells read (built for the
+slice, as one process of a split sum builds its own), so S consecutive steps cover the sweep
+exactly once. Shells are counted when they are non-empty (all four virtual-intertwiner
 ranges non-empty); the count over the whole grid is reported beside. Ranks of a multi-GPU run take
 different slices (weak scaling, no collective on the data path).
 
@@ -63,8 +64,9 @@ NCU_TRAFFIC = {"sha1": "39b46336c37b", "bytes_per_launch": 2244882432 + 75384064
 
 def workload_name(slices):
     return ("homogeneous sweep: 16 vertices, all spins j=lambda/2 for lambda=1..16, gamma=1.2, dl=10 (11^6 shells "
-            "each), rule r_max=40 / 40 panels x 50 nodes; one step = 6j tables + d-tables + boosters of all 16 "
-            "vertices + shell sum over a 1/%d slice of every vertex's group-major shell range" % slices)
+            "each), rule r_max=40 / 40 panels x 50 nodes; one step = shell sum over a 1/%d slice of every vertex's "
+            "group-major shell range with the 6j tables, d-tables and boosters the slice reads, built in the step"
+            % slices)
 
 
 def kernel_sha1():
@@ -405,7 +407,8 @@ def contraction_measure(hbm_peak, reps=5):
         D = 2 * J + 1
         A = torch.randn((D,) * 5, dtype=torch.float64, device="cuda", generator=g)
         B = torch.randn((D,) * 5, dtype=torch.float64, device="cuda", generator=g)
-        psis = [rng.standard_normal(D) + 1j * rng.standard_normal(D) for _ in range(5)]
+        psis = [torch.tensor(rng.standard_normal(D) + 1j * rng.standard_normal(D), dtype=torch.complex128,
+                             device="cuda") for _ in range(5)]
         row = {"J": J, "entries": D ** 5, "bytes": 8 * D ** 5}
         for label, fn, nbytes, fmas in (("vertex_vertex", lambda: sf.contract_vertices(A, B), 16 * D ** 5, D ** 5),
                                         ("vertex_5_vectors", lambda: sf.contract_vectors(A, psis), 8 * D ** 5,
@@ -562,7 +565,7 @@ def main():
 
     def step(k, prec, to_host):
         b, e, _, _ = slice_bounds(k % S)
-        t = sf.sf_6j_table(verts)
+        t = sf.sf_6j_table(verts, shell_range=(b, e))
         sf.sf_boosters(t, RULE)
         sf.sf_vertex_amplitude(t, prec, b, e, out=outs)
         kms = sf.last_kernel_ms()
@@ -652,7 +655,7 @@ def main():
     # every shell of the slice (kappa pass of the library, FP64)
     kappa = {}
     b, e, _, _ = slice_bounds(slices[-1])
-    tk = sf.sf_6j_table(verts)
+    tk = sf.sf_6j_table(verts, shell_range=(b, e))
     sf.sf_boosters(tk, RULE)
     _, ks = sf.sf_vertex_amplitude(tk, sf.SF_FP64, b, e, kappa=True)
     for (lam, dl), r, kv in zip(SWEEP, last["fp64"], ks):
@@ -721,9 +724,10 @@ def main():
         "config": {"workload": workload_name(S), "slices_per_pass": S, "precision": args.precision,
                    "counting": "non-empty shells (all four virtual-intertwiner ranges non-empty); all_shells_per_s "
                                "counts the whole (dl+1)^6 grid",
-                   "cache": "inputs larger than L2: every step rebuilds the {6j} tables, d-tables and boosters of "
-                            "all 16 vertices (the spin-8 S3 table alone, FP64 plus pair copy, is 384 MB, 3x the "
-                            "L2), so no step starts with its working set in L2; no separate flush"},
+                   "cache": "inputs larger than L2: every step rebuilds the {6j} tables, d-tables and boosters its "
+                            "slice reads (the spin-8 S3 table alone, FP64 plus pair copy, is 384 MB, 3x the L2; "
+                            "each slice reads the groups of other l35 values than the previous one), so no step "
+                            "starts with its working set in L2; no separate flush"},
         "all_shells_per_s": alls * world / (ms / 1e3),
         "roofline": roof,
         "cpu_baseline": cpu,

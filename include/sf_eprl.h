@@ -137,6 +137,18 @@ int64_t sf_num_shells(const sf_vertex* v);
  * v: host array of n vertices. *out receives a new object (free with sf_tables_free). */
 int sf_6j_table(const sf_vertex* v, int32_t n, sf_tables** out, cudaStream_t stream);
 
+/* The same tables object restricted to what the shells [shell_begin, shell_end) of every vertex
+ * read (the range as in sf_vertex_amplitude, widened to whole (l25, l35, l45) groups): the {6j}
+ * slots and, in sf_boosters, the booster triples of the other groups are left zero (S1, S5 and the
+ * edge-2 boosters are selected by l25, S2 by (l35, l45), S3 and the edge-3 boosters by l35, the
+ * edge-4 boosters by l45, the edge-5 boosters by the group; S4 is built whole). For a shell sum over
+ * part of the range, as one process of a split sum (Sec. 3 "Parallelization": each node computes
+ * its own shells) or one slice of a long sum, building only what it reads. Amplitude calls and
+ * plans on these tables must stay inside the groups (else SF_ERR_ARG); sf_vertex_adjoint needs the
+ * whole range. Errors: as sf_6j_table, SF_ERR_ARG for a negative or reversed range. */
+int sf_6j_table_range(const sf_vertex* v, int32_t n, int64_t shell_begin, int64_t shell_end, sf_tables** out,
+                      cudaStream_t stream);
+
 /* Compute the booster tensors of every vertex in t (Sec. 2 eq. booster, Sec. 3): d-tables
  * d^{gamma(j+1), j}_{j l m}(r_n) on the rule's nodes, 4jm symbols, quadrature and m-sum.
  * q: host pointer to the rule. */

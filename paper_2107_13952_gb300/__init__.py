@@ -24,6 +24,7 @@ SF_TAB_6J, SF_TAB_6J_SLOTS, SF_TAB_D, SF_TAB_NODES = 1, 2, 3, 4
 
 # names of every symbol declared in include/sf_eprl.h
 EXPORTS = ("sf_version", "sf_last_error", "sf_intertwiner_ranges", "sf_output_ranges", "sf_num_shells", "sf_6j_table",
+           "sf_6j_table_range",
            "sf_boosters", "sf_booster_shape", "sf_boosters_upload", "sf_boosters_download",
            "sf_vertex_amplitude", "sf_vertex_adjoint", "sf_table_size", "sf_table_copy", "sf_kernel_launches",
            "sf_last_kernel_ms", "sf_vertex_amplitude_noalloc", "sf_plan_create", "sf_plan_autotune",
@@ -76,6 +77,7 @@ def _declare(lib):
         "sf_output_ranges": (ctypes.c_int, [ctypes.POINTER(sf_vertex), ctypes.POINTER(I32), ctypes.POINTER(I32)]),
         "sf_num_shells": (I64, [ctypes.POINTER(sf_vertex)]),
         "sf_6j_table": (ctypes.c_int, [ctypes.POINTER(sf_vertex), I32, ctypes.POINTER(P), P]),
+        "sf_6j_table_range": (ctypes.c_int, [ctypes.POINTER(sf_vertex), I32, I64, I64, ctypes.POINTER(P), P]),
         "sf_boosters": (ctypes.c_int, [P, ctypes.POINTER(sf_quad_rule), P]),
         "sf_booster_shape": (ctypes.c_int, [P, I32, I32, ctypes.POINTER(I64)]),
         "sf_boosters_upload": (ctypes.c_int, [P, I32, I32, P, P]),
@@ -180,12 +182,18 @@ class Tables:
         return output_ranges(self.vertices[vtx])
 
 
-def sf_6j_table(vertices, stream=None):
+def sf_6j_table(vertices, stream=None, shell_range=None):
+    """Tables of the vertices; with ``shell_range`` = (begin, end) only what those shells of every
+    vertex read is built (``sf_6j_table_range``)."""
     lib = load()
     vs = list(vertices)
     arr = (sf_vertex * len(vs))(*vs)
     out = ctypes.c_void_p()
-    _check(lib.sf_6j_table(arr, len(vs), ctypes.byref(out), _stream(stream)))
+    if shell_range is None:
+        _check(lib.sf_6j_table(arr, len(vs), ctypes.byref(out), _stream(stream)))
+    else:
+        _check(lib.sf_6j_table_range(arr, len(vs), int(shell_range[0]), int(shell_range[1]), ctypes.byref(out),
+                                     _stream(stream)))
     return Tables(out, vs)
 
 

@@ -1,6 +1,7 @@
 // C ABI of the EPRL vertex library (include/sf_eprl.h): argument checks, table planning,
 // device memory ownership and the launch sequence of the kernels.
 #include "sf_internal.cuh"
+#include <climits>
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -60,6 +61,10 @@ struct VertexHost {
     int32_t nl[10];
     int64_t ngroups = 0;
     int mk3u = 1;            // largest union over l23 of the k3 ranges, over (l34, l35)
+    int64_t g_lo = 0, g_hi = 0;                 // (l25, l35, l45) groups the tables cover
+    bool restricted = false;                    // g_lo > 0 or g_hi < ngroups
+    unsigned char* d_need6[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // slots built
+    unsigned char* d_needB[4] = {nullptr, nullptr, nullptr, nullptr};            // triples computed
 };
 
 struct sf_tables {
@@ -324,7 +329,73 @@ extern "C" void sf_tables_free(sf_tables* t) {
     delete t;
 }
 
-extern "C" int sf_6j_table(const sf_vertex* v, int32_t n, sf_tables** out, cudaStream_t stream) {
+// The slots and booster triples that the shells of groups [g_lo, g_hi) read: S1, S5 and the edge-2
+// boosters by d25, S2 by (d35, d45), S3 and the edge-3 boosters by d35, the edge-4 boosters by
+// d45, the edge-5 boosters by the group itself; S4 is read by every group.
+static int build_needs(sf_tables* t, VertexHost& h) {
+    const int D = h.D;
+    std::vector<char> n25(D, 0), n35(D, 0), n45(D, 0), n3545((size_t)D * D, 0);
+    for (int64_t g = h.g_lo; g < h.g_hi; g++) {
+        const int d25 = (int)(g / ((int64_t)D * D)), d35 = (int)((g / D) % D), d45 = (int)(g % D);
+        n25[d25] = n35[d35] = n45[d45] = 1;
+        n3545[(size_t)d35 * D + d45] = 1;
+    }
+    std::vector<unsigned char> m;
+    auto put = [&](unsigned char** dst) -> int {
+        SF_TRY(dev_alloc(t, (void**)dst, m.size()));
+        SF_CUDA_TRY(cudaMemcpy(*dst, m.data(), m.size(), cudaMemcpyHostToDevice));
+        return SF_OK;
+    };
+    m.assign(D, 0);
+    for (int d = 0; d < D; d++) m[d] = n25[d];
+    SF_TRY(put(&h.d_need6[0]));
+    SF_TRY(put(&h.d_need6[4]));
+    m.assign((size_t)D * D, 0);
+    for (size_t q = 0; q < m.size(); q++) m[q] = n3545[q];
+    SF_TRY(put(&h.d_need6[1]));
+    m.assign((size_t)D * D * D, 0);
+    for (size_t q = 0; q < m.size(); q++) m[q] = n35[q % D];            // slot (d24 D + d34) D + d35
+    SF_TRY(put(&h.d_need6[2]));
+    // boosters: t = (a D + b) D + c over the edge's three offsets
+    for (size_t q = 0; q < m.size(); q++) m[q] = n25[q % D];            // edge 2 (d23, d24, d25)
+    SF_TRY(put(&h.d_needB[0]));
+    for (size_t q = 0; q < m.size(); q++) m[q] = n35[(q / D) % D];      // edge 3 (d34, d35, d23)
+    SF_TRY(put(&h.d_needB[1]));
+    for (size_t q = 0; q < m.size(); q++) m[q] = n45[q / ((size_t)D * D)];   // edge 4 (d45, d24, d34)
+    SF_TRY(put(&h.d_needB[2]));
+    for (size_t q = 0; q < m.size(); q++) m[q] = ((int64_t)q >= h.g_lo && (int64_t)q < h.g_hi) ? 1 : 0;   // edge 5 = g
+    SF_TRY(put(&h.d_needB[3]));
+    return SF_OK;
+}
+
+// the shells a call asks for lie in the groups its tables cover
+static int check_covered(const sf_tables* t, int64_t shell_begin, int64_t shell_end, const int64_t* shell_list,
+                         int64_t n_list) {
+    for (size_t i = 0; i < t->vs.size(); i++) {
+        const VertexHost& h = t->vs[i];
+        if (!h.restricted) continue;
+        const int64_t per = (int64_t)h.D * h.D * h.D;
+        if (shell_list) {
+            std::vector<int64_t> l((size_t)std::max<int64_t>(n_list, 0));
+            if (n_list > 0) SF_CUDA_TRY(cudaMemcpy(l.data(), shell_list, (size_t)n_list * sizeof(int64_t), cudaMemcpyDefault));
+            for (int64_t s : l)
+                if (s >= 0 && s < h.nshell && (s / per < h.g_lo || s / per >= h.g_hi))
+                    return sf_set_error(SF_ERR_ARG, "shell %lld lies outside the groups the tables were built for",
+                                        (long long)s);
+            continue;
+        }
+        const int64_t b = std::min<int64_t>(std::max<int64_t>(shell_begin, 0), h.nshell);
+        const int64_t e = std::min<int64_t>(std::max<int64_t>(shell_end, 0), h.nshell);
+        if (e > b && (b < h.g_lo * per || e > h.g_hi * per))
+            return sf_set_error(SF_ERR_ARG, "vertex %zu: shells [%lld, %lld) reach beyond the groups [%lld, %lld) its "
+                                            "tables were built for", i, (long long)b, (long long)e, (long long)h.g_lo,
+                                (long long)h.g_hi);
+    }
+    return SF_OK;
+}
+
+static int build_tables(const sf_vertex* v, int32_t n, int64_t range_begin, int64_t range_end, sf_tables** out,
+                        cudaStream_t stream) {
     if (!out) return sf_set_error(SF_ERR_ARG, "null output pointer");
     *out = nullptr;
     if (!v || n <= 0) return sf_set_error(SF_ERR_ARG, "need at least one vertex");
@@ -358,6 +429,14 @@ extern "C" int sf_6j_table(const sf_vertex* v, int32_t n, sf_tables** out, cudaS
             sub_range_of(&v[i], h.di, h.olo, h.od);   // validated above
             h.nshell = (int64_t)h.D * h.D * h.D * h.D * h.D * h.D;
             h.ngroups = (int64_t)h.D * h.D * h.D;
+            {
+                const int64_t per = h.ngroups;   // shells per group
+                const int64_t b = std::min<int64_t>(std::max<int64_t>(range_begin, 0), h.nshell);
+                const int64_t e = std::min<int64_t>(std::max<int64_t>(range_end, 0), h.nshell);
+                h.g_lo = b / per;
+                h.g_hi = e > b ? (e + per - 1) / per : h.g_lo;
+                h.restricted = h.g_lo > 0 || h.g_hi < h.ngroups;
+            }
             plan_6j(h);
             plan_boosters(h);
             for (int k = 0; k < 5 && rc == SF_OK; k++) {
@@ -389,6 +468,9 @@ extern "C" int sf_6j_table(const sf_vertex* v, int32_t n, sf_tables** out, cudaS
         if ((rc = dev_alloc(t, (void**)&t->d_status, sizeof(int))) != SF_OK) break;
         if (cudaMemsetAsync(t->d_status, 0, sizeof(int), stream) != cudaSuccess) { rc = sf_set_error(SF_ERR_CUDA, "memset"); break; }
         if ((rc = upload_vtxdev(t)) != SF_OK) break;
+        for (size_t i = 0; i < t->vs.size() && rc == SF_OK; i++)
+            if (t->vs[i].restricted) rc = build_needs(t, t->vs[i]);
+        if (rc != SF_OK) break;
         if ((rc = sf_fact_table_build(t->d_fact, stream)) != SF_OK) break;
         // triangle coefficients for every doubled spin that an argument of the tables reaches
         int tri_m = 0;
@@ -406,7 +488,7 @@ extern "C" int sf_6j_table(const sf_vertex* v, int32_t n, sf_tables** out, cudaS
             VertexHost& h = t->vs[i];
             for (int k = 0; k < 5 && rc == SF_OK; k++)
                 rc = sf_sixj_table_build(k + 1, t->d_vtx + i, h.S[k].d_slots, (int)h.S[k].slots.size(), h.S[k].n,
-                                         h.S[k].d_vals, d_tri, tri_m, t->d_status, t->num_sms, stream);
+                                         h.S[k].d_vals, d_tri, tri_m, h.d_need6[k], t->d_status, t->num_sms, stream);
             if (rc == SF_OK) rc = sf_to_float(h.S[3].d_vals, h.d_S4f, h.S[3].n, t->num_sms, stream);
             if (rc == SF_OK) rc = sf_scale_x(h.S[0].d_vals, h.S[0].d_slots, (int)h.S[0].slots.size(), h.d_S1x, stream);
             if (rc == SF_OK) rc = sf_to_float(h.S[4].d_vals, h.d_S5f, h.S[4].n, t->num_sms, stream);
@@ -418,6 +500,16 @@ extern "C" int sf_6j_table(const sf_vertex* v, int32_t n, sf_tables** out, cudaS
     if (rc != SF_OK) { sf_tables_free(t); return rc; }
     *out = t;
     return SF_OK;
+}
+
+extern "C" int sf_6j_table(const sf_vertex* v, int32_t n, sf_tables** out, cudaStream_t stream) {
+    return build_tables(v, n, 0, INT64_MAX, out, stream);
+}
+
+extern "C" int sf_6j_table_range(const sf_vertex* v, int32_t n, int64_t shell_begin, int64_t shell_end, sf_tables** out,
+                                 cudaStream_t stream) {
+    if (shell_begin < 0 || shell_end < shell_begin) return sf_set_error(SF_ERR_ARG, "bad shell range");
+    return build_tables(v, n, shell_begin, shell_end, out, stream);
 }
 
 extern "C" int sf_boosters(sf_tables* t, const sf_quad_rule* q, cudaStream_t stream) {
@@ -473,7 +565,7 @@ extern "C" int sf_boosters(sf_tables* t, const sf_quad_rule* q, cudaStream_t str
             size_t smem = sf_booster_smem(j[faces[e][0]], j[faces[e][1]], j[faces[e][2]], j[faces[e][3]], h.dkmax[e]);
             const int nc = sf_booster_chunk(j[faces[e][0]], j[faces[e][1]], j[faces[e][2]], j[faces[e][3]]);
             SF_TRY(sf_booster_build(t->d_vtx + i, e + 2, (int)h.ntrip, smem, nc, t->d_W, nnodes, t->d_fact, t->d_Aj, t->d_Cj,
-                                    h.d_B[e], t->d_status, stream));
+                                    h.d_B[e], h.d_needB[e], t->d_status, stream));
             SF_TRY(sf_to_float(h.d_B[e], h.d_Bf[e], (int64_t)h.ntrip * h.di[e + 1] * h.dkmax[e], t->num_sms, stream));
         }
         h.boosters_ready = true;
@@ -843,6 +935,7 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
         if (!t->vs[i].boosters_ready) return sf_set_error(SF_ERR_ARG, "boosters of vertex %zu were never computed or uploaded", i);
         if (!A_out[i]) return sf_set_error(SF_ERR_ARG, "null output for vertex %zu", i);
     }
+    SF_TRY(check_covered(t, shell_begin, shell_end, shell_list, n_list));
     const int mix = (int)precision;
     ShellConfig cfg;
     SF_TRY(shell_config(t, mix, sf_tiling{}, &cfg));
@@ -1009,6 +1102,7 @@ extern "C" int sf_plan_create(sf_tables* t, sf_precision precision, int64_t shel
         if (!t->vs[i].boosters_ready) return sf_set_error(SF_ERR_ARG, "boosters of vertex %zu were never computed or uploaded", i);
         if (!A_out[i]) return sf_set_error(SF_ERR_ARG, "null output for vertex %zu", i);
     }
+    SF_TRY(check_covered(t, shell_begin, shell_end, nullptr, 0));
     sf_plan* p = new sf_plan();
     p->t = t;
     p->mix = (int)precision;
@@ -1144,6 +1238,7 @@ extern "C" int sf_vertex_adjoint(sf_tables* t, sf_precision precision, const dou
     if (grad_B)
         for (int e = 0; e < 4; e++) if (!grad_B[e]) return sf_set_error(SF_ERR_ARG, "null grad_B[%d]", e);
     const VertexHost& hv = t->vs[0];
+    if (hv.restricted) return sf_set_error(SF_ERR_ARG, "the adjoint sums every shell: it needs tables of the whole range");
     for (int e = 0; e < 5; e++)
         if (hv.olo[e] != 0 || hv.od[e] != hv.di[e])
             return sf_set_error(SF_ERR_ARG, "the adjoint needs the whole intertwiner range (edge %d has a sub-range)", e + 1);
@@ -1273,6 +1368,7 @@ extern "C" int sf_vertex_amplitude_noalloc(sf_tables* t, int64_t shell_begin, in
         if (!t->vs[i].boosters_ready) return sf_set_error(SF_ERR_ARG, "boosters of vertex %zu were never computed or uploaded", i);
         if (!A_out[i]) return sf_set_error(SF_ERR_ARG, "null output for vertex %zu", i);
     }
+    SF_TRY(check_covered(t, shell_begin, shell_end, nullptr, 0));
     const int nv = (int)t->vs.size();
     // one work item per (vertex, i1, i2) tile covering the requested groups: the smallest scratch
     std::vector<WorkItem> items;

@@ -356,7 +356,8 @@ __global__ void k_boundary_3j(const VtxDev* __restrict__ vp, int edge, const dd*
 #define SF_BOOST_NT 512
 __global__ void __launch_bounds__(SF_BOOST_NT) k_booster(const VtxDev* __restrict__ vp, int edge, const double* __restrict__ Wm,
                                                  int nnodes, int NC, const dd* __restrict__ F, const double* __restrict__ gAj,
-                                                 const double* __restrict__ gCj, double* __restrict__ Bout, int* status) {
+                                                 const double* __restrict__ gCj, double* __restrict__ Bout,
+                                                 const unsigned char* __restrict__ need, int* status) {
     extern __shared__ __align__(16) double sm[];
     const VtxDev& v = *vp;
     const int e = edge - 2;
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(SF_BOOST_NT) k_booster(const VtxDev* __restric
     int klo, nk;
     sf_pair_range(tl[0], tl[1], tl[2], tl[3], &klo, &nk);
     for (int q = threadIdx.x; q < di * dkmax; q += blockDim.x) Bt[q] = 0.0;
-    if (nk == 0) return;
+    if (nk == 0 || (need && !need[t])) return;   // an empty range, or a triple no selected shell uses
     const int n1 = tj[0] + 1, n2 = tj[1] + 1, n3 = tj[2] + 1, n4 = tj[3] + 1;
     const int M = n1 * n2 * n3;
     const int Mh = M / 2;   // canonical tuples: [Mh, M); Mh itself is m = 0 when M is odd
@@ -507,13 +508,14 @@ size_t sf_booster_smem(int tj1, int tj2, int tj3, int tj4, int nk) {
 }
 
 int sf_booster_build(const VtxDev* d_v, int edge, int ntrip, size_t smem, int nc, const double* d_W, int nnodes,
-                     const dd* F, double* d_Aj, double* d_Cj, double* d_B, int* d_status, cudaStream_t s) {
+                     const dd* F, double* d_Aj, double* d_Cj, double* d_B, const unsigned char* d_need, int* d_status,
+                     cudaStream_t s) {
     if (smem > 227 * 1024) return sf_set_error(SF_ERR_LIMIT, "booster kernel needs %zu bytes of shared memory", smem);
     k_boundary_3j<<<64, 256, 0, s>>>(d_v, edge, F, d_Aj, d_Cj, d_status);
     sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     SF_CUDA_TRY(cudaFuncSetAttribute(k_booster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_booster<<<ntrip, SF_BOOST_NT, smem, s>>>(d_v, edge, d_W, nnodes, nc, F, d_Aj, d_Cj, d_B, d_status);
+    k_booster<<<ntrip, SF_BOOST_NT, smem, s>>>(d_v, edge, d_W, nnodes, nc, F, d_Aj, d_Cj, d_B, d_need, d_status);
     sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;

@@ -267,8 +267,10 @@ struct ReduceJob {             // one output tile's i3 range: items item0 + c * 
 int sf_fact_table_build(dd* F, cudaStream_t s);
 // triangle coefficients of every triad with doubled spins up to m: (m+1)^3 double-doubles
 int sf_tri_table_build(int m, const dd* F, dd* d_out, int num_sms, cudaStream_t s);
+// d_need (optional): per slot, nonzero if it is built (the others are zero-filled)
 int sf_sixj_table_build(int table_id, const VtxDev* d_v, const SlotDesc* d_slots, int nslots, int64_t n,
-                        double* d_out, const dd* d_tri, int tri_m, int* d_status, int num_sms, cudaStream_t s);
+                        double* d_out, const dd* d_tri, int tri_m, const unsigned char* d_need, int* d_status,
+                        int num_sms, cudaStream_t s);
 int sf_to_float(const double* d_in, float* d_out, int64_t n, int num_sms, cudaStream_t s);
 // (2x+1) S[entry] per slot entry (x = the entry's third argument, doubled)
 int sf_scale_x(const double* d_in, const SlotDesc* d_slots, int nslots, double* d_out, cudaStream_t s);
@@ -289,8 +291,10 @@ int sf_dtable_build(const int tk[10], double gamma, const int nl[10], int nnodes
 // node chunk of the booster kernel for the edge's four boundary spins, and its shared memory
 int sf_booster_chunk(int tj1, int tj2, int tj3, int tj4);
 size_t sf_booster_smem(int tj1, int tj2, int tj3, int tj4, int nk);
+// d_need (optional): per virtual-spin triple, nonzero if its booster is computed (the others are zero)
 int sf_booster_build(const VtxDev* d_v, int edge, int ntrip, size_t smem, int nc, const double* d_W, int nnodes,
-                     const dd* F, double* d_Aj, double* d_Cj, double* d_B, int* d_status, cudaStream_t s);
+                     const dd* F, double* d_Aj, double* d_Cj, double* d_B, const unsigned char* d_need, int* d_status,
+                     cudaStream_t s);
 // Shell-kernel modes: the sf_precision values (0 FP64, 1 mixed, 2 mixed with compensated FP32
 // pairs for the {6j} contractions).
 // shared memory (in doubles) of the shell kernel; mni3 = largest i3 extent of a work item

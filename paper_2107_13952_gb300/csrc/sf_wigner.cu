@@ -37,11 +37,13 @@ int sf_tri_table_build(int m, const dd* F, dd* d_out, int num_sms, cudaStream_t 
 
 // one thread per table entry (grid-stride); the slot of an entry is found by binary search. The
 // six arguments are selected per table and the symbol is evaluated at one call site (one copy of
-// the exact-arithmetic code in the instruction cache).
+// the exact-arithmetic code in the instruction cache). need (optional): per slot, nonzero if the
+// slot is built; entries of the other slots are set to zero.
 __global__ void __launch_bounds__(256) k_sixj_table(int table_id, const VtxDev* __restrict__ vp,
                                                     const SlotDesc* __restrict__ slots, int nslots,
                                                     int64_t n, double* __restrict__ out,
-                                                    const TriTable tt, int* status) {
+                                                    const TriTable tt, const unsigned char* __restrict__ need,
+                                                    int* status) {
     const VtxDev& v = *vp;
     const int D = v.D;
     const int j12 = v.tj[F12], j13 = v.tj[F13], j14 = v.tj[F14], j15 = v.tj[F15];
@@ -51,6 +53,10 @@ __global__ void __launch_bounds__(256) k_sixj_table(int table_id, const VtxDev* 
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
             if (slots[mid].off <= e) lo = mid; else hi = mid - 1;
+        }
+        if (need && !need[lo]) {
+            out[e] = 0.0;
+            continue;
         }
         const SlotDesc s = slots[lo];
         int64_t r = e - s.off;
@@ -96,7 +102,8 @@ int sf_fact_table_build(dd* F, cudaStream_t s) {
 }
 
 int sf_sixj_table_build(int table_id, const VtxDev* d_v, const SlotDesc* d_slots, int nslots, int64_t n,
-                        double* d_out, const dd* d_tri, int tri_m, int* d_status, int num_sms, cudaStream_t s) {
+                        double* d_out, const dd* d_tri, int tri_m, const unsigned char* d_need, int* d_status,
+                        int num_sms, cudaStream_t s) {
     if (n <= 0) return SF_OK;
     int64_t blocks = (n + 255) / 256;
     int64_t cap = (int64_t)num_sms * 16;
@@ -104,7 +111,7 @@ int sf_sixj_table_build(int table_id, const VtxDev* d_v, const SlotDesc* d_slots
     TriTable tt;
     tt.d = d_tri;
     tt.m1 = tri_m + 1;
-    k_sixj_table<<<(unsigned)blocks, 256, 0, s>>>(table_id, d_v, d_slots, nslots, n, d_out, tt, d_status);
+    k_sixj_table<<<(unsigned)blocks, 256, 0, s>>>(table_id, d_v, d_slots, nslots, n, d_out, tt, d_need, d_status);
     sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;
