@@ -217,12 +217,13 @@ int sf_vertex_amplitude_noalloc(sf_tables* t, int64_t shell_begin, int64_t shell
  *   x_chunk = auxiliary spins x per staged chunk of the {6j} contractions (1..16; the shared-memory
  *     footprint grows with it; default the largest that fits);
  *   items_per_sm = target number of work items per SM (granularity of the cost-balanced split of
- *     tiles x groups; default 8);
+ *     tiles x groups; default 16 with 512 threads, 8 with 256);
  *   threads = CTA size, 512 (one CTA per SM) or 256 (two CTAs per SM whose phases interleave);
  *   i3_split = 1 or 2 pieces of i3 per output tile (2 halves the per-CTA buffers and register
- *     tile so that two CTAs fit per SM, and stages the i3-independent operands twice; 256
- *     threads only). Default: 256 threads on whole tiles when they fit with an x chunk of at
- *     least 4, else (mixed path) 256 threads on half tiles, else 512 threads. */
+ *     tile, so that two CTAs of 256 threads fit per SM or one CTA of 512 threads gets larger x
+ *     chunks, and stages the i3-independent operands twice). Default: 256 threads on whole tiles
+ *     when they fit with an x chunk of at least 4, else 512 threads on whole tiles; half tiles
+ *     only on request. */
 typedef struct sf_tiling {
     int32_t x_chunk;
     int32_t items_per_sm;
@@ -241,7 +242,7 @@ typedef struct sf_plan sf_plan;
 int sf_plan_create(sf_tables* t, sf_precision precision, int64_t shell_begin, int64_t shell_end,
                    const sf_tiling* tiling, double* const* A_out, sf_plan** out);
 
-/* Time candidate tilings ((threads, i3_split) in (512, 1), (256, 1), (256, 2) x x_chunk 16, 8, 4
+/* Time candidate tilings ((threads, i3_split) in (512, 1), (256, 1), (256, 2), (512, 2) x x_chunk 16, 8, 4
  * (clamped to what fits) x items_per_sm 4, 8, 16) on the first sample_shells shells of the plan's
  * range of every vertex (best of two runs after a warm-up, CUDA events on stream) and rebuild the
  * plan with the fastest; *chosen (optional) receives it. Overwrites the plan's outputs;
