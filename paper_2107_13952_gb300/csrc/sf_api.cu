@@ -512,6 +512,8 @@ extern "C" int sf_6j_table_range(const sf_vertex* v, int32_t n, int64_t shell_be
     return build_tables(v, n, shell_begin, shell_end, out, stream);
 }
 
+static int boosters_all(sf_tables* t, int nnodes, double2* const d_P[2], double* const d_T[2], cudaStream_t stream);
+
 extern "C" int sf_boosters(sf_tables* t, const sf_quad_rule* q, cudaStream_t stream) {
     if (!t || !q) return sf_set_error(SF_ERR_ARG, "null argument");
     if (q->n_panels < 1 || q->order < 2 || q->order > 1024 || !(q->r_max > 0.0) || q->r_max > 700.0)
@@ -548,10 +550,46 @@ extern "C" int sf_boosters(sf_tables* t, const sf_quad_rule* q, cudaStream_t str
                     return sf_set_error(SF_ERR_LIMIT, "booster kernel supports boundary spins up to 8");
         }
     }
+    static const int bfaces[4][4] = {{F23, F24, F25, F12}, {F34, F35, F13, F23}, {F45, F14, F24, F34}, {F15, F25, F35, F45}};
+    static const int bslot[4][4] = {{0, 1, 2, -1}, {0, 1, -1, 2}, {0, -1, 1, 2}, {-1, 0, 1, 2}};
+    // per-pair tables of the booster kernel (largest edge), stream-ordered scratch freed on return
+    size_t pbytes_max[2] = {16, 16}, tbytes_max[2] = {16, 16};
+    for (auto& h : t->vs)
+        for (int e = 0; e < 4; e++) {
+            int tj4[4];
+            for (int a = 0; a < 4; a++) tj4[a] = h.v.two_j[bfaces[e][a]];
+            PairDims pd;
+            size_t pb[2], tb[2];
+            sf_pair_dims(tj4, bslot[e], h.D, nnodes, &pd, pb, tb);
+            for (int s = 0; s < 2; s++) {
+                pbytes_max[s] = std::max(pbytes_max[s], pb[s]);
+                tbytes_max[s] = std::max(tbytes_max[s], tb[s]);
+            }
+        }
     SF_TRY(dev_alloc(t, (void**)&t->d_Aj, aj * sizeof(double)));
     SF_TRY(dev_alloc(t, (void**)&t->d_Cj, aj * sizeof(double)));
     SF_TRY(upload_vtxdev(t));
     SF_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, sizeof(int), stream));
+    void* scratch = nullptr;
+    const size_t sbytes = pbytes_max[0] + pbytes_max[1] + tbytes_max[0] + tbytes_max[1];
+    {
+        cudaError_t ce = cudaMallocAsync(&scratch, sbytes, stream);
+        if (ce != cudaSuccess)
+            return sf_set_error(SF_ERR_OOM, "cudaMallocAsync(%zu) of the booster pair tables failed: %s", sbytes,
+                                cudaGetErrorString(ce));
+    }
+    double2* d_P[2] = {(double2*)scratch, (double2*)((char*)scratch + pbytes_max[0])};
+    double* d_T[2] = {(double*)((char*)scratch + pbytes_max[0] + pbytes_max[1]),
+                      (double*)((char*)scratch + pbytes_max[0] + pbytes_max[1] + tbytes_max[0])};
+    int rc = boosters_all(t, nnodes, d_P, d_T, stream);
+    cudaError_t fe = cudaFreeAsync(scratch, stream);
+    if (rc != SF_OK) return rc;
+    SF_CUDA_TRY(fe);
+    return check_status(t, stream, "sf_boosters");
+}
+
+static int boosters_all(sf_tables* t, int nnodes, double2* const d_P[2], double* const d_T[2], cudaStream_t stream) {
+    static const int bslot[4][4] = {{0, 1, 2, -1}, {0, 1, -1, 2}, {0, -1, 1, 2}, {-1, 0, 1, 2}};
     for (size_t i = 0; i < t->vs.size(); i++) {
         VertexHost& h = t->vs[i];
         {
@@ -564,13 +602,22 @@ extern "C" int sf_boosters(sf_tables* t, const sf_quad_rule* q, cudaStream_t str
             const int32_t* j = h.v.two_j;
             size_t smem = sf_booster_smem(j[faces[e][0]], j[faces[e][1]], j[faces[e][2]], j[faces[e][3]], h.dkmax[e]);
             const int nc = sf_booster_chunk(j[faces[e][0]], j[faces[e][1]], j[faces[e][2]], j[faces[e][3]]);
+            int tj4[4];
+            for (int a = 0; a < 4; a++) tj4[a] = j[faces[e][a]];
+            PairDims pd;
+            size_t pb[2], tb[2];
+            sf_pair_dims(tj4, bslot[e], h.D, nnodes, &pd, pb, tb);
+            SF_TRY(sf_pair_build(t->d_vtx + i, e + 2, pd, t->d_W, nnodes, t->d_fact, tj4, d_P, d_T, t->d_status, t->num_sms,
+                                 stream));
+            const double2* cP[2] = {d_P[0], d_P[1]};
+            const double* cT[2] = {d_T[0], d_T[1]};
             SF_TRY(sf_booster_build(t->d_vtx + i, e + 2, (int)h.ntrip, smem, nc, t->d_W, nnodes, t->d_fact, t->d_Aj, t->d_Cj,
-                                    h.d_B[e], h.d_needB[e], t->d_status, stream));
+                                    h.d_B[e], h.d_needB[e], cP, cT, pd, t->d_status, stream));
             SF_TRY(sf_to_float(h.d_B[e], h.d_Bf[e], (int64_t)h.ntrip * h.di[e + 1] * h.dkmax[e], t->num_sms, stream));
         }
         h.boosters_ready = true;
     }
-    return check_status(t, stream, "sf_boosters");
+    return SF_OK;
 }
 
 static int check_edge(const sf_tables* t, int32_t vertex, int32_t edge) {

@@ -352,12 +352,108 @@ __global__ void k_boundary_3j(const VtxDev* __restrict__ vp, int edge, const dd*
 // gives P12(-m1, -m2) = s12 conj(P12(m1, m2)) with s12 = (-1)^((k1 - l1) + (k2 - l2)) (likewise
 // P34), so only the upper half of each pair table is staged; a tuple whose pair lies in the
 // lower half reads its mirror, and Re(conj(a) b) = a.x b.x + a.y b.y flips one sign.
+// Pair tables of one side (s = 0: strands 1, 2; s = 1: strands 3, 4) of an edge, for every pair of
+// virtual spins (pid = il_a * nb + il_b, il the strands' offsets, 0 on a gauge face): the upper
+// halves (flat pair index f >= N/2) of P12 = W d1 d2 and P34 = d3 d4 on every node, the products
+// the booster kernel sums; and the virtual-side 3j symbols of that pair of spins for every k from
+// |l_a - l_b| to l_a + l_b (zero where the triangle fails). Every triple of virtual spins sharing
+// the pair reads them instead of forming them again.
+__global__ void k_pair_tables(const VtxDev* __restrict__ vp, int edge, int side, const double* __restrict__ Wm,
+                              int nnodes, int64_t total, double2* __restrict__ out) {
+    const VtxDev& v = *vp;
+    const int e = edge - 2;
+    const int fa = c_edge_face[e][2 * side], fb = c_edge_face[e][2 * side + 1];
+    const int nb = c_edge_slot[e][2 * side + 1] < 0 ? 1 : v.D;
+    const int ta = v.tj[fa], tb = v.tj[fb];
+    const int N = (ta + 1) * (tb + 1), h = N / 2, C = N - h;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
+        const int n = (int)(q % nnodes);
+        const int64_t r = q / nnodes;
+        const int f = h + (int)(r % C), pid = (int)(r / C);
+        const int ila = pid / nb, ilb = pid % nb;
+        const int a1 = f / (tb + 1), a2 = f % (tb + 1);
+        const double2 x = v.dtab[fa][((int64_t)ila * (ta + 1) + a1) * nnodes + n];
+        const double2 y = v.dtab[fb][((int64_t)ilb * (tb + 1) + a2) * nnodes + n];
+        double2 z;
+        if (side == 0) {
+            const double w = Wm[n];
+            z = make_double2(w * (x.x * y.x - x.y * y.y), w * (x.x * y.y + x.y * y.x));
+        } else {
+            z = make_double2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x);
+        }
+        out[q] = z;
+    }
+}
+
+__global__ void k_pair_3j(const VtxDev* __restrict__ vp, int edge, int side, int nkk, int64_t total,
+                          const dd* __restrict__ F, double* __restrict__ out, int* status) {
+    const VtxDev& v = *vp;
+    const int e = edge - 2;
+    const int fa = c_edge_face[e][2 * side], fb = c_edge_face[e][2 * side + 1];
+    const int nb = c_edge_slot[e][2 * side + 1] < 0 ? 1 : v.D;
+    const int ta = v.tj[fa], tb = v.tj[fb];
+    const int na1 = ta + 1, nb1 = tb + 1;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
+        const int r = (int)(q % (na1 * nb1));
+        const int64_t u = q / (na1 * nb1);
+        const int kk = (int)(u % nkk), pid = (int)(u / nkk);
+        const int tla = ta + 2 * (pid / nb), tlb = tb + 2 * (pid % nb);
+        const int k = iabs_(tla - tlb) + 2 * kk;
+        const int ia = r / nb1, ib = r % nb1;
+        const int tma = -ta + 2 * ia, tmb = -tb + 2 * ib;
+        double val = 0.0;
+        if (k <= tla + tlb) {
+            val = side == 0 ? dd_to_d(sf_threej_dd(tla, tlb, k, tma, tmb, -(tma + tmb), F, status))
+                            : dd_to_d(sf_threej_dd(k, tla, tlb, -(tma + tmb), tma, tmb, F, status));
+        }
+        out[q] = val;
+    }
+}
+
+int sf_pair_dims(const int tj4[4], const int slot4[4], int D, int nnodes, PairDims* pd, size_t pbytes[2], size_t tbytes[2]) {
+    for (int s = 0; s < 2; s++) {
+        const int ta = tj4[2 * s], tb = tj4[2 * s + 1];
+        const int na = slot4[2 * s] < 0 ? 1 : D, nb = slot4[2 * s + 1] < 0 ? 1 : D;
+        const int N = (ta + 1) * (tb + 1), C = N - N / 2;
+        pd->nb[s] = nb;
+        pd->npid[s] = na * nb;
+        pd->nkk[s] = imin_(ta + 2 * (na - 1), tb + 2 * (nb - 1)) + 1;   // k = |la - lb| .. la + lb
+        pbytes[s] = (size_t)pd->npid[s] * C * nnodes * sizeof(double2);
+        tbytes[s] = (size_t)pd->npid[s] * pd->nkk[s] * (ta + 1) * (tb + 1) * sizeof(double);
+    }
+    return SF_OK;
+}
+
+int sf_pair_build(const VtxDev* d_v, int edge, const PairDims& pd, const double* d_W, int nnodes, const dd* F,
+                  const int tj4[4], double2* const d_P[2], double* const d_T[2], int* d_status, int num_sms, cudaStream_t s) {
+    for (int side = 0; side < 2; side++) {
+        const int ta = tj4[2 * side], tb = tj4[2 * side + 1];
+        const int N = (ta + 1) * (tb + 1), C = N - N / 2;
+        const int64_t tp = (int64_t)pd.npid[side] * C * nnodes;
+        int64_t blocks = std::min<int64_t>((tp + 255) / 256, (int64_t)num_sms * 16);
+        k_pair_tables<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(d_v, edge, side, d_W, nnodes, tp, d_P[side]);
+        sf_note_launch(1);
+        SF_CUDA_TRY(cudaGetLastError());
+        const int64_t tt = (int64_t)pd.npid[side] * pd.nkk[side] * (ta + 1) * (tb + 1);
+        blocks = std::min<int64_t>((tt + 255) / 256, (int64_t)num_sms * 16);
+        k_pair_3j<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(d_v, edge, side, pd.nkk[side], tt, F, d_T[side],
+                                                                         d_status);
+        sf_note_launch(1);
+        SF_CUDA_TRY(cudaGetLastError());
+    }
+    return SF_OK;
+}
+
 #define SF_BT 6         // canonical tuples per thread (upper half of at most 17^3 tuples / 512 threads)
 #define SF_BOOST_NT 512
 __global__ void __launch_bounds__(SF_BOOST_NT) k_booster(const VtxDev* __restrict__ vp, int edge, const double* __restrict__ Wm,
                                                  int nnodes, int NC, const dd* __restrict__ F, const double* __restrict__ gAj,
                                                  const double* __restrict__ gCj, double* __restrict__ Bout,
-                                                 const unsigned char* __restrict__ need, int* status) {
+                                                 const unsigned char* __restrict__ need, const double2* __restrict__ gP12,
+                                                 const double2* __restrict__ gP34, const double* __restrict__ g3A,
+                                                 const double* __restrict__ g3C, PairDims pd, int* status) {
     extern __shared__ __align__(16) double sm[];
     const VtxDev& v = *vp;
     const int e = edge - 2;
@@ -394,10 +490,10 @@ __global__ void __launch_bounds__(SF_BOOST_NT) k_booster(const VtxDev* __restric
     double2* P34 = P12 + C12 * NC;
     double* sAl = sm + Mpad;
     double* sCl = sAl + nk * n1 * n2;
-    const double2* d0 = v.dtab[fc[0]] + (int64_t)il[0] * n1 * nnodes;
-    const double2* d1 = v.dtab[fc[1]] + (int64_t)il[1] * n2 * nnodes;
-    const double2* d2 = v.dtab[fc[2]] + (int64_t)il[2] * n3 * nnodes;
-    const double2* d3 = v.dtab[fc[3]] + (int64_t)il[3] * n4 * nnodes;
+    // this triple's pair tables (upper halves, [pair][node]) and virtual-side 3j tables
+    const int pid12 = il[0] * pd.nb[0] + il[1], pid34 = il[2] * pd.nb[1] + il[3];
+    const double2* q12 = gP12 + (int64_t)pid12 * C12 * nnodes;
+    const double2* q34 = gP34 + (int64_t)pid34 * C34 * nnodes;
     double acc[SF_BT];
 #pragma unroll
     for (int q = 0; q < SF_BT; q++) acc[q] = 0.0;
@@ -405,23 +501,12 @@ __global__ void __launch_bounds__(SF_BOOST_NT) k_booster(const VtxDev* __restric
         const int nc = imin_(NC, nnodes - n0);
         __syncthreads();
         for (int q = threadIdx.x; q < C12 * NC; q += blockDim.x) {
-            const int nn = q % NC, pr = h12 + q / NC, a2 = pr % n2, a1 = pr / n2;
-            double2 z = make_double2(0.0, 0.0);
-            if (nn < nc) {
-                const double2 x = d0[(int64_t)a1 * nnodes + n0 + nn], y = d1[(int64_t)a2 * nnodes + n0 + nn];
-                const double w = Wm[n0 + nn];
-                z = make_double2(w * (x.x * y.x - x.y * y.y), w * (x.x * y.y + x.y * y.x));
-            }
-            P12[q] = z;
+            const int nn = q % NC, f = q / NC;
+            P12[q] = (nn < nc) ? q12[(int64_t)f * nnodes + n0 + nn] : make_double2(0.0, 0.0);
         }
         for (int q = threadIdx.x; q < C34 * NC; q += blockDim.x) {
-            const int nn = q % NC, pr = h34 + q / NC, a4 = pr % n4, a3 = pr / n4;
-            double2 z = make_double2(0.0, 0.0);
-            if (nn < nc) {
-                const double2 x = d2[(int64_t)a3 * nnodes + n0 + nn], y = d3[(int64_t)a4 * nnodes + n0 + nn];
-                z = make_double2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x);
-            }
-            P34[q] = z;
+            const int nn = q % NC, f = q / NC;
+            P34[q] = (nn < nc) ? q34[(int64_t)f * nnodes + n0 + nn] : make_double2(0.0, 0.0);
         }
         __syncthreads();
 #pragma unroll
@@ -457,16 +542,14 @@ __global__ void __launch_bounds__(SF_BOOST_NT) k_booster(const VtxDev* __restric
         const int mt = Mh + threadIdx.x + q * blockDim.x;
         if (mt < M) sIr[mt] = ((M & 1) && mt == Mh) ? acc[q] : 2.0 * acc[q];
     }
-    // ---- virtual-side 3j tables: Al[c][m1][m2] = (l1 l2 k; m1 m2 mu), Cl[c][m3][m4] = (k l3 l4; -mu m3 m4)
-    for (int q = threadIdx.x; q < nk * n1 * n2; q += blockDim.x) {
-        int c = q / (n1 * n2), r = q % (n1 * n2), i1 = r / n2, i2 = r % n2;
-        int tm1 = -tj[0] + 2 * i1, tm2 = -tj[1] + 2 * i2;
-        sAl[q] = dd_to_d(sf_threej_dd(tl[0], tl[1], klo + 2 * c, tm1, tm2, -(tm1 + tm2), F, status));
-    }
-    for (int q = threadIdx.x; q < nk * n3 * n4; q += blockDim.x) {
-        int c = q / (n3 * n4), r = q % (n3 * n4), i3 = r / n4, i4 = r % n4;
-        int tm3 = -tj[2] + 2 * i3, tm4 = -tj[3] + 2 * i4;
-        sCl[q] = dd_to_d(sf_threej_dd(klo + 2 * c, tl[2], tl[3], -(tm3 + tm4), tm3, tm4, F, status));
+    // ---- virtual-side 3j tables: Al[c][m1][m2] = (l1 l2 k; m1 m2 mu), Cl[c][m3][m4] = (k l3 l4; -mu m3 m4),
+    // copied from the per-pair tables (k from |l1 - l2| and from |l3 - l4| in steps of one)
+    {
+        const int kk12 = (klo - iabs_(tl[0] - tl[1])) / 2, kk34 = (klo - iabs_(tl[2] - tl[3])) / 2;
+        const double* a3 = g3A + ((int64_t)pid12 * pd.nkk[0] + kk12) * n1 * n2;
+        const double* c3 = g3C + ((int64_t)pid34 * pd.nkk[1] + kk34) * n3 * n4;
+        for (int q = threadIdx.x; q < nk * n1 * n2; q += blockDim.x) sAl[q] = a3[q];
+        for (int q = threadIdx.x; q < nk * n3 * n4; q += blockDim.x) sCl[q] = c3[q];
     }
     __syncthreads();
     // ---- B[i][k] = sum_m (-1)^((i - mu) + (k - mu)) Aj Cj Al Cl Re I(m)
@@ -508,14 +591,16 @@ size_t sf_booster_smem(int tj1, int tj2, int tj3, int tj4, int nk) {
 }
 
 int sf_booster_build(const VtxDev* d_v, int edge, int ntrip, size_t smem, int nc, const double* d_W, int nnodes,
-                     const dd* F, double* d_Aj, double* d_Cj, double* d_B, const unsigned char* d_need, int* d_status,
+                     const dd* F, double* d_Aj, double* d_Cj, double* d_B, const unsigned char* d_need,
+                     const double2* const d_P[2], const double* const d_T[2], const PairDims& pd, int* d_status,
                      cudaStream_t s) {
     if (smem > 227 * 1024) return sf_set_error(SF_ERR_LIMIT, "booster kernel needs %zu bytes of shared memory", smem);
     k_boundary_3j<<<64, 256, 0, s>>>(d_v, edge, F, d_Aj, d_Cj, d_status);
     sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     SF_CUDA_TRY(cudaFuncSetAttribute(k_booster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_booster<<<ntrip, SF_BOOST_NT, smem, s>>>(d_v, edge, d_W, nnodes, nc, F, d_Aj, d_Cj, d_B, d_need, d_status);
+    k_booster<<<ntrip, SF_BOOST_NT, smem, s>>>(d_v, edge, d_W, nnodes, nc, F, d_Aj, d_Cj, d_B, d_need, d_P[0], d_P[1],
+                                               d_T[0], d_T[1], pd, d_status);
     sf_note_launch(1);
     SF_CUDA_TRY(cudaGetLastError());
     return SF_OK;

@@ -291,9 +291,17 @@ int sf_dtable_build(const int tk[10], double gamma, const int nl[10], int nnodes
 // node chunk of the booster kernel for the edge's four boundary spins, and its shared memory
 int sf_booster_chunk(int tj1, int tj2, int tj3, int tj4);
 size_t sf_booster_smem(int tj1, int tj2, int tj3, int tj4, int nk);
-// d_need (optional): per virtual-spin triple, nonzero if its booster is computed (the others are zero)
+// pair tables of a booster edge: per side, the stride of the second strand's offset, the number of
+// virtual-spin pairs and of k values of the 3j tables
+struct PairDims { int nb[2], npid[2], nkk[2]; };
+int sf_pair_dims(const int tj4[4], const int slot4[4], int D, int nnodes, PairDims* pd, size_t pbytes[2], size_t tbytes[2]);
+int sf_pair_build(const VtxDev* d_v, int edge, const PairDims& pd, const double* d_W, int nnodes, const dd* F,
+                  const int tj4[4], double2* const d_P[2], double* const d_T[2], int* d_status, int num_sms, cudaStream_t s);
+// d_need (optional): per virtual-spin triple, nonzero if its booster is computed (the others are zero);
+// d_P, d_T: the edge's pair tables (sf_pair_build)
 int sf_booster_build(const VtxDev* d_v, int edge, int ntrip, size_t smem, int nc, const double* d_W, int nnodes,
-                     const dd* F, double* d_Aj, double* d_Cj, double* d_B, const unsigned char* d_need, int* d_status,
+                     const dd* F, double* d_Aj, double* d_Cj, double* d_B, const unsigned char* d_need,
+                     const double2* const d_P[2], const double* const d_T[2], const PairDims& pd, int* d_status,
                      cudaStream_t s);
 // Shell-kernel modes: the sf_precision values (0 FP64, 1 mixed, 2 mixed with compensated FP32
 // pairs for the {6j} contractions).

@@ -253,3 +253,28 @@ def test_random_batch_boosters_match_single(lib):
             a = sf.sf_boosters_download(t, i, e)
             b = sf.sf_boosters_download(t1, 0, e)
             assert float((a - b).abs().max()) <= 1e-14 * max(float(b.abs().max()), 1e-300)
+
+
+SWEEP_SMALL_RULE = (40.0, 40, 50)
+
+
+@pytest.mark.parametrize("lam", [1, 2])
+def test_sweep_small_vertices_full_size(lib, lam):
+    """The two smallest vertices of the homogeneous sweep (all spins 1/2 and all spins 1, gamma 1.2,
+    dl 10: 11^6 shells each) in full: boosters by quadrature on the 2000-node rule and the whole
+    shell sum, every precision, against the oracle's tensors and cancellation sums written by
+    ``tests/golden/make_sweep_small.py``."""
+    g = np.load(os.path.join(GOLDEN, "sweep_small_dl10.npz"))
+    ref, kref = g["A_%d" % lam], float(g["kappa_%d" % lam])
+    t = sf.sf_6j_table([sf.vertex((lam,) * 10, 1.2, 10)])
+    sf.sf_boosters(t, SWEEP_SMALL_RULE)
+    outs, kap = sf.sf_vertex_amplitude(t, kappa=True)
+    assert abs(kap[0] - kref) <= 1e-10 * kref, (kap[0], kref)
+    amax = float(np.abs(ref).max())
+    for prec, bound in ((sf.SF_FP64, FP64_BOUND), (sf.SF_MIXED, MIXED_BOUND), (sf.SF_MIXED_FF, MIXED_BOUND),
+                        (sf.SF_MIXED_TC, MIXED_BOUND)):
+        a = outs[0] if prec == sf.SF_FP64 else sf.sf_vertex_amplitude(t, precision=prec)[0]
+        a = a.cpu().numpy()
+        assert a.shape == ref.shape
+        assert _rel(a, ref) <= bound, (prec, _rel(a, ref))
+        assert np.all(np.abs(a - ref) <= bound * np.abs(ref) + bound * amax), prec
