@@ -98,7 +98,7 @@ typedef enum {
                        keep nearly FP64 accuracy on the FP32 pipe; the sums across the (l24, l34)
                        sets of one (l25, l35, l45) group also in pairs; the k5 contraction and the
                        sums across groups in FP64                                                 */
-    SF_MIXED_TC = 3 /* the booster contractions over the virtual intertwiners in FP32-class
+    SF_MIXED_TC = 3, /* the booster contractions over the virtual intertwiners in FP32-class
                        arithmetic, the {15j} auxiliary-spin sum and the sums across shells in FP64:
                        the k4 contraction with the edge-4 booster on the tensor cores (mma.sync
                        m16n8k16, operands split into three BF16 pieces holding 24 significant
@@ -107,6 +107,14 @@ typedef enum {
                        sum with B3 and the k3 contraction with S3 in FP32 on the CUDA cores; the
                        x-sum (2x+1) S1 S2 of eq. 15j, the k5 contraction, and the sums across the
                        (l24, l34) sets and groups in FP64                                         */
+    SF_MIXED_PX = 4 /* the booster contractions over k2, k3, k4 (with S4, S5, B2, B3, B4) and the
+                       S3 contraction in FP32 on the CUDA cores; the x-sum (2x+1) S1 S2 of eq. 15j
+                       in compensated FP32 pairs as in SF_MIXED_FF: the products (2x+1) S1 S2
+                       formed as pairs from the (hi, lo) copies of S1 and S2, multiplied by the FP32
+                       result of the S3 contraction and summed over x (and across the x chunks of
+                       one (l24, l34) set) with Dot2; the k5 contraction and the sums across the
+                       (l24, l34) sets and groups in FP64. The fastest path: the FP64 pipe keeps
+                       only the k5 contraction and these sums                                     */
 } sf_precision;
 
 typedef struct sf_tables sf_tables;

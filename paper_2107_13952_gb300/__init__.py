@@ -19,7 +19,7 @@ _LIB_PATH = _build.LIB
 
 SF_OK, SF_ERR_ARG, SF_ERR_EMPTY, SF_ERR_OOM, SF_ERR_CUDA, SF_ERR_TIMEOUT, SF_ERR_NUMERIC, SF_ERR_LIMIT = \
     0, -1, -2, -3, -4, -5, -6, -7
-SF_FP64, SF_MIXED, SF_MIXED_FF, SF_MIXED_TC = 0, 1, 2, 3
+SF_FP64, SF_MIXED, SF_MIXED_FF, SF_MIXED_TC, SF_MIXED_PX = 0, 1, 2, 3, 4
 SF_TAB_6J, SF_TAB_6J_SLOTS, SF_TAB_D, SF_TAB_NODES = 1, 2, 3, 4
 
 # names of every symbol declared in include/sf_eprl.h
@@ -234,8 +234,11 @@ def sf_vertex_amplitude(tables, precision=SF_FP64, shell_begin=0, shell_end=2 **
     """Vertex tensors A[i1][i2][i3][i4][i5] (float64, cuda), one per vertex of ``tables``.
 
     precision: SF_FP64 (every step in FP64), SF_MIXED (booster contractions over k2, k3, k4 in
-    FP32) or SF_MIXED_FF (the same, with the {6j} contractions in compensated FP32 pairs); both
-    mixed paths stay within 1e-6 (normwise, relative) of the FP64 result.
+    FP32), SF_MIXED_FF (the same, with the {6j} contractions in compensated FP32 pairs),
+    SF_MIXED_TC (the booster contractions FP32-class with k4 on the tensor cores in split BF16,
+    the S3 contraction FP32, the x-sum FP64) or SF_MIXED_PX (the booster and S3 contractions in
+    FP32 on the CUDA cores, the x-sum in compensated FP32 pairs); every mixed path stays within
+    1e-6 (normwise, relative) of the FP64 result.
     With ``kappa`` True returns (tensors, sums) where sums[v] = sum_s ||C_s||_2 over the selected
     non-empty shells (one extra, unhoisted FP64 pass)."""
     import torch

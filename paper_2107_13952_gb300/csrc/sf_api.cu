@@ -973,7 +973,8 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
                                    const int64_t* shell_list, int64_t n_list, double* const* A_out, double* kappa_out,
                                    cudaStream_t stream) {
     if (!t || !A_out) return sf_set_error(SF_ERR_ARG, "null argument");
-    if (precision != SF_FP64 && precision != SF_MIXED && precision != SF_MIXED_FF && precision != SF_MIXED_TC)
+    if (precision != SF_FP64 && precision != SF_MIXED && precision != SF_MIXED_FF && precision != SF_MIXED_TC &&
+        precision != SF_MIXED_PX)
         return sf_set_error(SF_ERR_ARG, "unknown precision");
     if (shell_list && t->vs.size() != 1) return sf_set_error(SF_ERR_ARG, "a shell list needs single-vertex tables");
     if (shell_list && n_list < 0) return sf_set_error(SF_ERR_ARG, "negative list length");
@@ -1142,7 +1143,8 @@ extern "C" int sf_plan_create(sf_tables* t, sf_precision precision, int64_t shel
     if (!out) return sf_set_error(SF_ERR_ARG, "null output pointer");
     *out = nullptr;
     if (!t || !A_out) return sf_set_error(SF_ERR_ARG, "null argument");
-    if (precision != SF_FP64 && precision != SF_MIXED && precision != SF_MIXED_FF && precision != SF_MIXED_TC)
+    if (precision != SF_FP64 && precision != SF_MIXED && precision != SF_MIXED_FF && precision != SF_MIXED_TC &&
+        precision != SF_MIXED_PX)
         return sf_set_error(SF_ERR_ARG, "unknown precision");
     if (shell_begin < 0) return sf_set_error(SF_ERR_ARG, "negative shell_begin");
     for (size_t i = 0; i < t->vs.size(); i++) {

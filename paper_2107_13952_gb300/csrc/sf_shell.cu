@@ -226,13 +226,15 @@ __device__ __forceinline__ void gather_loop(int L, int tid, int nth, LoadF ld, S
 //   GEMM_FF_F: A and B pairs, Dot2 accumulation, C += the pair (pair addition);
 //   GEMM_F32:  A and B floats, FP32 FMA accumulation, C (double) += the float result.
 //   GEMM_F32_FF: as GEMM_F32, with C a pair (C += the float result, pair addition);
-//   GEMM_F32_SET: as GEMM_F32, C (double) = the float result.
-enum { GEMM_FF_D = 0, GEMM_FF_F = 1, GEMM_F32 = 2, GEMM_F32_FF = 3, GEMM_F32_SET = 4 };
+//   GEMM_F32_SET: as GEMM_F32, C (double) = the float result;
+//   GEMM_F32_SETF: as GEMM_F32, C (float) = the result;
+//   GEMM_FF_DA: as GEMM_FF_D, C += the pair (pair addition).
+enum { GEMM_FF_D = 0, GEMM_FF_F = 1, GEMM_F32 = 2, GEMM_F32_FF = 3, GEMM_F32_SET = 4, GEMM_F32_SETF = 5, GEMM_FF_DA = 6 };
 template <int KIND, int RM>
 __device__ __forceinline__ void rows_gemm(int nbatch, int M, int N, int K, const void* Av, int a_bs, int am,
                                           const void* Bv, int b_bs, int bk, void* Cv, int c_bs, int cm, int tid,
                                           int nth) {
-    constexpr bool F32 = KIND == GEMM_F32 || KIND == GEMM_F32_FF || KIND == GEMM_F32_SET;
+    constexpr bool F32 = KIND == GEMM_F32 || KIND == GEMM_F32_FF || KIND == GEMM_F32_SET || KIND == GEMM_F32_SETF;
     using TA = typename std::conditional<F32, float, float2>::type;
     using TB = typename std::conditional<KIND == GEMM_FF_F, float2, float>::type;
     const TA* A = reinterpret_cast<const TA*>(Av);
@@ -257,7 +259,7 @@ __device__ __forceinline__ void rows_gemm(int nbatch, int M, int N, int K, const
             for (int i = 0; i < RM; i++) {
                 const TA a = ap[i][k];
                 if constexpr (F32) sh[i] = fmaf(a, b, sh[i]);
-                else if constexpr (KIND == GEMM_FF_D) ff_dot_step(a.x, a.y, b, sh[i], sl[i]);
+                else if constexpr (KIND == GEMM_FF_D || KIND == GEMM_FF_DA) ff_dot_step(a.x, a.y, b, sh[i], sl[i]);
                 else ff_dot_step2(a.x, a.y, b.x, b.y, sh[i], sl[i]);
             }
         }
@@ -270,13 +272,15 @@ __device__ __forceinline__ void rows_gemm(int nbatch, int M, int N, int K, const
                     reinterpret_cast<double*>(Cv)[co] += (double)sh[i];
                 } else if constexpr (KIND == GEMM_F32_SET) {
                     reinterpret_cast<double*>(Cv)[co] = (double)sh[i];
+                } else if constexpr (KIND == GEMM_F32_SETF) {
+                    reinterpret_cast<float*>(Cv)[co] = sh[i];
                 } else if constexpr (KIND == GEMM_F32_FF) {
                     float2* cp = reinterpret_cast<float2*>(Cv) + co;
                     *cp = ff_add(*cp, make_float2(sh[i], 0.0f));
                 } else {
                     float2* cp = reinterpret_cast<float2*>(Cv) + co;
                     const float2 v = ff_norm(sh[i], sl[i]);
-                    if constexpr (KIND == GEMM_FF_F) *cp = ff_add(*cp, v);
+                    if constexpr (KIND == GEMM_FF_F || KIND == GEMM_FF_DA) *cp = ff_add(*cp, v);
                     else *cp = v;
                 }
             }
@@ -439,6 +443,11 @@ size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, int mni3
 // a pair across the x chunks of a 5-tuple and Y across the 5-tuples of a group (converted to FP64
 // for the k5 contraction); the booster operands come from FP32 copies of the boosters. GB300's FP64 pipe issues 2 FMAs per clock per SM
 // against 128 FP32 FMAs, so a pair step of about 11 FP32 instructions is several times cheaper.
+// MODE 3: as MODE 1, with the k4 contraction on the tensor cores (split BF16, below) and the S3
+// contraction in FP32. MODE 4: the booster contractions and the S3 contraction in FP32 on the
+// CUDA cores, the x-sum (phase F) on compensated FP32 pairs: Q from the (hi, lo) copies of S1 and
+// S2, P in FP32, V a pair accumulated by Dot2 steps (pair times float); the remaining FP64 work
+// is the k5 contraction and the sums across 5-tuples and groups.
 // NT threads per CTA: 512 (one CTA per SM) or 256 (two CTAs per SM, whose phases interleave).
 // A work item covers the i3 sub-range [i3b, i3b + ni3) of its output tile.
 template <int MODE, int NT>
@@ -449,6 +458,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
     constexpr bool MIX = MODE >= 1;
     constexpr bool FF = MODE == 2;
     constexpr bool TC = MODE == 3;   // k4 contraction on the tensor cores, S3 contraction FP32, x-sum FP64
+    constexpr bool PX = MODE == 4;   // S3 contraction FP32, x-sum on compensated pairs
+    constexpr bool F32IN = FF || TC || PX;   // booster operands from the FP32 copies
     constexpr int GU = FF ? 4 : 2;   // staging elements in flight per thread (FP64 values: register budget)
     extern __shared__ double smem[];
     __shared__ int s_item;
@@ -596,7 +607,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                         dst[pl] = (uint32_t)a1 | ((uint32_t)b1 << 16);
                         dst[2 * pl] = (uint32_t)a2 | ((uint32_t)b2 << 16);
                     }
-                } else if constexpr (FF) {
+                } else if constexpr (FF || PX) {
                     const float* B4 = v.Bf[2] + (int64_t)t4 * v.di[3] * v.dkmax[2];
                     for (int q = tid; q < di4 * nk4; q += nth) {
                         const int i4 = q / nk4, c4 = q % nk4;
@@ -620,7 +631,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                         d = fdiv_q(r, f_di3);
                         i3 = r - d * di3;
                     };
-                    if constexpr (FF || TC) {
+                    if constexpr (F32IN) {
                         gather_loop<4>(D * mdk * di3, tid, nth, [&](int q) {
                             int d, i3, c3;
                             b3_at(q, d, i3, c3);
@@ -660,7 +671,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                             d = fdiv_q(r, f_mdk);
                             c2 = r - d * mdk;
                         };
-                        using T2 = typename std::conditional<FF || TC, float2, double2>::type;
+                        using T2 = typename std::conditional<F32IN, float2, double2>::type;
                         gather_loop<GU>(D * mdk * nxc, tid, nth, [&](int q) {
                             int d, c2, xc;
                             sb_at(q, d, c2, xc);
@@ -669,7 +680,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                             if (c2 < s_nk2[d]) {
                                 const int k2 = s_k2lo[d] + 2 * c2, x = xc0 + 2 * xc;
                                 const int64_t bi = ((int64_t)((d * D + d24) * D + d25) * v.di[1] + ci2) * v.dkmax[0] + c2;
-                                if constexpr (FF || TC) {
+                                if constexpr (F32IN) {
                                     val.x = __ldg(v.Bf[0] + bi);
                                     val.y = s6f(v.S5f, sd5, k2, i1, x);
                                 } else {
@@ -683,7 +694,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                             sb_at(q, d, c2, xc);
                             if (c2 >= s_nk2[d]) return;
                             const int k2 = s_k2lo[d] + 2 * c2;
-                            if constexpr (FF || TC) {
+                            if constexpr (F32IN) {
                                 const float f = (float)(k2 + 1) * ((c2 & 1) ? -s_sigf[d] : s_sigf[d]);
                                 reinterpret_cast<float*>(sm.SB)[(d * mdk + c2) * XC + xc] = (f * val.x) * val.y;
                             } else {
@@ -703,7 +714,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                             c4 = fdiv_q(r, f_nk3u);
                             ku = r - c4 * nk3u;
                         };
-                        if constexpr (TC) {
+                        if constexpr (TC || PX) {
                             gather_loop<4>(nxc * nk4 * nk3u, tid, nth, [&](int q) {
                                 int xc, c4, ku;
                                 s3_at(q, xc, c4, ku);
@@ -736,7 +747,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                         }
                     }
                     // E: Q[k5][k4][x] = (2x+1) S1[i1,k5,x] S2[k5,k4,x]
-                    if constexpr (FF) {
+                    if constexpr (FF || PX) {
                         gather_loop<4>(nk5 * nk4 * nxc, tid, nth, [&](int q) {
                             const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, c5 = fdiv_q(r, f_nk4), c4 = r - c5 * nk4;
                             const int k5 = k5lo + 2 * c5, k4 = k4lo + 2 * c4, x = xc0 + 2 * xc;
@@ -831,7 +842,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                                     if (i30 + 2 < di3) f2 = fmaf(rr, bp[2], f2);
                                     if (i30 + 3 < di3) f3 = fmaf(rr, bp[3], f3);
                                 }
-                                if constexpr (FF || TC) {
+                                if constexpr (F32IN) {
                                     float* up = reinterpret_cast<float*>(sm.U) + (ku * nxc + xc) * di3 + i30;
                                     up[0] = f0;
                                     if (i30 + 1 < di3) up[1] = f1;
@@ -866,6 +877,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                     if constexpr (FF)
                         rows_gemm<GEMM_FF_D, 2>(nxc, nk4, di3, nk3u, sm.S3s, nk4 * nk3u, nk3u, sm.U, di3, nxc * di3,
                                                 sm.P, di3, nxc * di3, tid, nth);
+                    else if constexpr (PX)
+                        rows_gemm<GEMM_F32_SETF, 2>(nxc, nk4, di3, nk3u, sm.S3s, nk4 * nk3u, nk3u, sm.U, di3, nxc * di3,
+                                                    sm.P, di3, nxc * di3, tid, nth);
                     else if constexpr (TC)
                         rows_gemm<GEMM_F32_SET, 2>(nxc, nk4, di3, nk3u, sm.S3s, nk4 * nk3u, nk3u, sm.U, di3, nxc * di3,
                                                    sm.P, di3, nxc * di3, tid, nth);
@@ -877,6 +891,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                     if constexpr (FF)
                         rows_gemm<GEMM_FF_F, 2>(nk4, nk5, di3, nxc, sm.Q, nxc, nk4 * nxc, sm.P, nxc * di3, di3, sm.V,
                                                 nk5 * di3, di3, tid, nth);
+                    else if constexpr (PX)
+                        rows_gemm<GEMM_FF_DA, 2>(nk4, nk5, di3, nxc, sm.Q, nxc, nk4 * nxc, sm.P, nxc * di3, di3, sm.V,
+                                                 nk5 * di3, di3, tid, nth);
                     else
                         flat_gemm<double, true>(nk4, nk5, di3, nxc, sm.Q, nxc, nk4 * nxc, 1, sm.P, nxc * di3, di3, 1,
                                                 sm.V, nk5 * di3, di3, 1, tid, nth);
@@ -904,14 +921,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                     tc_gemm_acc(sm.Ap, sm.Bp, Mv, di4, nk4, ks, sm.Y, tid, nth);
                 } else if constexpr (MIX) {
                     for (int q = tid; q < nk4 * nk5 * di3; q += nth) {
-                        if constexpr (FF) {
+                        if constexpr (FF || PX) {
                             const float2 vv = reinterpret_cast<const float2*>(sm.V)[q];
                             sm.Vf[q] = vv.x + vv.y;
                         } else {
                             sm.Vf[q] = (float)sm.V[q];
                         }
                     }
-                    if constexpr (!FF) for (int q = tid; q < di4 * nk4; q += nth) sm.B4f[q] = (float)sm.B4[q];
+                    if constexpr (!FF && !PX) for (int q = tid; q < di4 * nk4; q += nth) sm.B4f[q] = (float)sm.B4[q];
                     __syncthreads();
                     rows_gemm<FF ? GEMM_F32_FF : GEMM_F32, 2>(nk5, di4, di3, nk4, sm.B4f, 0, nk4, sm.Vf, di3, nk5 * di3,
                                                               sm.Y, di3, nk5 * di3, tid, nth);
@@ -1007,14 +1024,14 @@ static const void* shell_fn() { return (const void*)k_shell<MODE, NT>; }
 
 static const void* shell_kernel(int mode, int nt) {
     if (nt == 256)
-        return mode == 3 ? shell_fn<3, 256>() : mode == 2 ? shell_fn<2, 256>() : mode == 1 ? shell_fn<1, 256>() : shell_fn<0, 256>();
-    return mode == 3 ? shell_fn<3, 512>() : mode == 2 ? shell_fn<2, 512>() : mode == 1 ? shell_fn<1, 512>() : shell_fn<0, 512>();
+        return mode == 4 ? shell_fn<4, 256>() : mode == 3 ? shell_fn<3, 256>() : mode == 2 ? shell_fn<2, 256>() : mode == 1 ? shell_fn<1, 256>() : shell_fn<0, 256>();
+    return mode == 4 ? shell_fn<4, 512>() : mode == 3 ? shell_fn<3, 512>() : mode == 2 ? shell_fn<2, 512>() : mode == 1 ? shell_fn<1, 512>() : shell_fn<0, 512>();
 }
 
 int sf_shell_prepare(int mode, int nt, int mdi, int mdk, int mk3u, int xc, int Dmax, int mni3, int n_items, int num_sms,
                      int* grid, size_t* smem) {
     if (nt != 256 && nt != 512) return sf_set_error(SF_ERR_ARG, "shell kernel runs 256 or 512 threads per CTA");
-    if (mode < 0 || mode > 3) return sf_set_error(SF_ERR_ARG, "unknown shell-kernel mode %d", mode);
+    if (mode < 0 || mode > 4) return sf_set_error(SF_ERR_ARG, "unknown shell-kernel mode %d", mode);
     const size_t bytes = sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax, mni3, mode) * sizeof(double);
     if (bytes > 200 * 1024) return sf_set_error(SF_ERR_LIMIT, "shell kernel needs %zu bytes of shared memory", bytes);
     const void* fn = shell_kernel(mode, nt);
@@ -1035,14 +1052,16 @@ int sf_shell_launch_prepared(int mode, int nt, int grid, size_t smem, const VtxD
     SF_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(int), s));
 #define SF_SHELL_GO(M, N)                                                                                     \
     k_shell<M, N><<<grid, N, smem, s>>>(d_v, mdi, mdk, mk3u, xc, Dmax, mni3, d_items, n_items, d_counter, d_part, filt)
-    if (mode < 0 || mode > 3) return sf_set_error(SF_ERR_ARG, "unknown shell-kernel mode %d", mode);
+    if (mode < 0 || mode > 4) return sf_set_error(SF_ERR_ARG, "unknown shell-kernel mode %d", mode);
     if (nt == 256) {
-        if (mode == 3) SF_SHELL_GO(3, 256);
+        if (mode == 4) SF_SHELL_GO(4, 256);
+        else if (mode == 3) SF_SHELL_GO(3, 256);
         else if (mode == 2) SF_SHELL_GO(2, 256);
         else if (mode == 1) SF_SHELL_GO(1, 256);
         else SF_SHELL_GO(0, 256);
     } else {
-        if (mode == 3) SF_SHELL_GO(3, 512);
+        if (mode == 4) SF_SHELL_GO(4, 512);
+        else if (mode == 3) SF_SHELL_GO(3, 512);
         else if (mode == 2) SF_SHELL_GO(2, 512);
         else if (mode == 1) SF_SHELL_GO(1, 512);
         else SF_SHELL_GO(0, 512);

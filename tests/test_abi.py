@@ -57,6 +57,6 @@ def test_argument_validation():
 def test_precision_values_match_header():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    vals = dict((k, int(v)) for k, v in re.findall(r"\b(SF_FP64|SF_MIXED_FF|SF_MIXED_TC|SF_MIXED)\s*=\s*(\d+)", src))
+    vals = dict((k, int(v)) for k, v in re.findall(r"\b(SF_FP64|SF_MIXED_FF|SF_MIXED_PX|SF_MIXED_TC|SF_MIXED)\s*=\s*(\d+)", src))
     assert vals == {"SF_FP64": sf.SF_FP64, "SF_MIXED": sf.SF_MIXED, "SF_MIXED_FF": sf.SF_MIXED_FF,
-                    "SF_MIXED_TC": sf.SF_MIXED_TC}
+                    "SF_MIXED_TC": sf.SF_MIXED_TC, "SF_MIXED_PX": sf.SF_MIXED_PX}

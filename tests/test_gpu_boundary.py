@@ -34,7 +34,7 @@ CASES = [((6,) * 10, 2, [(1, 3), (0, 2), (2, 0), (1, 4), (0, 1)]),
 
 
 @pytest.mark.parametrize("tj,dl,sub", CASES)
-@pytest.mark.parametrize("prec", [sf.SF_FP64, sf.SF_MIXED, sf.SF_MIXED_FF, sf.SF_MIXED_TC])
+@pytest.mark.parametrize("prec", [sf.SF_FP64, sf.SF_MIXED, sf.SF_MIXED_FF, sf.SF_MIXED_TC, sf.SF_MIXED_PX])
 def test_sub_range_is_block_of_whole_tensor(lib, tj, dl, sub, prec):
     bs = ob.random_boosters(tj, dl, 77)
     tw = sf.sf_6j_table([sf.vertex(tj, 1.2, dl)])
@@ -100,7 +100,7 @@ def test_adjoint_precision_and_sub_range_checks(lib):
     t = _adjoint_tables(tj, dl)
     _, dims = sf.intertwiner_ranges(tj, 1.2, dl)
     psis = [torch.tensor(v, dtype=torch.complex128, device="cuda") for v in inputs.boundary_vectors(dims)]
-    for p in (sf.SF_MIXED, sf.SF_MIXED_FF, sf.SF_MIXED_TC, 7):
+    for p in (sf.SF_MIXED, sf.SF_MIXED_FF, sf.SF_MIXED_TC, sf.SF_MIXED_PX, 7):
         with pytest.raises(sf.SfError) as e:
             sf.sf_vertex_adjoint(t, psis, precision=p)
         assert e.value.code == sf.SF_ERR_ARG

@@ -3,7 +3,8 @@ inputs with FP32 accumulation inside one (l24, l34) 5-tuple; the {6j} contractio
 every cross-shell sum stay FP64. SF_MIXED_FF: the same booster contractions, with the {6j}
 contractions and the x-sum in compensated FP32 pairs (Dot2). SF_MIXED_TC: the k4 contraction on the
 tensor cores (split BF16, FP32 accumulation), the k2, l23 and k3 contractions in FP32, the x-sum
-and the cross-shell sums in FP64. Stated bound for all three: normwise
+and the cross-shell sums in FP64. SF_MIXED_PX: the booster and S3 contractions in FP32 on the
+CUDA cores, the x-sum in compensated FP32 pairs. Stated bound for all four: normwise
 relative error <= 1e-6 against the FP64 results, reported beside the cancellation factor
 kappa = sum_s ||C_s|| / ||sum_s C_s||."""
 import numpy as np
@@ -23,7 +24,7 @@ def _rel(a, b):
     return float((a - b).norm() / b.norm())
 
 
-MIXED_PATHS = [sf.SF_MIXED, sf.SF_MIXED_FF, sf.SF_MIXED_TC]
+MIXED_PATHS = [sf.SF_MIXED, sf.SF_MIXED_FF, sf.SF_MIXED_TC, sf.SF_MIXED_PX]
 
 
 @pytest.mark.parametrize("prec", MIXED_PATHS)
@@ -61,5 +62,6 @@ def test_fp64_path_unchanged_by_mixed_instantiation(lib):
     sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED)
     sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED_FF)
     sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED_TC)
+    sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED_PX)
     b = sf.sf_vertex_amplitude(t)[0]
     assert torch.equal(a, b)

@@ -34,7 +34,7 @@ def batch(lib):
     return bt, t, bss
 
 
-@pytest.mark.parametrize("prec", [sf.SF_FP64, sf.SF_MIXED, sf.SF_MIXED_FF, sf.SF_MIXED_TC])
+@pytest.mark.parametrize("prec", [sf.SF_FP64, sf.SF_MIXED, sf.SF_MIXED_FF, sf.SF_MIXED_TC, sf.SF_MIXED_PX])
 def test_plan_run_equals_plain_call(batch, prec):
     bt, t, _ = batch
     plan = sf.Plan(t, prec, 0, SHELL_END)
@@ -102,7 +102,7 @@ def test_explicit_tilings(batch, tiling):
     plan.sync()
     for a, b in zip(outs, base):
         assert float((a - b).norm()) <= 1e-13 * max(float(b.norm()), 1e-300)
-    for prec in (sf.SF_MIXED, sf.SF_MIXED_FF, sf.SF_MIXED_TC):
+    for prec in (sf.SF_MIXED, sf.SF_MIXED_FF, sf.SF_MIXED_TC, sf.SF_MIXED_PX):
         mixed = sf.Plan(t, prec, 0, SHELL_END, tiling=tiling)
         outm = mixed.run()
         mixed.sync()

@@ -25,7 +25,7 @@ def test_restricted_tables_give_the_same_bits(lib, lam, dl, frac):
     sf.sf_boosters(full, RULE)
     part = sf.sf_6j_table(verts, shell_range=(b, e))
     sf.sf_boosters(part, RULE)
-    for prec in (sf.SF_FP64, sf.SF_MIXED, sf.SF_MIXED_FF, sf.SF_MIXED_TC):
+    for prec in (sf.SF_FP64, sf.SF_MIXED, sf.SF_MIXED_FF, sf.SF_MIXED_TC, sf.SF_MIXED_PX):
         a = sf.sf_vertex_amplitude(full, prec, b, e)
         c = sf.sf_vertex_amplitude(part, prec, b, e)
         for x, y in zip(a, c):

@@ -60,8 +60,10 @@ def test_full_size_shell_subsets(lib, name):
     amx = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED, shell_list=shells)[0].cpu().numpy()
     aff = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED_FF, shell_list=shells)[0].cpu().numpy()
     atc = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED_TC, shell_list=shells)[0].cpu().numpy()
+    atf = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED_PX, shell_list=shells)[0].cpu().numpy()
     ref = g["A"]
-    for a, bound in ((a64, FP64_BOUND), (amx, MIXED_BOUND), (aff, MIXED_BOUND), (atc, MIXED_BOUND)):
+    for a, bound in ((a64, FP64_BOUND), (amx, MIXED_BOUND), (aff, MIXED_BOUND), (atc, MIXED_BOUND),
+                     (atf, MIXED_BOUND)):
         if "idx" in g:      # large tensor: a seeded sample of entries plus the norm of the whole
             assert abs(np.linalg.norm(a) - float(g["A_norm"])) <= bound * float(g["A_norm"])
             got = a.reshape(-1)[g["idx"]]
@@ -209,6 +211,7 @@ def test_random_batch_256_against_oracle(lib, batch256):
     outmx = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED, shell_end=BATCH_SHELL_END)
     outff = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED_FF, shell_end=BATCH_SHELL_END)
     outtc = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED_TC, shell_end=BATCH_SHELL_END)
+    outtf = sf.sf_vertex_amplitude(t, precision=sf.SF_MIXED_PX, shell_end=BATCH_SHELL_END)
     small = [i for i, b in enumerate(batch) if b["dl"] <= 2]
     assert small
     rng = np.random.default_rng(7)
@@ -219,6 +222,7 @@ def test_random_batch_256_against_oracle(lib, batch256):
         assert _rel(outmx[int(i)].cpu().numpy(), ref) <= MIXED_BOUND
         assert _rel(outff[int(i)].cpu().numpy(), ref) <= MIXED_BOUND
         assert _rel(outtc[int(i)].cpu().numpy(), ref) <= MIXED_BOUND
+        assert _rel(outtf[int(i)].cpu().numpy(), ref) <= MIXED_BOUND
 
 
 def test_random_batch_256_against_single_launches(lib, batch256):
@@ -272,7 +276,7 @@ def test_sweep_small_vertices_full_size(lib, lam):
     assert abs(kap[0] - kref) <= 1e-10 * kref, (kap[0], kref)
     amax = float(np.abs(ref).max())
     for prec, bound in ((sf.SF_FP64, FP64_BOUND), (sf.SF_MIXED, MIXED_BOUND), (sf.SF_MIXED_FF, MIXED_BOUND),
-                        (sf.SF_MIXED_TC, MIXED_BOUND)):
+                        (sf.SF_MIXED_TC, MIXED_BOUND), (sf.SF_MIXED_PX, MIXED_BOUND)):
         a = outs[0] if prec == sf.SF_FP64 else sf.sf_vertex_amplitude(t, precision=prec)[0]
         a = a.cpu().numpy()
         assert a.shape == ref.shape
