@@ -305,6 +305,22 @@ __device__ __forceinline__ float s6f(const float* __restrict__ S, const SlotDesc
     return i < 0 ? 0.0f : __ldg(S + sd.off + i);
 }
 
+// Asynchronous global-to-shared copies of 4 or 8 bytes (cp.async, cached at all levels): the
+// bytes beyond src_bytes are zero-filled, and with src_bytes 0 nothing is read. A thread issues
+// any number of them without holding registers for the values; cp_async_wait_all waits for all
+// of the thread's copies (a barrier then publishes them to the block).
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // ----------------------------------------------------------------------------------------------
 // Tensor-core booster contraction (SF_MIXED_TC). An FP32 value v is split into three BF16 pieces,
 // h0 = bf16(v), h1 = bf16(v - h0), h2 = bf16(v - h0 - h1) (each difference exact in FP32), which
@@ -388,6 +404,8 @@ struct ShellSmem {
     double *Y, *V, *B3s, *B4, *B5, *S3s, *Q, *R, *P, *SB, *U;
     float *Vf, *B4f;   // mixed path: FP32 copies for the k4 booster contraction
     unsigned short *Ap, *Bp;   // tensor-core path: BF16 planes of V^T and of B4'
+    float* B2s;                // pair x-sum path: the scaled B2 entries of the 5-tuple, [d][c2]
+    float2* S1s;               // pair x-sum path: the S1 pairs of the x chunk, [c5][x]
 };
 
 // Shared-memory layout of one CTA. mni3: largest i3 extent of a work item. Buffers whose
@@ -399,8 +417,12 @@ __host__ __device__ inline size_t shell_chunk_doubles(int mdk, int mk3u, int xc,
     const size_t su = (size_t)D * mdk * xc > (size_t)mk3u * xc * mni3 ? (size_t)D * mdk * xc : (size_t)mk3u * xc * mni3;
     return (size_t)xc * mdk * mk3u + (size_t)mdk * mdk * xc + rp + su;
 }
+// extra space of the pair x-sum path: B2s (D x mdk floats) and S1s (mdk x xc pairs)
+__host__ __device__ inline size_t shell_px_doubles(int mdk, int xc, int D) {
+    return ((size_t)D * mdk + 1) / 2 + (size_t)mdk * xc;
+}
 
-__device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int xc, int D, int mni3, bool tc) {
+__device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int xc, int D, int mni3, bool tc, bool px) {
     ShellSmem s;
     double* p = base;
     s.Y = p;   p += mdi * mdk * mni3;
@@ -412,6 +434,9 @@ __device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int 
     p += (mdi * mdk + 1) / 2;
     s.Bp = reinterpret_cast<unsigned short*>(p);
     if (tc) p += tc_bp_doubles(mdi, mdk);
+    s.B2s = reinterpret_cast<float*>(p);
+    s.S1s = reinterpret_cast<float2*>(p + ((size_t)D * mdk + 1) / 2);
+    if (px) p += shell_px_doubles(mdk, xc, D);
     double* chunk = p;
     s.Ap = reinterpret_cast<unsigned short*>(chunk);   // after the x loop, over the chunk buffers
     s.S3s = p; p += xc * mdk * mk3u;
@@ -426,12 +451,13 @@ __device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int 
 }
 
 size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, int mni3, int mode) {
-    const bool mix = mode >= 1, tc = mode == 3;
+    const bool mix = mode >= 1, tc = mode == 3, px = mode == 4;
     const size_t chunk = shell_chunk_doubles(mdk, mk3u, xc, D, mni3);
     size_t over = mix ? ((size_t)mdk * mdk * mni3 + 1) / 2 : 0;   // Vf, or the V^T planes
     if (tc) over = tc_ap_doubles(mdk, mni3);
     return (size_t)mdi * mdk * mni3 + (size_t)mdk * mdk * mni3 + (size_t)D * mdk * mni3 + 2ull * mdi * mdk +
-           ((size_t)mdi * mdk + 1) / 2 + (tc ? tc_bp_doubles(mdi, mdk) : 0) + (chunk > over ? chunk : over);
+           ((size_t)mdi * mdk + 1) / 2 + (tc ? tc_bp_doubles(mdi, mdk) : 0) + (px ? shell_px_doubles(mdk, xc, D) : 0) +
+           (chunk > over ? chunk : over);
 }
 
 // MODE 0: every phase in FP64 (the FP64 path). MODE 1 (the mixed path): the booster
@@ -472,7 +498,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
     __shared__ VtxDev s_v;          // the current work item's vertex record
     __shared__ int s_vtx;
     if (threadIdx.x == 0) s_vtx = -1;
-    const ShellSmem sm = carve(smem, mdi, mdk, mk3u, XC, Dmax, mni3, TC);
+    const ShellSmem sm = carve(smem, mdi, mdk, mk3u, XC, Dmax, mni3, TC, PX);
     const int tid = threadIdx.x, nth = NT;
     for (;;) {
         __syncthreads();
@@ -631,7 +657,28 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                         d = fdiv_q(r, f_di3);
                         i3 = r - d * di3;
                     };
-                    if constexpr (F32IN) {
+                    if constexpr (PX) {
+                        // asynchronous copies (zero past the row's dk1 entries), and the scaled
+                        // B2 entries of the 5-tuple: B2s[d][c2] = sigma_d (2k2+1)(-1)^c2 B2[t2][i2][k2]
+                        float* b3f = reinterpret_cast<float*>(sm.B3s);
+                        for (int q = tid; q < D * mdk * di3; q += nth) {
+                            int d, i3, c3;
+                            b3_at(q, d, i3, c3);
+                            const float* src = v.Bf[1] + ((int64_t)(t30 + d) * di3f + i3b + i3) * dk1 + c3;
+                            cp_async4(b3f + (d * mdk + c3) * di3 + i3, c3 < dk1 ? src : v.Bf[1], c3 < dk1 ? 4 : 0);
+                        }
+                        for (int q = tid; q < D * mdk; q += nth) {
+                            const int d = q / mdk, c2 = q - d * mdk;
+                            float b = 0.0f;
+                            if (c2 < s_nk2[d]) {
+                                const int k2 = s_k2lo[d] + 2 * c2;
+                                const int64_t bi = ((int64_t)((d * D + d24) * D + d25) * v.di[1] + ci2) * v.dkmax[0] + c2;
+                                const float f = (float)(k2 + 1) * ((c2 & 1) ? -s_sigf[d] : s_sigf[d]);
+                                b = f * __ldg(v.Bf[0] + bi);
+                            }
+                            sm.B2s[q] = b;
+                        }
+                    } else if constexpr (F32IN) {
                         gather_loop<4>(D * mdk * di3, tid, nth, [&](int q) {
                             int d, i3, c3;
                             b3_at(q, d, i3, c3);
@@ -663,6 +710,48 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                     // A: SB[d][k2][x] = sigma_d (2k2+1)(-1)^(k2-k2lo) B2[t2][i2][k2] S5[k2,i1,x];
                     //    S3s[x][k4][k3u] staged from the S3 slot (zero outside its box)
                     const FDiv f_nxc = fdiv_make(nxc), f_mdk = fdiv_make(mdk), f_nk4 = fdiv_make(nk4);
+                    if constexpr (PX) {
+                        // every operand by asynchronous copies (zero outside the slot boxes), then
+                        // the products in place: SB = B2s S5 and Q = ((S1 S2) (2x+1)) as pairs, with
+                        // the roundings of forming them from loaded values
+                        float* sbf = reinterpret_cast<float*>(sm.SB);
+                        float* s3f = reinterpret_cast<float*>(sm.S3s);
+                        float2* qf = reinterpret_cast<float2*>(sm.Q);
+                        for (int q = tid; q < D * mdk * nxc; q += nth) {
+                            const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, d = fdiv_q(r, f_mdk), c2 = r - d * mdk;
+                            if (c2 >= s_nk2[d]) continue;
+                            const int i = s6_index(sd5, s_k2lo[d] + 2 * c2, i1, xc0 + 2 * xc);
+                            cp_async4(sbf + (d * mdk + c2) * XC + xc, i < 0 ? v.S5f : v.S5f + sd5.off + i, i < 0 ? 0 : 4);
+                        }
+                        for (int q = tid; q < nxc * nk4 * nk3u; q += nth) {
+                            const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, c4 = fdiv_q(r, f_nk3u), ku = r - c4 * nk3u;
+                            const int i = s6_index(sd3, k4lo + 2 * c4, k3ulo + 2 * ku, xc0 + 2 * xc);
+                            const float* src = reinterpret_cast<const float*>(v.Sff[2] + (i < 0 ? 0 : sd3.off + i));
+                            cp_async4(s3f + (xc * nk4 + c4) * nk3u + ku, src, i < 0 ? 0 : 4);   // the high part
+                        }
+                        for (int q = tid; q < nk5 * nk4 * nxc; q += nth) {
+                            const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, c5 = fdiv_q(r, f_nk4), c4 = r - c5 * nk4;
+                            const int i = s6_index(sd2, k5lo + 2 * c5, k4lo + 2 * c4, xc0 + 2 * xc);
+                            cp_async8(qf + q, v.Sff[1] + (i < 0 ? 0 : sd2.off + i), i < 0 ? 0 : 8);
+                        }
+                        for (int q = tid; q < nk5 * nxc; q += nth) {
+                            const int c5 = fdiv_q(q, f_nxc), xc = q - c5 * nxc;
+                            const int i = s6_index(sd1, i1, k5lo + 2 * c5, xc0 + 2 * xc);
+                            cp_async8(sm.S1s + q, v.Sff[0] + (i < 0 ? 0 : sd1.off + i), i < 0 ? 0 : 8);
+                        }
+                        cp_async_wait_all();
+                        __syncthreads();
+                        for (int q = tid; q < D * mdk * nxc; q += nth) {
+                            const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, d = fdiv_q(r, f_mdk), c2 = r - d * mdk;
+                            if (c2 >= s_nk2[d]) continue;
+                            float* e = sbf + (d * mdk + c2) * XC + xc;
+                            *e = sm.B2s[d * mdk + c2] * *e;
+                        }
+                        for (int q = tid; q < nk5 * nk4 * nxc; q += nth) {
+                            const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, c5 = fdiv_q(r, f_nk4);
+                            qf[q] = ff_mul_f(ff_mul(sm.S1s[c5 * nxc + xc], qf[q]), (float)(xc0 + 2 * xc + 1));
+                        }
+                    } else {
                     {
                         // SB: gather (B2 entry, S5 entry) pairs, then scale and store
                         auto sb_at = [&](int q, int& d, int& c2, int& xc) {
@@ -768,6 +857,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                         }, [&](int q, double2 val) {
                             sm.Q[q] = val.x * val.y;
                         });
+                    }
                     }
                     __syncthreads();
                     // B: R[d][k3][x] = (2k3+1)(-1)^(k3-k3lo) sum_k2 S4_d[k3,k2,x] SB[d][k2][x]
