@@ -572,19 +572,14 @@ extern "C" int sf_boosters(sf_tables* t, const sf_quad_rule* q, cudaStream_t str
     SF_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, sizeof(int), stream));
     void* scratch = nullptr;
     const size_t sbytes = pbytes_max[0] + pbytes_max[1] + tbytes_max[0] + tbytes_max[1];
-    {
-        cudaError_t ce = cudaMallocAsync(&scratch, sbytes, stream);
-        if (ce != cudaSuccess)
-            return sf_set_error(SF_ERR_OOM, "cudaMallocAsync(%zu) of the booster pair tables failed: %s", sbytes,
-                                cudaGetErrorString(ce));
-    }
+    SF_TRY(sf_scratch_alloc(&scratch, sbytes, stream));
     double2* d_P[2] = {(double2*)scratch, (double2*)((char*)scratch + pbytes_max[0])};
     double* d_T[2] = {(double*)((char*)scratch + pbytes_max[0] + pbytes_max[1]),
                       (double*)((char*)scratch + pbytes_max[0] + pbytes_max[1] + tbytes_max[0])};
     int rc = boosters_all(t, nnodes, d_P, d_T, stream);
-    cudaError_t fe = cudaFreeAsync(scratch, stream);
+    const int fr = sf_scratch_free(scratch, stream);
     if (rc != SF_OK) return rc;
-    SF_CUDA_TRY(fe);
+    SF_TRY(fr);
     return check_status(t, stream, "sf_boosters");
 }
 

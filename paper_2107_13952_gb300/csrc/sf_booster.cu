@@ -120,6 +120,48 @@ int sf_gl_library(cudaStream_t s, const double** out) {
     return SF_OK;
 }
 
+// Stream-ordered scratch from a memory pool of the library's own on each device. The pool keeps
+// the memory that is freed into it (no release threshold), so a scratch buffer of the same size
+// on the next call is served without mapping new pages; the runtime's default pool, whose
+// threshold is zero, would hand the memory back to the driver at every synchronisation.
+static std::mutex g_pool_mutex;
+static cudaMemPool_t g_pool[SF_MAX_DEVICES];
+static bool g_pool_made[SF_MAX_DEVICES];
+
+int sf_scratch_alloc(void** p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    int dev = 0;
+    SF_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= SF_MAX_DEVICES) return sf_set_error(SF_ERR_LIMIT, "device ordinal %d beyond %d", dev, SF_MAX_DEVICES);
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mutex);
+        if (!g_pool_made[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            SF_CUDA_TRY(cudaMemPoolCreate(&g_pool[dev], &props));
+            uint64_t keep = UINT64_MAX;
+            SF_CUDA_TRY(cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+            g_pool_made[dev] = true;
+        }
+        pool = g_pool[dev];
+    }
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes ? bytes : 16, pool, s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return sf_set_error(SF_ERR_OOM, "scratch allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    return SF_OK;
+}
+
+int sf_scratch_free(void* p, cudaStream_t s) {
+    if (!p) return SF_OK;
+    SF_CUDA_TRY(cudaFreeAsync(p, s));
+    return SF_OK;
+}
+
 int sf_rule_build(const sf_quad_rule* q, double* d_x, double* d_w, double* d_r, double* d_W, cudaStream_t s) {
     int n = q->n_panels * q->order;
     k_rule_nodes<<<(n + 127) / 128, 128, 0, s>>>(q->r_max, q->n_panels, q->order, d_x, d_w, d_r, d_W);

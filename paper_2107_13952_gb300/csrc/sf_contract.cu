@@ -142,7 +142,7 @@ extern "C" int sf_contract_vectors(const double* A, const int32_t dim[5], int32_
     c2* P = reinterpret_cast<c2*>(out);
     void* tmp = nullptr;
     if (n_vec > 3) {
-        SF_CUDA_TRY(cudaMallocAsync(&tmp, (size_t)dim[0] * dim[1] * sizeof(c2), stream));
+        SF_TRY(sf_scratch_alloc(&tmp, (size_t)dim[0] * dim[1] * sizeof(c2), stream));
         P = reinterpret_cast<c2*>(tmp);
     }
     int rc = launch_slabs(A, dim, p[2], p[3], p[4], P, stream);
@@ -153,7 +153,7 @@ extern "C" int sf_contract_vectors(const double* A, const int32_t dim[5], int32_
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) rc = sf_set_error(SF_ERR_CUDA, "contraction launch: %s", cudaGetErrorString(e));
     }
-    if (tmp) cudaFreeAsync(tmp, stream);
+    if (tmp) sf_scratch_free(tmp, stream);
     return rc;
 }
 
@@ -213,7 +213,7 @@ extern "C" int sf_contract_vertices(const double* A, const double* B, int64_t n,
     if (G > (n + 511) / 512) G = (n + 511) / 512;
     if (G < 1) G = 1;
     double* part = nullptr;
-    SF_CUDA_TRY(cudaMallocAsync((void**)&part, (size_t)G * sizeof(double), stream));
+    SF_TRY(sf_scratch_alloc((void**)&part, (size_t)G * sizeof(double), stream));
     k_dot_chunks<<<(unsigned)G, 256, 0, stream>>>(A, B, n, part);
     sf_note_launch(1);
     cudaError_t e = cudaGetLastError();
@@ -222,7 +222,7 @@ extern "C" int sf_contract_vertices(const double* A, const double* B, int64_t n,
         sf_note_launch(1);
         e = cudaGetLastError();
     }
-    cudaFreeAsync(part, stream);
+    sf_scratch_free(part, stream);
     if (e != cudaSuccess) return sf_set_error(SF_ERR_CUDA, "contraction launch: %s", cudaGetErrorString(e));
     return SF_OK;
 }
@@ -291,10 +291,9 @@ extern "C" int sf_delta3_amplitudes(int32_t n_x, const double* const* A, const i
     }
     c2* T = nullptr;
     int* d_meta = nullptr;
-    SF_CUDA_TRY(cudaMallocAsync((void**)&T, (size_t)tot * sizeof(c2), stream));
-    int rc = SF_OK;
-    cudaError_t e = cudaMallocAsync((void**)&d_meta, meta.size() * sizeof(int), stream);
-    if (e != cudaSuccess) rc = sf_set_error(SF_ERR_OOM, "delta3 scratch: %s", cudaGetErrorString(e));
+    SF_TRY(sf_scratch_alloc((void**)&T, (size_t)tot * sizeof(c2), stream));
+    int rc = sf_scratch_alloc((void**)&d_meta, meta.size() * sizeof(int), stream);
+    cudaError_t e = cudaSuccess;
     if (rc == SF_OK) {
         e = cudaMemcpyAsync(d_meta, meta.data(), meta.size() * sizeof(int), cudaMemcpyHostToDevice, stream);
         if (e != cudaSuccess) rc = sf_set_error(SF_ERR_CUDA, "delta3 copy: %s", cudaGetErrorString(e));
@@ -317,8 +316,8 @@ extern "C" int sf_delta3_amplitudes(int32_t n_x, const double* const* A, const i
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = sf_set_error(SF_ERR_CUDA, "delta3 launch: %s", cudaGetErrorString(e));
     }
-    cudaFreeAsync(T, stream);
-    if (d_meta) cudaFreeAsync(d_meta, stream);
+    sf_scratch_free(T, stream);
+    if (d_meta) sf_scratch_free(d_meta, stream);
     if (rc != SF_OK) return rc;
     // the metadata was copied from this call's host vector: wait for the copy before it goes away
     SF_CUDA_TRY(cudaStreamSynchronize(stream));

@@ -279,6 +279,9 @@ int sf_to_ff(const double* d_in, float2* d_out, int64_t n, int num_sms, cudaStre
 // Gauss-Legendre library of the d-table kernel (sizes 64..SF_GL_NMAX in steps of 32), built once
 // per device and kept for the life of the process
 int sf_gl_library(cudaStream_t s, const double** out);
+// stream-ordered scratch (kept by a per-device pool of the library for reuse across calls)
+int sf_scratch_alloc(void** p, size_t bytes, cudaStream_t s);
+int sf_scratch_free(void* p, cudaStream_t s);
 int sf_rule_build(const sf_quad_rule* q, double* d_x, double* d_w, double* d_r, double* d_W, cudaStream_t s);
 // d-tables of the ten faces of one vertex (one launch): doubled boundary spins tk, l counts nl
 struct DtabFaces {
