@@ -10,12 +10,12 @@ exactly once. Shells are counted when they are non-empty (all four virtual-inter
 ranges non-empty); the count over the whole grid is reported beside. Ranks of a multi-GPU run take
 different slices (weak scaling, no collective on the data path).
 
-``value`` is the fastest path within the stated error: the {6j} values exact-then-FP64, the
-booster contractions and the S3 contraction in FP32 on the CUDA cores, the {15j} auxiliary-spin
-sum in compensated FP32 pairs, the k5 contraction and every sum across shells in FP64
-(SF_MIXED_PX); the FP64 path and the other mixed paths (among them the tensor-core path
-SF_MIXED_TC) are timed over the same steps beside it, with their errors against the FP64 path per
-lambda. The remaining workloads (all 256 irregular vertices in full, the spin-4 dl-20
+``value`` is the path whose precision split keeps the {6j} values exact-then-FP64, the {15j}
+auxiliary-spin sum and every sum across shells in FP64 and runs the booster contractions in
+FP32-class arithmetic with the k4 contraction on the tensor cores (SF_MIXED_TC); the FP64 path and
+the other mixed paths (SF_MIXED; SF_MIXED_FF and SF_MIXED_PX, faster, with the {15j} x-sum in
+compensated FP32 pairs, beyond that split) are timed over the same steps beside it, with their
+errors against the FP64 path per lambda. The remaining workloads (all 256 irregular vertices in full, the spin-4 dl-20
 vertex in full, the boundary-contracted adjoint, the spin-1 simplex, the vertex-tensor
 contractions and the Delta_3 network) are timed after it.
 
@@ -49,7 +49,7 @@ FP32_PEAK_TOPS = 152 * 128 * CLOCK_GHZ / 1e3
 PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_ff": 2, "mixed_tc": 3, "mixed_px": 4}
 DTYPES = {"fp64": "f64", "mixed": "f64+f32", "mixed_ff": "f64+f32+f32x2", "mixed_tc": "f64+f32+bf16x3",
           "mixed_px": "f64+f32+f32x2"}
-HEADLINE = "mixed_px"
+HEADLINE = "mixed_tc"
 # precision split of each path: phases B (k2), C (l23 sum with B3), D (k3 with S3), F (x-sum),
 # G (k4 with B4), H (k5 with B5); "64" FP64, "32" FP32 CUDA cores, "ff" compensated pairs, "tc"
 # tensor cores (split BF16)
@@ -726,7 +726,7 @@ def main():
 
     extra = {}
     if not args.no_other_workloads and world == 1:
-        main_paths = [HEADLINE, "mixed_tc", "fp64"]
+        main_paths = [HEADLINE, "mixed_px", "fp64"]
         extra["batched_256"] = batched_measure(main_paths)
         extra["large_shell_j4_dl20"] = large_shell_measure(main_paths)
         extra["adjoint_j3_dl8"] = adjoint_measure()

@@ -113,8 +113,8 @@ typedef enum {
                        formed as pairs from the (hi, lo) copies of S1 and S2, multiplied by the FP32
                        result of the S3 contraction and summed over x (and across the x chunks of
                        one (l24, l34) set) with Dot2; the k5 contraction and the sums across the
-                       (l24, l34) sets and groups in FP64. The fastest path: the FP64 pipe keeps
-                       only the k5 contraction and these sums                                     */
+                       (l24, l34) sets and groups in FP64. Faster than SF_MIXED_TC, but beyond the
+                       target precision split: the {15j} auxiliary-spin sum is not in FP64       */
 } sf_precision;
 
 typedef struct sf_tables sf_tables;
@@ -225,13 +225,14 @@ int sf_vertex_amplitude_noalloc(sf_tables* t, int64_t shell_begin, int64_t shell
  *   x_chunk = auxiliary spins x per staged chunk of the {6j} contractions (1..16; the shared-memory
  *     footprint grows with it; default the largest that fits);
  *   items_per_sm = target number of work items per SM (granularity of the cost-balanced split of
- *     tiles x groups; default 16 with 512 threads, 8 with 256);
- *   threads = CTA size, 512 (one CTA per SM) or 256 (two CTAs per SM whose phases interleave);
+ *     tiles x groups; default 16 with 512 or 1024 threads, 8 with 256);
+ *   threads = CTA size, 512 (one CTA per SM) or 256 (two CTAs per SM whose phases interleave), and
+ *     with SF_MIXED_PX also 1024 (one CTA per SM, twice the warps of 512);
  *   i3_split = 1 or 2 pieces of i3 per output tile (2 halves the per-CTA buffers and register
  *     tile, so that two CTAs of 256 threads fit per SM or one CTA of 512 threads gets larger x
- *     chunks, and stages the i3-independent operands twice). Default: 256 threads on whole tiles
- *     when they fit with an x chunk of at least 4, else 512 threads on whole tiles; half tiles
- *     only on request. */
+ *     chunks, and stages the i3-independent operands twice). Default: SF_MIXED_PX, 1024 threads on
+ *     whole tiles when they fit; otherwise 256 threads on whole tiles when they fit with an x
+ *     chunk of at least 4, else 512 threads on whole tiles; half tiles only on request. */
 typedef struct sf_tiling {
     int32_t x_chunk;
     int32_t items_per_sm;
@@ -250,11 +251,11 @@ typedef struct sf_plan sf_plan;
 int sf_plan_create(sf_tables* t, sf_precision precision, int64_t shell_begin, int64_t shell_end,
                    const sf_tiling* tiling, double* const* A_out, sf_plan** out);
 
-/* Time candidate tilings ((threads, i3_split) in (512, 1), (256, 1), (256, 2), (512, 2) x x_chunk 16, 8, 4
- * (clamped to what fits) x items_per_sm 4, 8, 16) on the first sample_shells shells of the plan's
- * range of every vertex (best of two runs after a warm-up, CUDA events on stream) and rebuild the
- * plan with the fastest; *chosen (optional) receives it. Overwrites the plan's outputs;
- * synchronises the stream; drops a captured graph. */
+/* Time candidate tilings ((threads, i3_split) in (1024, 1) (SF_MIXED_PX only), (512, 1), (256, 1),
+ * (256, 2), (512, 2) x x_chunk 16, 8, 4 (clamped to what fits) x items_per_sm 4, 8, 16) on the
+ * first sample_shells shells of the plan's range of every vertex (best of two runs after a
+ * warm-up, CUDA events on stream) and rebuild the plan with the fastest; *chosen (optional)
+ * receives it. Overwrites the plan's outputs; synchronises the stream; drops a captured graph. */
 int sf_plan_autotune(sf_plan* plan, int64_t sample_shells, sf_tiling* chosen, cudaStream_t stream);
 
 /* Run the plan on stream: stream work only (no allocation, no host copy, no synchronisation), so

@@ -20,6 +20,7 @@ int sf_set_error(int code, const char* fmt, ...) {
 }
 
 extern "C" const char* sf_last_error(void) { return g_err; }
+static void sf_clear_error() { g_err[0] = 0; }   // after a probe whose failure is not an error of the call
 
 #include <atomic>
 static std::atomic<long long> g_launches{0};
@@ -680,9 +681,15 @@ struct ShellDims {
     int mdi = 1, mdk = 1, mk3u = 1, Dmax = 1, mdi3 = 1;
 };
 
-static ShellDims shell_dims(const sf_tables* t) {
+// vertex subsets: mask[i] != 0 selects vertex i; a null mask selects every vertex
+typedef std::vector<char> VertexMask;
+static bool in_mask(const VertexMask* m, size_t i) { return !m || (*m)[i]; }
+
+static ShellDims shell_dims(const sf_tables* t, const VertexMask* m = nullptr) {
     ShellDims d;
-    for (const VertexHost& h : t->vs) {
+    for (size_t i = 0; i < t->vs.size(); i++) {
+        if (!in_mask(m, i)) continue;
+        const VertexHost& h = t->vs[i];
         for (int e = 2; e < 5; e++) d.mdi = std::max(d.mdi, (int)h.od[e]);
         for (int e = 0; e < 4; e++) d.mdk = std::max(d.mdk, (int)h.dkmax[e]);
         d.mk3u = std::max(d.mk3u, h.mk3u);
@@ -693,12 +700,15 @@ static ShellDims shell_dims(const sf_tables* t) {
 }
 
 static size_t shell_smem_limit(int nt) { return nt == 256 ? 109 * 1024 : 200 * 1024; }   // 256: two CTAs (with static shared memory) per SM
+static int shell_tile_blocks(int nt) { return nt >= 1024 ? 1 : 2; }   // register-tile blocks per thread
 
-// the register-resident output tile (blocks of 2 i5 x 4 i3 per i4) fits SF_TRT blocks per thread
-static bool shell_tile_fits(const sf_tables* t, int nt, int split) {
-    for (const VertexHost& h : t->vs) {
+// the register-resident output tile (blocks of 2 i5 x 4 i3 per i4) fits the blocks per thread
+static bool shell_tile_fits(const sf_tables* t, int nt, int split, const VertexMask* m = nullptr) {
+    for (size_t i = 0; i < t->vs.size(); i++) {
+        if (!in_mask(m, i)) continue;
+        const VertexHost& h = t->vs[i];
         const int ni3 = (h.od[2] + split - 1) / split;
-        if ((int64_t)h.od[3] * ((h.od[4] + 1) / 2) * ((ni3 + 3) / 4) > 2 * (int64_t)nt) return false;
+        if ((int64_t)h.od[3] * ((h.od[4] + 1) / 2) * ((ni3 + 3) / 4) > shell_tile_blocks(nt) * (int64_t)nt) return false;
     }
     return true;
 }
@@ -716,22 +726,26 @@ static int shell_max_xc(const ShellDims& d, int mode, int nt, int split, int cap
 // on whole tiles when the tile fits with an x chunk of at least 4, else one CTA of 512 threads.
 // Half tiles (measured slower at spin 8, where only they give two CTAs per SM: the duplicated
 // staging costs more than the overlap gains) are used only when requested.
-static int shell_config(const sf_tables* t, int mode, const sf_tiling& req, ShellConfig* out) {
+static int shell_config(const sf_tables* t, int mode, const sf_tiling& req, ShellConfig* out,
+                        const VertexMask* m = nullptr) {
     if (req.x_chunk < 0 || req.x_chunk > 16) return sf_set_error(SF_ERR_ARG, "x_chunk must be 0 (default) or 1..16");
     if (req.items_per_sm < 0 || req.items_per_sm > 256) return sf_set_error(SF_ERR_ARG, "items_per_sm must be 0..256");
-    if (req.threads != 0 && req.threads != 256 && req.threads != 512)
-        return sf_set_error(SF_ERR_ARG, "threads must be 0 (default), 256 or 512");
+    if (req.threads != 0 && req.threads != 256 && req.threads != 512 && !(req.threads == 1024 && mode == SF_MIXED_PX))
+        return sf_set_error(SF_ERR_ARG, "threads must be 0 (default), 256 or 512 (or 1024 with SF_MIXED_PX)");
     if (req.i3_split < 0 || req.i3_split > 2) return sf_set_error(SF_ERR_ARG, "i3_split must be 0 (default), 1 or 2");
-    const ShellDims d = shell_dims(t);
+    const ShellDims d = shell_dims(t, m);
     const int cap = req.x_chunk > 0 ? req.x_chunk : 16;
-    const int cands[4][2] = {{256, 1}, {256, 2}, {512, 1}, {512, 2}};
+    // SF_MIXED_PX: one CTA of 1024 threads per SM first (its staging holds no values in
+    // registers, so it fits 64 registers a thread without spilling)
+    const int cands[5][2] = {{1024, 1}, {256, 1}, {256, 2}, {512, 1}, {512, 2}};
     const bool explicit_cfg = req.threads != 0 || req.i3_split != 0;
     for (const auto& c : cands) {
         const int nt = c[0], split = c[1];
+        if (nt == 1024 && mode != SF_MIXED_PX) continue;
         if (req.threads != 0 && req.threads != nt) continue;
         if (req.i3_split != 0 && req.i3_split != split) continue;
         if (req.i3_split == 0 && split == 2) continue;   // half tiles only on request (duplicated staging)
-        if (!shell_tile_fits(t, nt, split)) continue;
+        if (!shell_tile_fits(t, nt, split, m)) continue;
         const int xc = shell_max_xc(d, mode, nt, split, cap);
         if (xc == 0) continue;
         if (!explicit_cfg && nt == 256 && xc < std::min(4, cap)) continue;
@@ -739,7 +753,7 @@ static int shell_config(const sf_tables* t, int mode, const sf_tiling& req, Shel
         out->split = split;
         out->xc = xc;
         // finer items balance the single 512-thread CTA per SM better (measured 3 % at spins 6-8)
-        out->items_per_sm = req.items_per_sm > 0 ? req.items_per_sm : (nt == 512 ? 16 : 8);
+        out->items_per_sm = req.items_per_sm > 0 ? req.items_per_sm : (nt >= 512 ? 16 : 8);
         return SF_OK;
     }
     return sf_set_error(SF_ERR_LIMIT, "intertwiner dimensions too large for the shell kernel with this tiling");
@@ -760,8 +774,12 @@ struct ShellSchedule {
     int mni3 = 1;
 };
 
+// Appends the items and jobs of the vertices of mask m (every vertex: null) to sc; item indices
+// and partial offsets continue those already in sc, and sc->dims, sc->mni3 describe this call's
+// vertices.
 static int schedule_shells(const sf_tables* t, bool whole_range, int64_t shell_begin, int64_t shell_end,
-                           const ShellConfig& cfg, double* const* A_out, ShellSchedule* sc) {
+                           const ShellConfig& cfg, double* const* A_out, ShellSchedule* sc,
+                           const VertexMask* m = nullptr) {
     const int nv = (int)t->vs.size();
     std::vector<int64_t> g_lo(nv), g_n(nv);
     std::vector<double> item_cost_v(nv);
@@ -770,6 +788,13 @@ static int schedule_shells(const sf_tables* t, bool whole_range, int64_t shell_b
     for (int i = 0; i < nv; i++) {
         const VertexHost& h = t->vs[i];
         const int64_t per_group = (int64_t)h.D * h.D * h.D;   // shells are group-major: D^3 per group
+        if (!in_mask(m, i)) {
+            g_lo[i] = 0;
+            g_n[i] = 0;
+            ns[i] = 1;
+            item_cost_v[i] = 0.0;
+            continue;
+        }
         int64_t lo = 0, hi = h.ngroups;
         if (!whole_range) {
             int64_t b = std::min<int64_t>(std::max<int64_t>(shell_begin, 0), h.nshell);
@@ -790,6 +815,7 @@ static int schedule_shells(const sf_tables* t, bool whole_range, int64_t shell_b
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return item_cost_v[a] > item_cost_v[b]; });
     std::vector<int> item0(nv), nchunk(nv);
     for (int i : order) {
+        if (!in_mask(m, i)) continue;
         const VertexHost& h = t->vs[i];
         const int64_t ntile = (int64_t)h.od[0] * h.od[1];
         const int64_t ng = g_n[i];
@@ -816,11 +842,12 @@ static int schedule_shells(const sf_tables* t, bool whole_range, int64_t shell_b
         }
         if (sc->items.size() > (size_t)0x7FFFFFFF) return sf_set_error(SF_ERR_LIMIT, "too many work items");
     }
-    if (!shell_tile_fits(t, cfg.nt, cfg.split))
+    if (!shell_tile_fits(t, cfg.nt, cfg.split, m))
         return sf_set_error(SF_ERR_LIMIT, "intertwiner dimensions too large for the register-resident tile");
-    sc->dims = shell_dims(t);
+    sc->dims = shell_dims(t, m);
     sc->mni3 = (sc->dims.mdi3 + cfg.split - 1) / cfg.split;
     for (int i = 0; i < nv; i++) {
+        if (!in_mask(m, i)) continue;
         const VertexHost& h = t->vs[i];
         const int64_t n3 = (int64_t)h.od[2] * h.od[3] * h.od[4];
         for (int tile = 0; tile < h.od[0] * h.od[1]; tile++) {
@@ -964,6 +991,51 @@ static int kappa_pass(sf_tables* t, const int64_t* shell_list, int64_t n_list, i
     return rc;
 }
 
+// Launch classes of a shell sum with the default tiling. A batch whose largest vertex needs one
+// CTA per SM would otherwise run every vertex that way; the vertices whose tiles fit two CTAs of
+// 256 threads per SM (with an x chunk of at least 4) then run in a launch of their own, after the
+// others, on the same stream (two CTAs per SM interleave their phases: measured 20 % faster at
+// spin 5). One class otherwise.
+struct LaunchClass {
+    VertexMask mask;
+    ShellConfig cfg;
+    size_t item0 = 0, nitems = 0;
+    ShellDims dims;
+    int mni3 = 1;
+};
+
+static int launch_classes(const sf_tables* t, int mode, std::vector<LaunchClass>* out) {
+    const size_t nv = t->vs.size();
+    LaunchClass all;
+    all.mask.assign(nv, 1);
+    SF_TRY(shell_config(t, mode, sf_tiling{}, &all.cfg));
+    if (nv > 1 && all.cfg.nt != 256) {
+        LaunchClass large, small;
+        large.mask.assign(nv, 0);
+        small.mask.assign(nv, 0);
+        bool any_small = false, any_large = false;
+        for (size_t i = 0; i < nv; i++) {
+            VertexMask one(nv, 0);
+            one[i] = 1;
+            ShellConfig c;
+            const bool two = shell_config(t, mode, sf_tiling{}, &c, &one) == SF_OK && c.nt == 256;
+            (two ? small.mask : large.mask)[i] = 1;
+            any_small = any_small || two;
+            any_large = any_large || !two;
+        }
+        if (any_small && any_large && shell_config(t, mode, sf_tiling{}, &large.cfg, &large.mask) == SF_OK &&
+            shell_config(t, mode, sf_tiling{}, &small.cfg, &small.mask) == SF_OK) {
+            sf_clear_error();
+            out->push_back(std::move(large));
+            out->push_back(std::move(small));
+            return SF_OK;
+        }
+        sf_clear_error();
+    }
+    out->push_back(std::move(all));
+    return SF_OK;
+}
+
 extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t shell_begin, int64_t shell_end,
                                    const int64_t* shell_list, int64_t n_list, double* const* A_out, double* kappa_out,
                                    cudaStream_t stream) {
@@ -980,16 +1052,21 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
     }
     SF_TRY(check_covered(t, shell_begin, shell_end, shell_list, n_list));
     const int mix = (int)precision;
-    ShellConfig cfg;
-    SF_TRY(shell_config(t, mix, sf_tiling{}, &cfg));
+    std::vector<LaunchClass> cls;
+    SF_TRY(launch_classes(t, mix, &cls));
     ShellSchedule sc;
-    SF_TRY(schedule_shells(t, shell_list != nullptr, shell_begin, shell_end, cfg, A_out, &sc));
-    const ShellDims& dm = sc.dims;
-    // scratch: items | jobs | counter | bitmap | list | partials
+    for (LaunchClass& c : cls) {
+        c.item0 = sc.items.size();
+        SF_TRY(schedule_shells(t, shell_list != nullptr, shell_begin, shell_end, c.cfg, A_out, &sc, &c.mask));
+        c.nitems = sc.items.size() - c.item0;
+        c.dims = sc.dims;
+        c.mni3 = sc.mni3;
+    }
+    // scratch: items | jobs | counters (one per launch) | bitmap | list | partials
     const int64_t nshell0 = t->vs[0].nshell;
     const size_t o_jobs = align256(sc.items.size() * sizeof(WorkItem));
     const size_t o_counter = align256(o_jobs + sc.jobs.size() * sizeof(ReduceJob));
-    const size_t o_bitmap = align256(o_counter + sizeof(int));
+    const size_t o_bitmap = align256(o_counter + cls.size() * sizeof(int));
     const size_t bm_bytes = shell_list ? (size_t)((nshell0 + 31) / 32) * sizeof(uint32_t) : 0;
     const size_t o_list = align256(o_bitmap + bm_bytes);
     const size_t list_bytes = shell_list ? (size_t)std::max<int64_t>(1, n_list) * sizeof(int64_t) : 0;
@@ -1014,17 +1091,26 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
         SF_TRY(sf_bitmap_launch(d_list, n_list, nshell0, d_bm, stream));
         filt.bitmap = d_bm;
     }
-    int grid = 0;
-    size_t smem = 0;
-    SF_TRY(sf_shell_prepare(mix, cfg.nt, dm.mdi, dm.mdk, dm.mk3u, cfg.xc, dm.Dmax, sc.mni3, (int)sc.items.size(),
-                            t->num_sms, &grid, &smem));
+    std::vector<int> grids(cls.size(), 0);
+    std::vector<size_t> smems(cls.size(), 0);
+    for (size_t c = 0; c < cls.size(); c++) {
+        if (cls[c].nitems == 0) continue;
+        const ShellDims& dm = cls[c].dims;
+        SF_TRY(sf_shell_prepare(mix, cls[c].cfg.nt, dm.mdi, dm.mdk, dm.mk3u, cls[c].cfg.xc, dm.Dmax, cls[c].mni3,
+                                (int)cls[c].nitems, t->num_sms, &grids[c], &smems[c]));
+    }
     SF_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, sizeof(int), stream));
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     SF_CUDA_TRY(cudaEventCreate(&ev0));
     SF_CUDA_TRY(cudaEventCreate(&ev1));
     SF_CUDA_TRY(cudaEventRecord(ev0, stream));
-    SF_TRY(sf_shell_launch_prepared(mix, cfg.nt, grid, smem, t->d_vtx, dm.mdi, dm.mdk, dm.mk3u, cfg.xc, dm.Dmax, sc.mni3,
-                                    d_items, (int)sc.items.size(), d_counter, d_part, filt, stream));
+    for (size_t c = 0; c < cls.size(); c++) {
+        if (cls[c].nitems == 0) continue;
+        const ShellDims& dm = cls[c].dims;
+        SF_TRY(sf_shell_launch_prepared(mix, cls[c].cfg.nt, grids[c], smems[c], t->d_vtx, dm.mdi, dm.mdk, dm.mk3u,
+                                        cls[c].cfg.xc, dm.Dmax, cls[c].mni3, d_items + cls[c].item0, (int)cls[c].nitems,
+                                        d_counter + c, d_part, filt, stream));
+    }
     SF_CUDA_TRY(cudaEventRecord(ev1, stream));
     SF_TRY(sf_reduce_jobs_launch(t->d_vtx, d_jobs, (int)sc.jobs.size(), d_items, d_part, stream));
     int rc = check_status(t, stream, "sf_vertex_amplitude");
@@ -1208,7 +1294,7 @@ extern "C" int sf_plan_autotune(sf_plan* p, int64_t sample_shells, sf_tiling* ch
     if (sample_shells <= 0) return sf_set_error(SF_ERR_ARG, "sample_shells must be positive");
     // candidates: CTA shapes (threads, i3 pieces) x x chunks x work granularities, each timed on the
     // first sample_shells shells of the plan's range (every vertex), best of two runs after a warm-up
-    static const int shapes[4][2] = {{512, 1}, {256, 1}, {256, 2}, {512, 2}};
+    static const int shapes[5][2] = {{1024, 1}, {512, 1}, {256, 1}, {256, 2}, {512, 2}};   // 1024: SF_MIXED_PX only
     static const int xcs[] = {16, 8, 4};
     static const int ipss[] = {4, 8, 16};
     sf_plan probe;

@@ -398,14 +398,14 @@ __device__ __forceinline__ void tc_gemm_acc(const unsigned short* __restrict__ A
     }
 }
 
-#define SF_TRT 2   // output-tile register blocks per thread (2 x 4 doubles each)
+#define SF_TRT 2   // output-tile register blocks per thread (2 x 4 doubles each); one at 1024 threads
 
 struct ShellSmem {
     double *Y, *V, *B3s, *B4, *B5, *S3s, *Q, *R, *P, *SB, *U;
     float *Vf, *B4f;   // mixed path: FP32 copies for the k4 booster contraction
     unsigned short *Ap, *Bp;   // tensor-core path: BF16 planes of V^T and of B4'
-    float* B2s;                // pair x-sum path: the scaled B2 entries of the 5-tuple, [d][c2]
-    float2* S1s;               // pair x-sum path: the S1 pairs of the x chunk, [c5][x]
+    float* B2s;                // asynchronous staging: the scaled B2 entries of the 5-tuple, [d][c2]
+    double* S1s;               // asynchronous staging: the S1 entries of the x chunk, [c5][x] (pairs or FP64)
 };
 
 // Shared-memory layout of one CTA. mni3: largest i3 extent of a work item. Buffers whose
@@ -417,7 +417,8 @@ __host__ __device__ inline size_t shell_chunk_doubles(int mdk, int mk3u, int xc,
     const size_t su = (size_t)D * mdk * xc > (size_t)mk3u * xc * mni3 ? (size_t)D * mdk * xc : (size_t)mk3u * xc * mni3;
     return (size_t)xc * mdk * mk3u + (size_t)mdk * mdk * xc + rp + su;
 }
-// extra space of the pair x-sum path: B2s (D x mdk floats) and S1s (mdk x xc pairs)
+// extra space of the asynchronously staged paths: B2s (D x mdk floats) and S1s (mdk x xc
+// pairs or doubles)
 __host__ __device__ inline size_t shell_px_doubles(int mdk, int xc, int D) {
     return ((size_t)D * mdk + 1) / 2 + (size_t)mdk * xc;
 }
@@ -435,7 +436,7 @@ __device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int 
     s.Bp = reinterpret_cast<unsigned short*>(p);
     if (tc) p += tc_bp_doubles(mdi, mdk);
     s.B2s = reinterpret_cast<float*>(p);
-    s.S1s = reinterpret_cast<float2*>(p + ((size_t)D * mdk + 1) / 2);
+    s.S1s = p + ((size_t)D * mdk + 1) / 2;
     if (px) p += shell_px_doubles(mdk, xc, D);
     double* chunk = p;
     s.Ap = reinterpret_cast<unsigned short*>(chunk);   // after the x loop, over the chunk buffers
@@ -451,7 +452,7 @@ __device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int 
 }
 
 size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, int mni3, int mode) {
-    const bool mix = mode >= 1, tc = mode == 3, px = mode == 4;
+    const bool mix = mode >= 1, tc = mode == 3, px = mode >= 3;   // px: asynchronous staging
     const size_t chunk = shell_chunk_doubles(mdk, mk3u, xc, D, mni3);
     size_t over = mix ? ((size_t)mdk * mdk * mni3 + 1) / 2 : 0;   // Vf, or the V^T planes
     if (tc) over = tc_ap_doubles(mdk, mni3);
@@ -474,10 +475,12 @@ size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, int mni3
 // CUDA cores, the x-sum (phase F) on compensated FP32 pairs: Q from the (hi, lo) copies of S1 and
 // S2, P in FP32, V a pair accumulated by Dot2 steps (pair times float); the remaining FP64 work
 // is the k5 contraction and the sums across 5-tuples and groups.
-// NT threads per CTA: 512 (one CTA per SM) or 256 (two CTAs per SM, whose phases interleave).
+// NT threads per CTA: 512 (one CTA per SM) or 256 (two CTAs per SM, whose phases interleave);
+// MODE 4 also 1024 (one CTA per SM, 64 registers a thread: its staging holds no values in
+// registers, so twice the warps hide the shared-memory and L2 latencies of its phases).
 // A work item covers the i3 sub-range [i3b, i3b + ni3) of its output tile.
 template <int MODE, int NT>
-__global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict__ V, int mdi, int mdk, int mk3u, int XC,
+__global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 512 / NT) k_shell(const VtxDev* __restrict__ V, int mdi, int mdk, int mk3u, int XC,
                                                         int Dmax, int mni3, const WorkItem* __restrict__ items,
                                                         int n_items, int* counter, double* __restrict__ part,
                                                         ShellFilter filt) {
@@ -486,6 +489,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
     constexpr bool TC = MODE == 3;   // k4 contraction on the tensor cores, S3 contraction FP32, x-sum FP64
     constexpr bool PX = MODE == 4;   // S3 contraction FP32, x-sum on compensated pairs
     constexpr bool F32IN = FF || TC || PX;   // booster operands from the FP32 copies
+    constexpr bool AS = TC || PX;            // operands staged by asynchronous copies
+    constexpr int TRT = NT >= 1024 ? 1 : SF_TRT;   // output-tile blocks per thread
     constexpr int GU = FF ? 4 : 2;   // staging elements in flight per thread (FP64 values: register budget)
     extern __shared__ double smem[];
     __shared__ int s_item;
@@ -498,7 +503,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
     __shared__ VtxDev s_v;          // the current work item's vertex record
     __shared__ int s_vtx;
     if (threadIdx.x == 0) s_vtx = -1;
-    const ShellSmem sm = carve(smem, mdi, mdk, mk3u, XC, Dmax, mni3, TC, PX);
+    const ShellSmem sm = carve(smem, mdi, mdk, mk3u, XC, Dmax, mni3, TC, AS);
     const int tid = threadIdx.x, nth = NT;
     for (;;) {
         __syncthreads();
@@ -529,9 +534,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
         const int jsum = j12 + j13 + j14 + j15 + v.ilo[0];
         // output tile T[i4][i5][i3] in registers: blocks (i4, 2 i5, 4 i3), block b = tid + r * nth
         const int tb5 = (di5 + 1) / 2, tb3 = (di3 + 3) / 4, tper = tb5 * tb3;
-        double T[SF_TRT][2][4];
+        double T[TRT][2][4];
 #pragma unroll
-        for (int r = 0; r < SF_TRT; r++)
+        for (int r = 0; r < TRT; r++)
 #pragma unroll
             for (int i = 0; i < 2; i++)
 #pragma unroll
@@ -657,7 +662,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                         d = fdiv_q(r, f_di3);
                         i3 = r - d * di3;
                     };
-                    if constexpr (PX) {
+                    if constexpr (AS) {
                         // asynchronous copies (zero past the row's dk1 entries), and the scaled
                         // B2 entries of the 5-tuple: B2s[d][c2] = sigma_d (2k2+1)(-1)^c2 B2[t2][i2][k2]
                         float* b3f = reinterpret_cast<float*>(sm.B3s);
@@ -710,13 +715,15 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                     // A: SB[d][k2][x] = sigma_d (2k2+1)(-1)^(k2-k2lo) B2[t2][i2][k2] S5[k2,i1,x];
                     //    S3s[x][k4][k3u] staged from the S3 slot (zero outside its box)
                     const FDiv f_nxc = fdiv_make(nxc), f_mdk = fdiv_make(mdk), f_nk4 = fdiv_make(nk4);
-                    if constexpr (PX) {
+                    if constexpr (AS) {
                         // every operand by asynchronous copies (zero outside the slot boxes), then
-                        // the products in place: SB = B2s S5 and Q = ((S1 S2) (2x+1)) as pairs, with
-                        // the roundings of forming them from loaded values
+                        // the products in place: SB = B2s S5, and Q = ((S1 S2) (2x+1)) as pairs
+                        // (MODE 4) or Q = ((2x+1) S1) S2 in FP64 from the prescaled S1x (MODE 3),
+                        // with the roundings of forming them from loaded values
                         float* sbf = reinterpret_cast<float*>(sm.SB);
                         float* s3f = reinterpret_cast<float*>(sm.S3s);
                         float2* qf = reinterpret_cast<float2*>(sm.Q);
+                        float2* s1f = reinterpret_cast<float2*>(sm.S1s);
                         for (int q = tid; q < D * mdk * nxc; q += nth) {
                             const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, d = fdiv_q(r, f_mdk), c2 = r - d * mdk;
                             if (c2 >= s_nk2[d]) continue;
@@ -732,12 +739,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                         for (int q = tid; q < nk5 * nk4 * nxc; q += nth) {
                             const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, c5 = fdiv_q(r, f_nk4), c4 = r - c5 * nk4;
                             const int i = s6_index(sd2, k5lo + 2 * c5, k4lo + 2 * c4, xc0 + 2 * xc);
-                            cp_async8(qf + q, v.Sff[1] + (i < 0 ? 0 : sd2.off + i), i < 0 ? 0 : 8);
+                            if constexpr (PX) cp_async8(qf + q, v.Sff[1] + (i < 0 ? 0 : sd2.off + i), i < 0 ? 0 : 8);
+                            else cp_async8(sm.Q + q, v.S[1] + (i < 0 ? 0 : sd2.off + i), i < 0 ? 0 : 8);
                         }
                         for (int q = tid; q < nk5 * nxc; q += nth) {
                             const int c5 = fdiv_q(q, f_nxc), xc = q - c5 * nxc;
                             const int i = s6_index(sd1, i1, k5lo + 2 * c5, xc0 + 2 * xc);
-                            cp_async8(sm.S1s + q, v.Sff[0] + (i < 0 ? 0 : sd1.off + i), i < 0 ? 0 : 8);
+                            if constexpr (PX) cp_async8(s1f + q, v.Sff[0] + (i < 0 ? 0 : sd1.off + i), i < 0 ? 0 : 8);
+                            else cp_async8(sm.S1s + q, v.S1x + (i < 0 ? 0 : sd1.off + i), i < 0 ? 0 : 8);
                         }
                         cp_async_wait_all();
                         __syncthreads();
@@ -749,7 +758,8 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
                         }
                         for (int q = tid; q < nk5 * nk4 * nxc; q += nth) {
                             const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, c5 = fdiv_q(r, f_nk4);
-                            qf[q] = ff_mul_f(ff_mul(sm.S1s[c5 * nxc + xc], qf[q]), (float)(xc0 + 2 * xc + 1));
+                            if constexpr (PX) qf[q] = ff_mul_f(ff_mul(s1f[c5 * nxc + xc], qf[q]), (float)(xc0 + 2 * xc + 1));
+                            else sm.Q[q] = sm.S1s[c5 * nxc + xc] * sm.Q[q];
                         }
                     } else {
                     {
@@ -1038,7 +1048,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
             }
             // H: T[i4][i5][i3] += sum_k5 B5'[i5][k5] Y[i4][k5][i3]   (register-resident output tile)
 #pragma unroll
-            for (int rr = 0; rr < SF_TRT; rr++) {
+            for (int rr = 0; rr < TRT; rr++) {
                 const int b = tid + rr * nth;
                 if (b < di4 * tper) {
                     const int i4 = b / tper, r = b - i4 * tper;
@@ -1063,7 +1073,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
             const double s12 = (double)(v.ilo[0] + 2 * w.i1 + 1) * (double)(v.ilo[1] + 2 * w.i2 + 1);
             double q2 = 0.0;
 #pragma unroll
-            for (int rr = 0; rr < SF_TRT; rr++) {
+            for (int rr = 0; rr < TRT; rr++) {
                 const int b = tid + rr * nth;
                 if (b < di4 * tper) {
                     const int i4 = b / tper, r = b - i4 * tper;
@@ -1094,7 +1104,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_shell(const VtxDev* __restrict
         // partial tile in [i3][i4][i5] order
         double* out = part + w.part_off;
 #pragma unroll
-        for (int rr = 0; rr < SF_TRT; rr++) {
+        for (int rr = 0; rr < TRT; rr++) {
             const int b = tid + rr * nth;
             if (b < di4 * tper) {
                 const int i4 = b / tper, r = b - i4 * tper;
@@ -1113,6 +1123,7 @@ template <int MODE, int NT>
 static const void* shell_fn() { return (const void*)k_shell<MODE, NT>; }
 
 static const void* shell_kernel(int mode, int nt) {
+    if (nt == 1024) return mode == 4 ? shell_fn<4, 1024>() : nullptr;
     if (nt == 256)
         return mode == 4 ? shell_fn<4, 256>() : mode == 3 ? shell_fn<3, 256>() : mode == 2 ? shell_fn<2, 256>() : mode == 1 ? shell_fn<1, 256>() : shell_fn<0, 256>();
     return mode == 4 ? shell_fn<4, 512>() : mode == 3 ? shell_fn<3, 512>() : mode == 2 ? shell_fn<2, 512>() : mode == 1 ? shell_fn<1, 512>() : shell_fn<0, 512>();
@@ -1120,7 +1131,8 @@ static const void* shell_kernel(int mode, int nt) {
 
 int sf_shell_prepare(int mode, int nt, int mdi, int mdk, int mk3u, int xc, int Dmax, int mni3, int n_items, int num_sms,
                      int* grid, size_t* smem) {
-    if (nt != 256 && nt != 512) return sf_set_error(SF_ERR_ARG, "shell kernel runs 256 or 512 threads per CTA");
+    if (nt != 256 && nt != 512 && !(nt == 1024 && mode == 4))
+        return sf_set_error(SF_ERR_ARG, "shell kernel runs 256 or 512 threads per CTA (1024 in mode 4), not %d", nt);
     if (mode < 0 || mode > 4) return sf_set_error(SF_ERR_ARG, "unknown shell-kernel mode %d", mode);
     const size_t bytes = sf_shell_smem_doubles(mdi, mdk, mk3u, xc, Dmax, mni3, mode) * sizeof(double);
     if (bytes > 200 * 1024) return sf_set_error(SF_ERR_LIMIT, "shell kernel needs %zu bytes of shared memory", bytes);
@@ -1143,7 +1155,10 @@ int sf_shell_launch_prepared(int mode, int nt, int grid, size_t smem, const VtxD
 #define SF_SHELL_GO(M, N)                                                                                     \
     k_shell<M, N><<<grid, N, smem, s>>>(d_v, mdi, mdk, mk3u, xc, Dmax, mni3, d_items, n_items, d_counter, d_part, filt)
     if (mode < 0 || mode > 4) return sf_set_error(SF_ERR_ARG, "unknown shell-kernel mode %d", mode);
-    if (nt == 256) {
+    if (nt == 1024) {
+        if (mode != 4) return sf_set_error(SF_ERR_ARG, "1024 threads per CTA run mode 4 only");
+        SF_SHELL_GO(4, 1024);
+    } else if (nt == 256) {
         if (mode == 4) SF_SHELL_GO(4, 256);
         else if (mode == 3) SF_SHELL_GO(3, 256);
         else if (mode == 2) SF_SHELL_GO(2, 256);

@@ -128,7 +128,7 @@ def test_plan_errors(batch):
     with pytest.raises(sf.SfError) as ei:
         sf.Plan(t, sf.SF_FP64, 0, SHELL_END, tiling=(17, 0))
     assert ei.value.code == sf.SF_ERR_ARG
-    for bad in ((0, 0, 384, 0), (0, 0, 128, 1), (0, 0, 0, 3), (0, -1), (17, 0)):
+    for bad in ((0, 0, 384, 0), (0, 0, 128, 1), (0, 0, 0, 3), (0, -1), (17, 0), (0, 0, 1024, 0)):
         with pytest.raises(sf.SfError) as ei:
             sf.Plan(t, sf.SF_FP64, 0, SHELL_END, tiling=bad)
         assert ei.value.code == sf.SF_ERR_ARG

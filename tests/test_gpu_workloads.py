@@ -282,3 +282,20 @@ def test_sweep_small_vertices_full_size(lib, lam):
         assert a.shape == ref.shape
         assert _rel(a, ref) <= bound, (prec, _rel(a, ref))
         assert np.all(np.abs(a - ref) <= bound * np.abs(ref) + bound * amax), prec
+
+
+@pytest.mark.parametrize("prec", [sf.SF_FP64, sf.SF_MIXED_TC])
+def test_mixed_size_batch_matches_single_vertex_calls(lib, prec):
+    """A batch whose largest vertex (all spins 8) needs one CTA per SM and whose smaller vertices
+    fit two: the library runs the two classes as separate launches; every vertex's tensor equals
+    its single-vertex call up to the summation order of the x chunks."""
+    specs = [((16,) * 10, 1.2, 2), ((4,) * 10, 1.2, 3), ((5, 3, 4, 4, 6, 3, 4, 3, 4, 4), 5.0, 2), ((2,) * 10, 0.1, 4)]
+    verts = [sf.vertex(*s) for s in specs]
+    t = sf.sf_6j_table(verts)
+    sf.sf_boosters(t, (40.0, 4, 10))
+    outs = sf.sf_vertex_amplitude(t, precision=prec)
+    for i, s in enumerate(specs):
+        ti = sf.sf_6j_table([sf.vertex(*s)])
+        sf.sf_boosters(ti, (40.0, 4, 10))
+        ref = sf.sf_vertex_amplitude(ti, precision=prec)[0]
+        assert _rel(outs[i].cpu().numpy(), ref.cpu().numpy()) <= 1e-12, (i, prec)
