@@ -79,6 +79,30 @@ def test_booster_real_and_symmetric_at_l_equal_j():
     assert im <= 1e-14 * np.abs(B).max()
 
 
+def test_booster_strand_exchange_phases():
+    """The booster couples its strands as (a1 a2)(a3 a4) in both 4jm symbols and integrates a
+    product symmetric in the strands, so exchanging strands changes it by the 3j phases alone
+    (eq. booster with the 4jm of the framed algorithm): a1 <-> a2 by (-1)^(j1+j2+i+l1+l2+k),
+    a3 <-> a4 by (-1)^(j3+j4+i+l3+l4+k), and the pairs (a1 a2) <-> (a3 a4) by (-1)^(2i+2k).
+    A booster that coupled (a1 a3)(a2 a4), or a 4jm without its (-1)^(i-m), fails these."""
+    xs, ws = quadrature.rule_nodes(40, 6, 12)
+    wm = booster.node_weights(xs, ws)
+    tj, tl = (2, 1, 3, 2), (4, 3, 5, 2)
+    tabs = [booster.DTable(a, 1.2, [b], xs) for a, b in zip(tj, tl)]
+    B, ir, kr, _ = booster.booster(tj, tl, tabs, wm)
+    assert np.abs(B).max() > 0
+    cases = [((1, 0, 2, 3), lambda ti, tk: (tj[0] + tj[1] + ti + tl[0] + tl[1] + tk) // 2),
+             ((0, 1, 3, 2), lambda ti, tk: (tj[2] + tj[3] + ti + tl[2] + tl[3] + tk) // 2),
+             ((2, 3, 0, 1), lambda ti, tk: ti + tk)]
+    for perm, phase in cases:
+        Bp, irp, krp, _ = booster.booster(tuple(tj[q] for q in perm), tuple(tl[q] for q in perm),
+                                          [tabs[q] for q in perm], wm)
+        assert list(irp) == list(ir) and list(krp) == list(kr)
+        sign = np.array([[(-1) ** (phase(ti, tk) % 2) for tk in kr] for ti in ir], dtype=float)
+        np.testing.assert_allclose(Bp, sign * B, rtol=0, atol=1e-13 * np.abs(B).max())
+        assert np.abs(Bp - B).max() > 1e-3 * np.abs(B).max() or np.all(sign == 1)
+
+
 def test_booster_quadrature_converges():
     tj, tl = (2, 2, 2, 2), (2, 4, 4, 2)
     out = []
