@@ -231,6 +231,7 @@ __global__ void __launch_bounds__(SF_DT_NT) k_dtable(const __grid_constant__ Dta
     const double r = R[n];
     const double emr = exp(-r);
     const double sh2 = 2.0 * sinh(r);   // 2 sinh r (not e^r - e^-r, which cancels at small r)
+    const double ish2 = 1.0 / sh2;      // one division per node; the integrand multiplies by it
     const int kpm = (tk + tm) / 2, kmm = (tk - tm) / 2;
     double sqc = 1.0;              // sqrt(C(2k, k+m))
     {
@@ -261,8 +262,8 @@ __global__ void __launch_bounds__(SF_DT_NT) k_dtable(const __grid_constant__ Dta
             const double ev = exp(v), emv = 1.0 / ev;
             const double A = expm1(a1);   // e^{v+r} - 1
             const double Bq = expm1(a2);  // e^{r-v} - 1
-            const double t = fmin(1.0, emr * A / sh2), omt = fmin(1.0, ev * Bq / sh2);
-            const double tr = fmin(1.0, emv * A / sh2), omtr = fmin(1.0, emr * Bq / sh2);
+            const double t = fmin(1.0, emr * A * ish2), omt = fmin(1.0, ev * Bq * ish2);
+            const double tr = fmin(1.0, emv * A * ish2), omtr = fmin(1.0, emr * Bq * ish2);
             const double dk = sqc * ipow_(sqrt(omt), kpm) * ipow_(sqrt(t), kmm);
             double sn, cs;
             sincos(rho * v, &sn, &cs);

@@ -404,7 +404,7 @@ struct ShellSmem {
     double *Y, *V, *B3s, *B4, *B5, *S3s, *Q, *R, *P, *SB, *U;
     float *Vf, *B4f;   // mixed path: FP32 copies for the k4 booster contraction
     unsigned short *Ap, *Bp;   // tensor-core path: BF16 planes of V^T and of B4'
-    float* B2s;                // asynchronous staging: the scaled B2 entries of the 5-tuple, [d][c2]
+    float* B2s;                // asynchronous staging: the scaled B2 entries of the 5-tuple, [d][c2] (FP32 or FP64)
     double* S1s;               // asynchronous staging: the S1 entries of the x chunk, [c5][x] (pairs or FP64)
 };
 
@@ -417,13 +417,17 @@ __host__ __device__ inline size_t shell_chunk_doubles(int mdk, int mk3u, int xc,
     const size_t su = (size_t)D * mdk * xc > (size_t)mk3u * xc * mni3 ? (size_t)D * mdk * xc : (size_t)mk3u * xc * mni3;
     return (size_t)xc * mdk * mk3u + (size_t)mdk * mdk * xc + rp + su;
 }
-// extra space of the asynchronously staged paths: B2s (D x mdk floats) and S1s (mdk x xc
-// pairs or doubles)
-__host__ __device__ inline size_t shell_px_doubles(int mdk, int xc, int D) {
-    return ((size_t)D * mdk + 1) / 2 + (size_t)mdk * xc;
+// extra space of the asynchronously staged paths: B2s (D x mdk floats, or doubles in the FP64
+// path) and S1s (mdk x xc pairs or doubles)
+__host__ __device__ inline size_t shell_b2s_doubles(int mdk, int D, bool d64) {
+    return d64 ? (size_t)D * mdk : ((size_t)D * mdk + 1) / 2;
+}
+__host__ __device__ inline size_t shell_px_doubles(int mdk, int xc, int D, bool d64) {
+    return shell_b2s_doubles(mdk, D, d64) + (size_t)mdk * xc;
 }
 
-__device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int xc, int D, int mni3, bool tc, bool px) {
+__device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int xc, int D, int mni3, bool tc, bool px,
+                                  bool d64) {
     ShellSmem s;
     double* p = base;
     s.Y = p;   p += mdi * mdk * mni3;
@@ -436,8 +440,8 @@ __device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int 
     s.Bp = reinterpret_cast<unsigned short*>(p);
     if (tc) p += tc_bp_doubles(mdi, mdk);
     s.B2s = reinterpret_cast<float*>(p);
-    s.S1s = p + ((size_t)D * mdk + 1) / 2;
-    if (px) p += shell_px_doubles(mdk, xc, D);
+    s.S1s = p + shell_b2s_doubles(mdk, D, d64);
+    if (px) p += shell_px_doubles(mdk, xc, D, d64);
     double* chunk = p;
     s.Ap = reinterpret_cast<unsigned short*>(chunk);   // after the x loop, over the chunk buffers
     s.S3s = p; p += xc * mdk * mk3u;
@@ -452,12 +456,12 @@ __device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int 
 }
 
 size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, int mni3, int mode) {
-    const bool mix = mode >= 1, tc = mode == 3, px = mode >= 3;   // px: asynchronous staging
+    const bool mix = mode >= 1, tc = mode == 3, px = mode >= 3 || mode == 0;   // px: asynchronous staging
     const size_t chunk = shell_chunk_doubles(mdk, mk3u, xc, D, mni3);
     size_t over = mix ? ((size_t)mdk * mdk * mni3 + 1) / 2 : 0;   // Vf, or the V^T planes
     if (tc) over = tc_ap_doubles(mdk, mni3);
     return (size_t)mdi * mdk * mni3 + (size_t)mdk * mdk * mni3 + (size_t)D * mdk * mni3 + 2ull * mdi * mdk +
-           ((size_t)mdi * mdk + 1) / 2 + (tc ? tc_bp_doubles(mdi, mdk) : 0) + (px ? shell_px_doubles(mdk, xc, D) : 0) +
+           ((size_t)mdi * mdk + 1) / 2 + (tc ? tc_bp_doubles(mdi, mdk) : 0) + (px ? shell_px_doubles(mdk, xc, D, mode == 0) : 0) +
            (chunk > over ? chunk : over);
 }
 
@@ -489,7 +493,8 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 512 / NT) k_shell(const Vt
     constexpr bool TC = MODE == 3;   // k4 contraction on the tensor cores, S3 contraction FP32, x-sum FP64
     constexpr bool PX = MODE == 4;   // S3 contraction FP32, x-sum on compensated pairs
     constexpr bool F32IN = FF || TC || PX;   // booster operands from the FP32 copies
-    constexpr bool AS = TC || PX;            // operands staged by asynchronous copies
+    constexpr bool AS = TC || PX || MODE == 0;   // operands staged by asynchronous copies
+    constexpr bool D64 = MODE == 0;              // ... as FP64 values (B2s, SB, S3s, B3 rows)
     constexpr int TRT = NT >= 1024 ? 1 : SF_TRT;   // output-tile blocks per thread
     constexpr int GU = FF ? 4 : 2;   // staging elements in flight per thread (FP64 values: register budget)
     extern __shared__ double smem[];
@@ -503,7 +508,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 512 / NT) k_shell(const Vt
     __shared__ VtxDev s_v;          // the current work item's vertex record
     __shared__ int s_vtx;
     if (threadIdx.x == 0) s_vtx = -1;
-    const ShellSmem sm = carve(smem, mdi, mdk, mk3u, XC, Dmax, mni3, TC, AS);
+    const ShellSmem sm = carve(smem, mdi, mdk, mk3u, XC, Dmax, mni3, TC, AS, D64);
     const int tid = threadIdx.x, nth = NT;
     for (;;) {
         __syncthreads();
@@ -669,19 +674,31 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 512 / NT) k_shell(const Vt
                         for (int q = tid; q < D * mdk * di3; q += nth) {
                             int d, i3, c3;
                             b3_at(q, d, i3, c3);
-                            const float* src = v.Bf[1] + ((int64_t)(t30 + d) * di3f + i3b + i3) * dk1 + c3;
-                            cp_async4(b3f + (d * mdk + c3) * di3 + i3, c3 < dk1 ? src : v.Bf[1], c3 < dk1 ? 4 : 0);
+                            const int64_t o = ((int64_t)(t30 + d) * di3f + i3b + i3) * dk1 + c3;
+                            const int e = (d * mdk + c3) * di3 + i3;
+                            if constexpr (D64) cp_async8(sm.B3s + e, c3 < dk1 ? v.B[1] + o : v.B[1], c3 < dk1 ? 8 : 0);
+                            else cp_async4(b3f + e, c3 < dk1 ? v.Bf[1] + o : v.Bf[1], c3 < dk1 ? 4 : 0);
                         }
+                        double* b2d = reinterpret_cast<double*>(sm.B2s);
                         for (int q = tid; q < D * mdk; q += nth) {
                             const int d = q / mdk, c2 = q - d * mdk;
-                            float b = 0.0f;
-                            if (c2 < s_nk2[d]) {
-                                const int k2 = s_k2lo[d] + 2 * c2;
-                                const int64_t bi = ((int64_t)((d * D + d24) * D + d25) * v.di[1] + ci2) * v.dkmax[0] + c2;
-                                const float f = (float)(k2 + 1) * ((c2 & 1) ? -s_sigf[d] : s_sigf[d]);
-                                b = f * __ldg(v.Bf[0] + bi);
+                            const int k2 = s_k2lo[d] + 2 * c2;
+                            const int64_t bi = ((int64_t)((d * D + d24) * D + d25) * v.di[1] + ci2) * v.dkmax[0] + c2;
+                            if constexpr (D64) {
+                                double b = 0.0;
+                                if (c2 < s_nk2[d]) {
+                                    const double f = (double)(k2 + 1) * ((c2 & 1) ? -s_sig[d] : s_sig[d]);
+                                    b = f * __ldg(v.B[0] + bi);
+                                }
+                                b2d[q] = b;
+                            } else {
+                                float b = 0.0f;
+                                if (c2 < s_nk2[d]) {
+                                    const float f = (float)(k2 + 1) * ((c2 & 1) ? -s_sigf[d] : s_sigf[d]);
+                                    b = f * __ldg(v.Bf[0] + bi);
+                                }
+                                sm.B2s[q] = b;
                             }
-                            sm.B2s[q] = b;
                         }
                     } else if constexpr (F32IN) {
                         gather_loop<4>(D * mdk * di3, tid, nth, [&](int q) {
@@ -717,9 +734,10 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 512 / NT) k_shell(const Vt
                     const FDiv f_nxc = fdiv_make(nxc), f_mdk = fdiv_make(mdk), f_nk4 = fdiv_make(nk4);
                     if constexpr (AS) {
                         // every operand by asynchronous copies (zero outside the slot boxes), then
-                        // the products in place: SB = B2s S5, and Q = ((S1 S2) (2x+1)) as pairs
-                        // (MODE 4) or Q = ((2x+1) S1) S2 in FP64 from the prescaled S1x (MODE 3),
-                        // with the roundings of forming them from loaded values
+                        // the products in place: SB = B2s S5 (FP32, or FP64 in MODE 0), and
+                        // Q = ((S1 S2) (2x+1)) as pairs (MODE 4) or Q = ((2x+1) S1) S2 in FP64 from
+                        // the prescaled S1x (MODES 0 and 3), with the roundings of forming them
+                        // from loaded values
                         float* sbf = reinterpret_cast<float*>(sm.SB);
                         float* s3f = reinterpret_cast<float*>(sm.S3s);
                         float2* qf = reinterpret_cast<float2*>(sm.Q);
@@ -728,13 +746,20 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 512 / NT) k_shell(const Vt
                             const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, d = fdiv_q(r, f_mdk), c2 = r - d * mdk;
                             if (c2 >= s_nk2[d]) continue;
                             const int i = s6_index(sd5, s_k2lo[d] + 2 * c2, i1, xc0 + 2 * xc);
-                            cp_async4(sbf + (d * mdk + c2) * XC + xc, i < 0 ? v.S5f : v.S5f + sd5.off + i, i < 0 ? 0 : 4);
+                            const int e = (d * mdk + c2) * XC + xc;
+                            if constexpr (D64) cp_async8(sm.SB + e, v.S[4] + (i < 0 ? 0 : sd5.off + i), i < 0 ? 0 : 8);
+                            else cp_async4(sbf + e, i < 0 ? v.S5f : v.S5f + sd5.off + i, i < 0 ? 0 : 4);
                         }
                         for (int q = tid; q < nxc * nk4 * nk3u; q += nth) {
                             const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, c4 = fdiv_q(r, f_nk3u), ku = r - c4 * nk3u;
                             const int i = s6_index(sd3, k4lo + 2 * c4, k3ulo + 2 * ku, xc0 + 2 * xc);
-                            const float* src = reinterpret_cast<const float*>(v.Sff[2] + (i < 0 ? 0 : sd3.off + i));
-                            cp_async4(s3f + (xc * nk4 + c4) * nk3u + ku, src, i < 0 ? 0 : 4);   // the high part
+                            const int e = (xc * nk4 + c4) * nk3u + ku;
+                            if constexpr (D64) {
+                                cp_async8(sm.S3s + e, v.S[2] + (i < 0 ? 0 : sd3.off + i), i < 0 ? 0 : 8);
+                            } else {
+                                const float* src = reinterpret_cast<const float*>(v.Sff[2] + (i < 0 ? 0 : sd3.off + i));
+                                cp_async4(s3f + e, src, i < 0 ? 0 : 4);   // the high part
+                            }
                         }
                         for (int q = tid; q < nk5 * nk4 * nxc; q += nth) {
                             const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, c5 = fdiv_q(r, f_nk4), c4 = r - c5 * nk4;
@@ -753,8 +778,13 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 512 / NT) k_shell(const Vt
                         for (int q = tid; q < D * mdk * nxc; q += nth) {
                             const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, d = fdiv_q(r, f_mdk), c2 = r - d * mdk;
                             if (c2 >= s_nk2[d]) continue;
-                            float* e = sbf + (d * mdk + c2) * XC + xc;
-                            *e = sm.B2s[d * mdk + c2] * *e;
+                            if constexpr (D64) {
+                                double* e = sm.SB + (d * mdk + c2) * XC + xc;
+                                *e = reinterpret_cast<const double*>(sm.B2s)[d * mdk + c2] * *e;
+                            } else {
+                                float* e = sbf + (d * mdk + c2) * XC + xc;
+                                *e = sm.B2s[d * mdk + c2] * *e;
+                            }
                         }
                         for (int q = tid; q < nk5 * nk4 * nxc; q += nth) {
                             const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, c5 = fdiv_q(r, f_nk4);
