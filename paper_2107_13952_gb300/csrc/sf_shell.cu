@@ -456,7 +456,7 @@ __device__ inline ShellSmem carve(double* base, int mdi, int mdk, int mk3u, int 
 }
 
 size_t sf_shell_smem_doubles(int mdi, int mdk, int mk3u, int xc, int D, int mni3, int mode) {
-    const bool mix = mode >= 1, tc = mode == 3, px = mode >= 3 || mode == 0;   // px: asynchronous staging
+    const bool mix = mode >= 1, tc = mode == 3, px = mode != 1;   // px: asynchronous staging
     const size_t chunk = shell_chunk_doubles(mdk, mk3u, xc, D, mni3);
     size_t over = mix ? ((size_t)mdk * mdk * mni3 + 1) / 2 : 0;   // Vf, or the V^T planes
     if (tc) over = tc_ap_doubles(mdk, mni3);
@@ -493,7 +493,8 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 512 / NT) k_shell(const Vt
     constexpr bool TC = MODE == 3;   // k4 contraction on the tensor cores, S3 contraction FP32, x-sum FP64
     constexpr bool PX = MODE == 4;   // S3 contraction FP32, x-sum on compensated pairs
     constexpr bool F32IN = FF || TC || PX;   // booster operands from the FP32 copies
-    constexpr bool AS = TC || PX || MODE == 0;   // operands staged by asynchronous copies
+    constexpr bool AS = MODE != 1;               // operands staged by asynchronous copies
+    constexpr bool PQ = FF || PX;                // Q and S1 as compensated pairs
     constexpr bool D64 = MODE == 0;              // ... as FP64 values (B2s, SB, S3s, B3 rows)
     constexpr int TRT = NT >= 1024 ? 1 : SF_TRT;   // output-tile blocks per thread
     constexpr int GU = FF ? 4 : 2;   // staging elements in flight per thread (FP64 values: register budget)
@@ -735,9 +736,9 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 512 / NT) k_shell(const Vt
                     if constexpr (AS) {
                         // every operand by asynchronous copies (zero outside the slot boxes), then
                         // the products in place: SB = B2s S5 (FP32, or FP64 in MODE 0), and
-                        // Q = ((S1 S2) (2x+1)) as pairs (MODE 4) or Q = ((2x+1) S1) S2 in FP64 from
-                        // the prescaled S1x (MODES 0 and 3), with the roundings of forming them
-                        // from loaded values
+                        // Q = ((S1 S2) (2x+1)) as pairs (MODES 2 and 4) or Q = ((2x+1) S1) S2 in FP64
+                        // from the prescaled S1x (MODES 0 and 3), with the roundings of forming
+                        // them from loaded values
                         float* sbf = reinterpret_cast<float*>(sm.SB);
                         float* s3f = reinterpret_cast<float*>(sm.S3s);
                         float2* qf = reinterpret_cast<float2*>(sm.Q);
@@ -756,6 +757,9 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 512 / NT) k_shell(const Vt
                             const int e = (xc * nk4 + c4) * nk3u + ku;
                             if constexpr (D64) {
                                 cp_async8(sm.S3s + e, v.S[2] + (i < 0 ? 0 : sd3.off + i), i < 0 ? 0 : 8);
+                            } else if constexpr (FF) {   // the (hi, lo) pair
+                                cp_async8(reinterpret_cast<float2*>(sm.S3s) + e, v.Sff[2] + (i < 0 ? 0 : sd3.off + i),
+                                          i < 0 ? 0 : 8);
                             } else {
                                 const float* src = reinterpret_cast<const float*>(v.Sff[2] + (i < 0 ? 0 : sd3.off + i));
                                 cp_async4(s3f + e, src, i < 0 ? 0 : 4);   // the high part
@@ -764,13 +768,13 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 512 / NT) k_shell(const Vt
                         for (int q = tid; q < nk5 * nk4 * nxc; q += nth) {
                             const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, c5 = fdiv_q(r, f_nk4), c4 = r - c5 * nk4;
                             const int i = s6_index(sd2, k5lo + 2 * c5, k4lo + 2 * c4, xc0 + 2 * xc);
-                            if constexpr (PX) cp_async8(qf + q, v.Sff[1] + (i < 0 ? 0 : sd2.off + i), i < 0 ? 0 : 8);
+                            if constexpr (PQ) cp_async8(qf + q, v.Sff[1] + (i < 0 ? 0 : sd2.off + i), i < 0 ? 0 : 8);
                             else cp_async8(sm.Q + q, v.S[1] + (i < 0 ? 0 : sd2.off + i), i < 0 ? 0 : 8);
                         }
                         for (int q = tid; q < nk5 * nxc; q += nth) {
                             const int c5 = fdiv_q(q, f_nxc), xc = q - c5 * nxc;
                             const int i = s6_index(sd1, i1, k5lo + 2 * c5, xc0 + 2 * xc);
-                            if constexpr (PX) cp_async8(s1f + q, v.Sff[0] + (i < 0 ? 0 : sd1.off + i), i < 0 ? 0 : 8);
+                            if constexpr (PQ) cp_async8(s1f + q, v.Sff[0] + (i < 0 ? 0 : sd1.off + i), i < 0 ? 0 : 8);
                             else cp_async8(sm.S1s + q, v.S1x + (i < 0 ? 0 : sd1.off + i), i < 0 ? 0 : 8);
                         }
                         cp_async_wait_all();
@@ -788,7 +792,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 1 : 512 / NT) k_shell(const Vt
                         }
                         for (int q = tid; q < nk5 * nk4 * nxc; q += nth) {
                             const int r = fdiv_q(q, f_nxc), xc = q - r * nxc, c5 = fdiv_q(r, f_nk4);
-                            if constexpr (PX) qf[q] = ff_mul_f(ff_mul(s1f[c5 * nxc + xc], qf[q]), (float)(xc0 + 2 * xc + 1));
+                            if constexpr (PQ) qf[q] = ff_mul_f(ff_mul(s1f[c5 * nxc + xc], qf[q]), (float)(xc0 + 2 * xc + 1));
                             else sm.Q[q] = sm.S1s[c5 * nxc + xc] * sm.Q[q];
                         }
                     } else {
