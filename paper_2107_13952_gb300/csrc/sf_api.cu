@@ -84,6 +84,7 @@ struct sf_tables {
     double *d_Aj = nullptr, *d_Cj = nullptr;   // boundary-side 3j scratch (largest edge)
     // amplitude scratch (grown on demand)
     void* d_scratch = nullptr;
+    cudaStream_t side = nullptr;   // second stream of the shell sum's launch classes (created on first use)
     size_t scratch_bytes = 0;
     std::vector<void*> owned;
 };
@@ -327,6 +328,7 @@ extern "C" void sf_tables_free(sf_tables* t) {
     if (!t) return;
     for (void* p : t->owned) cudaFree(p);
     if (t->d_scratch) cudaFree(t->d_scratch);
+    if (t->side) cudaStreamDestroy(t->side);
     delete t;
 }
 
@@ -993,9 +995,9 @@ static int kappa_pass(sf_tables* t, const int64_t* shell_list, int64_t n_list, i
 
 // Launch classes of a shell sum with the default tiling. A batch whose largest vertex needs one
 // CTA per SM would otherwise run every vertex that way; the vertices whose tiles fit two CTAs of
-// 256 threads per SM (with an x chunk of at least 4) then run in a launch of their own, after the
-// others, on the same stream (two CTAs per SM interleave their phases: measured 20 % faster at
-// spin 5). One class otherwise.
+// 256 threads per SM (with an x chunk of at least 4) then run in a launch of their own on a second
+// stream, whose CTAs take the SMs that the first launch's CTAs leave (two CTAs per SM interleave
+// their phases: measured 20 % faster at spin 5). One class otherwise.
 struct LaunchClass {
     VertexMask mask;
     ShellConfig cfg;
@@ -1104,12 +1106,25 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
     SF_CUDA_TRY(cudaEventCreate(&ev0));
     SF_CUDA_TRY(cudaEventCreate(&ev1));
     SF_CUDA_TRY(cudaEventRecord(ev0, stream));
+    // the second class runs on a second stream, so that its CTAs take the SMs the first launch's
+    // persistent CTAs leave at its tail; the caller's stream waits for both before the reduction
+    const bool two = cls.size() > 1 && cls[0].nitems > 0 && cls[1].nitems > 0;
+    if (two && !t->side) SF_CUDA_TRY(cudaStreamCreateWithFlags(&t->side, cudaStreamNonBlocking));
+    if (two) SF_CUDA_TRY(cudaStreamWaitEvent(t->side, ev0, 0));
     for (size_t c = 0; c < cls.size(); c++) {
         if (cls[c].nitems == 0) continue;
         const ShellDims& dm = cls[c].dims;
         SF_TRY(sf_shell_launch_prepared(mix, cls[c].cfg.nt, grids[c], smems[c], t->d_vtx, dm.mdi, dm.mdk, dm.mk3u,
                                         cls[c].cfg.xc, dm.Dmax, cls[c].mni3, d_items + cls[c].item0, (int)cls[c].nitems,
-                                        d_counter + c, d_part, filt, stream));
+                                        d_counter + c, d_part, filt, (two && c > 0) ? t->side : stream));
+    }
+    if (two) {
+        cudaEvent_t join = nullptr;
+        SF_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+        cudaError_t e = cudaEventRecord(join, t->side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, join, 0);
+        cudaEventDestroy(join);
+        SF_CUDA_TRY(e);
     }
     SF_CUDA_TRY(cudaEventRecord(ev1, stream));
     SF_TRY(sf_reduce_jobs_launch(t->d_vtx, d_jobs, (int)sc.jobs.size(), d_items, d_part, stream));
