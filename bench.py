@@ -65,7 +65,7 @@ FFD_OPS = 11
 # DRAM bytes (read + write) of the headline path's shell-sum launches of one step (the step's two
 # launch classes) from one ncu capture of the benchmark's first timed step after three warm-up
 # steps (slice 3 of 32), valid while the kernel source hashes to "sha1"
-NCU_TRAFFIC = {"sha1": "884ba02a215a", "bytes_per_step": 338953472 + 90769664 + 454982912 + 29517056}
+NCU_TRAFFIC = {"sha1": "0cf314fbb99f", "bytes_per_step": 329967360 + 90086912 + 507539200 + 30302720}
 
 
 def workload_name(slices):
