@@ -159,7 +159,10 @@ int sf_6j_table_range(const sf_vertex* v, int32_t n, int64_t shell_begin, int64_
 
 /* Compute the booster tensors of every vertex in t (Sec. 2 eq. booster, Sec. 3): d-tables
  * d^{gamma(j+1), j}_{j l m}(r_n) on the rule's nodes, 4jm symbols, quadrature and m-sum.
- * q: host pointer to the rule. */
+ * q: host pointer to the rule. Per edge, the node products of each pair of strands and the
+ * virtual-side 3j symbols of each pair of virtual spins are tabulated first, in stream-ordered
+ * scratch from a memory pool of the library's own on the current device (kept for reuse by later
+ * calls: at dl 10 and spin 8 about 1.2 GB). Synchronises the stream (status check). */
 int sf_boosters(sf_tables* t, const sf_quad_rule* q, cudaStream_t stream);
 
 /* Shape of the booster tensor of (vertex, edge in 2..5): shape = {n_triples, D_i, D_kmax}. */
@@ -173,7 +176,7 @@ int sf_boosters_upload(sf_tables* t, int32_t vertex, int32_t edge, const double*
 int sf_boosters_download(const sf_tables* t, int32_t vertex, int32_t edge, double* B, cudaStream_t stream);
 
 /* Vertex amplitude tensors by the shell sum (framed algorithm steps 5-7).
- *   precision  SF_FP64, SF_MIXED or SF_MIXED_FF.
+ *   precision  any sf_precision value (SF_FP64, SF_MIXED, SF_MIXED_FF, SF_MIXED_TC, SF_MIXED_PX).
  *   shell_begin, shell_end: linear shell range [begin, end) of every vertex (clamped to its shell
  *     count; pass 0 and INT64_MAX for all shells). Partial sums over disjoint ranges add up, so a
  *     long sum can be split or resumed.
@@ -188,7 +191,10 @@ int sf_boosters_download(const sf_tables* t, int32_t vertex, int32_t edge, doubl
  *     rounding errors (error ~ kappa times the FP32 unit roundoff). It costs one extra pass with
  *     the shell sum unhoisted across shells (about a full framed-algorithm evaluation per shell,
  *     several times the amplitude itself), so ask for it on shell lists or small ranges.
- * Uses library-owned scratch for per-block partial sums, reduced in a fixed order (deterministic). */
+ * Uses library-owned scratch for per-block partial sums, reduced in a fixed order (deterministic).
+ * A batch whose vertices need different CTA shapes runs as two launches, the second on a stream
+ * the tables own, ordered after the caller's stream's earlier work and joined back into it before
+ * the reduction. Synchronises the caller's stream (status check). */
 int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t shell_begin, int64_t shell_end,
                         const int64_t* shell_list, int64_t n_list, double* const* A_out, double* kappa_out,
                         cudaStream_t stream);
