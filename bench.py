@@ -303,7 +303,8 @@ def batched_measure(precisions):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         res[name] = {"value": n_ne / (ms / 1e3), "unit": "non-empty shells/s", "all_shells_per_s": n_all / (ms / 1e3),
-                     "ms_per_launch": ms, "tiling": dict(zip(("x_chunk", "items_per_sm", "threads", "i3_split"), tiling))}
+                     "amplitudes_per_s": len(batch) / (ms / 1e3), "ms_per_launch": ms,
+                     "tiling": dict(zip(("x_chunk", "items_per_sm", "threads", "i3_split"), tiling))}
         outs[name] = [o.clone() for o in plan.outputs]
         del plan
     if "fp64" in outs:
@@ -337,7 +338,7 @@ def large_shell_measure(precisions):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         res[name] = {"value": n_ne / (ms / 1e3), "unit": "non-empty shells/s", "ms": ms,
-                     "kernel_ms": sf.last_kernel_ms()}
+                     "amplitudes_per_s": 1e3 / ms, "kernel_ms": sf.last_kernel_ms()}
         outs[name] = A.clone()
     for name in outs:
         if name != "fp64" and "fp64" in outs:
@@ -370,7 +371,7 @@ def adjoint_measure():
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        out[label] = {"value": n_ne / (ms / 1e3), "unit": "non-empty shells/s", "ms": ms}
+        out[label] = {"value": n_ne / (ms / 1e3), "unit": "non-empty shells/s", "ms": ms, "amplitudes_per_s": 1e3 / ms}
     return dict(workload="all spins 3, gamma 1.2, dl 8 (531,441 shells, %d non-empty): boundary-contracted "
                          "amplitude, FP64" % n_ne, **out)
 
@@ -752,6 +753,8 @@ def main():
                             "each slice reads the groups of other l35 values than the previous one), so no step "
                             "starts with its working set in L2; no separate flush"},
         "all_shells_per_s": alls * world / (ms / 1e3),
+        # whole vertex tensors of the sweep per second at this rate (16 tensors per S steps)
+        "amplitudes_per_s": len(SWEEP) * world / (S * ms / args.steps / 1e3),
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "non-empty shells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
