@@ -66,6 +66,7 @@ struct VertexHost {
     bool restricted = false;                    // g_lo > 0 or g_hi < ngroups
     unsigned char* d_need6[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // slots built
     unsigned char* d_needB[4] = {nullptr, nullptr, nullptr, nullptr};            // triples computed
+    std::vector<unsigned char> needB_h[4];      // host copies of d_needB (empty: every triple)
 };
 
 struct sf_tables {
@@ -362,12 +363,16 @@ static int build_needs(sf_tables* t, VertexHost& h) {
     // boosters: t = (a D + b) D + c over the edge's three offsets
     for (size_t q = 0; q < m.size(); q++) m[q] = n25[q % D];            // edge 2 (d23, d24, d25)
     SF_TRY(put(&h.d_needB[0]));
+    h.needB_h[0] = m;
     for (size_t q = 0; q < m.size(); q++) m[q] = n35[(q / D) % D];      // edge 3 (d34, d35, d23)
     SF_TRY(put(&h.d_needB[1]));
+    h.needB_h[1] = m;
     for (size_t q = 0; q < m.size(); q++) m[q] = n45[q / ((size_t)D * D)];   // edge 4 (d45, d24, d34)
     SF_TRY(put(&h.d_needB[2]));
+    h.needB_h[2] = m;
     for (size_t q = 0; q < m.size(); q++) m[q] = ((int64_t)q >= h.g_lo && (int64_t)q < h.g_hi) ? 1 : 0;   // edge 5 = g
     SF_TRY(put(&h.d_needB[3]));
+    h.needB_h[3] = m;
     return SF_OK;
 }
 
@@ -609,8 +614,37 @@ static int boosters_all(sf_tables* t, int nnodes, double2* const d_P[2], double*
                                  stream));
             const double2* cP[2] = {d_P[0], d_P[1]};
             const double* cT[2] = {d_T[0], d_T[1]};
-            SF_TRY(sf_booster_build(t->d_vtx + i, e + 2, (int)h.ntrip, smem, nc, t->d_W, nnodes, t->d_fact, t->d_Aj, t->d_Cj,
-                                    h.d_B[e], h.d_needB[e], cP, cT, pd, t->d_status, stream));
+            // the edge's pair of free strands (coupling positions pos, pos + 1): with equal spins
+            // the triples whose two offsets there decrease are filled from the exchanged triple
+            const int pos = e < 2 ? 0 : 2;
+            const bool mirror = j[faces[e][pos]] == j[faces[e][pos + 1]];
+            const unsigned char* d_need = h.d_needB[e];
+            unsigned char* d_masks = nullptr;
+            if (mirror) {
+                const int D = h.D, sa = bslot[e][pos], sb = bslot[e][pos + 1];
+                const std::vector<unsigned char>& need = h.needB_h[e];
+                std::vector<unsigned char> masks(2 * (size_t)h.ntrip, 0);   // computed | filled by exchange
+                for (int64_t q = 0; q < h.ntrip; q++) {
+                    if (!need.empty() && !need[q]) continue;
+                    int off[3] = {(int)(q / ((int64_t)D * D)), (int)((q / D) % D), (int)(q % D)};
+                    if (off[sa] <= off[sb]) {
+                        masks[q] = 1;
+                    } else {
+                        std::swap(off[sa], off[sb]);
+                        masks[((int64_t)off[0] * D + off[1]) * D + off[2]] = 1;
+                        masks[h.ntrip + q] = 1;
+                    }
+                }
+                SF_TRY(sf_scratch_alloc((void**)&d_masks, masks.size(), stream));
+                SF_CUDA_TRY(cudaMemcpyAsync(d_masks, masks.data(), masks.size(), cudaMemcpyHostToDevice, stream));
+                d_need = d_masks;
+            }
+            int rc = sf_booster_build(t->d_vtx + i, e + 2, (int)h.ntrip, smem, nc, t->d_W, nnodes, t->d_fact, t->d_Aj,
+                                      t->d_Cj, h.d_B[e], d_need, cP, cT, pd, t->d_status, stream);
+            if (rc == SF_OK && mirror) rc = sf_booster_mirror(t->d_vtx + i, e + 2, pos, (int)h.ntrip, d_masks + h.ntrip,
+                                                             h.d_B[e], stream);
+            if (d_masks) sf_scratch_free(d_masks, stream);
+            SF_TRY(rc);
             SF_TRY(sf_to_float(h.d_B[e], h.d_Bf[e], (int64_t)h.ntrip * h.di[e + 1] * h.dkmax[e], t->num_sms, stream));
         }
         h.boosters_ready = true;

@@ -624,6 +624,52 @@ __global__ void __launch_bounds__(SF_BOOST_NT) k_booster(const VtxDev* __restric
     }
 }
 
+// Boosters of the triples that sf_boosters fills by exchange. When the two strands of a coupled
+// pair carry equal spins, their d-functions coincide, and exchanging the strands multiplies the
+// booster by the 3j exchange phase in both 4jm symbols, (-1)^((j_a + j_b + i) + (l_a + l_b + k))
+// (eq. booster with the (a1 a2)(a3 a4) coupling): so the booster of a triple whose offsets on the
+// pair decrease is the exchanged triple's, times that sign. One CTA per triple; fill[t] != 0
+// selects the triples; the exchanged triples were computed by k_booster.
+__global__ void k_booster_mirror(const VtxDev* __restrict__ vp, int edge, int pos, const unsigned char* __restrict__ fill,
+                                 double* __restrict__ Bout) {
+    const VtxDev& v = *vp;
+    const int e = edge - 2, D = v.D, t = blockIdx.x;
+    if (!fill[t]) return;
+    int off[3] = {t / (D * D), (t / D) % D, t % D};
+    int tj[4], tl[4];
+    for (int a = 0; a < 4; a++) {
+        tj[a] = v.tj[c_edge_face[e][a]];
+        const int sl = c_edge_slot[e][a];
+        tl[a] = tj[a] + 2 * (sl < 0 ? 0 : off[sl]);
+    }
+    const int sa = c_edge_slot[e][pos], sb = c_edge_slot[e][pos + 1];
+    const int tmp = off[sa];
+    off[sa] = off[sb];
+    off[sb] = tmp;
+    const int t2 = (off[0] * D + off[1]) * D + off[2];
+    int klo, nk;
+    sf_pair_range(tl[0], tl[1], tl[2], tl[3], &klo, &nk);
+    const int di = v.di[e + 1], ilo = v.ilo[e + 1], dkmax = v.dkmax[e];
+    const double* src = Bout + (int64_t)t2 * di * dkmax;
+    double* dst = Bout + (int64_t)t * di * dkmax;
+    const int base = tj[pos] + tj[pos + 1] + tl[pos] + tl[pos + 1] + ilo + klo;
+    for (int q = threadIdx.x; q < di * nk; q += blockDim.x) {
+        const int ci = q / nk, ck = q - ci * nk;
+        const int ex = (base + 2 * ci + 2 * ck) / 2;   // (j_a + j_b + i + l_a + l_b + k) in whole units
+        const double b = src[ci * dkmax + ck];
+        dst[ci * dkmax + ck] = (ex & 1) ? -b : b;
+    }
+}
+
+int sf_booster_mirror(const VtxDev* d_v, int edge, int pos, int ntrip, const unsigned char* d_fill, double* d_B,
+                      cudaStream_t s) {
+    if (ntrip <= 0) return SF_OK;
+    k_booster_mirror<<<ntrip, 128, 0, s>>>(d_v, edge, pos, d_fill, d_B);
+    sf_note_launch(1);
+    SF_CUDA_TRY(cudaGetLastError());
+    return SF_OK;
+}
+
 size_t sf_booster_smem(int tj1, int tj2, int tj3, int tj4, int nk) {
     int n1 = tj1 + 1, n2 = tj2 + 1, n3 = tj3 + 1, n4 = tj4 + 1;
     size_t M = ((size_t)n1 * n2 * n3 + 1) & ~(size_t)1;

@@ -300,6 +300,10 @@ struct PairDims { int nb[2], npid[2], nkk[2]; };
 int sf_pair_dims(const int tj4[4], const int slot4[4], int D, int nnodes, PairDims* pd, size_t pbytes[2], size_t tbytes[2]);
 int sf_pair_build(const VtxDev* d_v, int edge, const PairDims& pd, const double* d_W, int nnodes, const dd* F,
                   const int tj4[4], double2* const d_P[2], double* const d_T[2], int* d_status, int num_sms, cudaStream_t s);
+// boosters of the triples fill[t] != 0 from their exchanged triples on the pair of free strands at
+// coupling positions (pos, pos + 1), whose spins are equal
+int sf_booster_mirror(const VtxDev* d_v, int edge, int pos, int ntrip, const unsigned char* d_fill, double* d_B,
+                      cudaStream_t s);
 // d_need (optional): per virtual-spin triple, nonzero if its booster is computed (the others are zero);
 // d_P, d_T: the edge's pair tables (sf_pair_build)
 int sf_booster_build(const VtxDev* d_v, int edge, int ntrip, size_t smem, int nc, const double* d_W, int nnodes,
