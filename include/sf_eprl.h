@@ -162,7 +162,10 @@ int sf_6j_table_range(const sf_vertex* v, int32_t n, int64_t shell_begin, int64_
  * q: host pointer to the rule. Per edge, the node products of each pair of strands and the
  * virtual-side 3j symbols of each pair of virtual spins are tabulated first, in stream-ordered
  * scratch from a memory pool of the library's own on the current device (kept for reuse by later
- * calls: at dl 10 and spin 8 about 1.2 GB). Synchronises the stream (status check). */
+ * calls: at dl 10 and spin 8 about 1.2 GB). When the two free strands of an edge's coupled pair
+ * carry equal spins, the triples with decreasing offsets on that pair are filled from the
+ * exchanged triple times the 3j exchange phase (-1)^(j_a + j_b + i + l_a + l_b + k) instead of
+ * being integrated again. Synchronises the stream (status check). */
 int sf_boosters(sf_tables* t, const sf_quad_rule* q, cudaStream_t stream);
 
 /* Shape of the booster tensor of (vertex, edge in 2..5): shape = {n_triples, D_i, D_kmax}. */
