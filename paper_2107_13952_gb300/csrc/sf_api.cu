@@ -636,7 +636,11 @@ static int boosters_all(sf_tables* t, int nnodes, double2* const d_P[2], double*
                     }
                 }
                 SF_TRY(sf_scratch_alloc((void**)&d_masks, masks.size(), stream));
-                SF_CUDA_TRY(cudaMemcpyAsync(d_masks, masks.data(), masks.size(), cudaMemcpyHostToDevice, stream));
+                const cudaError_t ce = cudaMemcpyAsync(d_masks, masks.data(), masks.size(), cudaMemcpyHostToDevice, stream);
+                if (ce != cudaSuccess) {
+                    sf_scratch_free(d_masks, stream);
+                    return sf_set_error(SF_ERR_CUDA, "booster mask copy: %s", cudaGetErrorString(ce));
+                }
                 d_need = d_masks;
             }
             int rc = sf_booster_build(t->d_vtx + i, e + 2, (int)h.ntrip, smem, nc, t->d_W, nnodes, t->d_fact, t->d_Aj,
@@ -1136,9 +1140,17 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
                                 (int)cls[c].nitems, t->num_sms, &grids[c], &smems[c]));
     }
     SF_CUDA_TRY(cudaMemsetAsync(t->d_status, 0, sizeof(int), stream));
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    SF_CUDA_TRY(cudaEventCreate(&ev0));
-    SF_CUDA_TRY(cudaEventCreate(&ev1));
+    // events destroyed on every return path (destroying an event with work pending is allowed)
+    struct EventPair {
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~EventPair() {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } evs;
+    SF_CUDA_TRY(cudaEventCreate(&evs.a));
+    SF_CUDA_TRY(cudaEventCreate(&evs.b));
+    cudaEvent_t ev0 = evs.a, ev1 = evs.b;
     SF_CUDA_TRY(cudaEventRecord(ev0, stream));
     // the second class runs on a second stream, so that its CTAs take the SMs the first launch's
     // persistent CTAs leave at its tail; the caller's stream waits for both before the reduction
@@ -1165,8 +1177,6 @@ extern "C" int sf_vertex_amplitude(sf_tables* t, sf_precision precision, int64_t
     int rc = check_status(t, stream, "sf_vertex_amplitude");
     float ms = -1.0f;
     if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) g_last_kernel_ms = ms;
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
     if (rc == SF_OK && kappa_out) {
         rc = kappa_pass(t, shell_list, n_list, shell_begin, shell_end, filt, kappa_out, stream);
         if (rc == SF_OK) rc = check_status(t, stream, "sf_vertex_amplitude (kappa)");
